@@ -1,0 +1,180 @@
+"""Pins of the oracle's Valencia pieces: conserved-variable map, primitive recovery,
+fluxes, stress-energy tensor, 3+1 matter terms and geometric sources.
+
+Paper: "GRMHD Conservative Form", "The Primitive Variable Recovery", "The Conserved
+Fluxes and Geometric Source Terms", "Stress-Energy Tensor".
+"""
+import numpy as np
+import pytest
+
+from oracle import kerr_schild as ks
+from oracle import valencia as va
+
+from helpers import assert_within
+
+GAM = 4.0 / 3.0
+
+
+def random_states(n=600, seed=11, a=0.7, bmax=True):
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(1.5, 30, n)
+    th = rng.uniform(0.2, np.pi - 0.2, n)
+    alpha, beta, gam = ks.adm(1.0, a, r, th)
+    rho = 10 ** rng.uniform(-8, 0, n)
+    eps = 10 ** rng.uniform(-6, 1, n)
+    vd = rng.normal(size=(n, 3))
+    vu = np.einsum("nij,nj->ni", ks.inv3(gam), vd)
+    v2 = np.einsum("ni,ni->n", vd, vu)
+    vu *= (rng.uniform(0, 0.99, n) / np.sqrt(v2))[:, None]
+    B = rng.normal(size=(n, 3))
+    p = (GAM - 1) * rho * eps
+    B2 = np.einsum("ni,ni->n", va.lower(gam, B), B)
+    beta_pl = 10 ** rng.uniform(-2, 4, n)
+    B *= np.sqrt(2 * p / beta_pl / B2)[:, None]
+    return dict(rho=rho, v=vu, eps=eps, B=B, alpha=alpha, beta=beta, gam=gam)
+
+
+def test_p2c_two_forms_agree():
+    s = random_states()
+    D, S, tau, _ = va.prim_to_cons(s["rho"], s["v"], s["eps"], s["B"], s["alpha"], s["beta"],
+                                   s["gam"], GAM)
+    D2, S2, tau2 = va.prim_to_cons_eulerian(s["rho"], s["v"], s["eps"], s["B"], s["gam"], GAM)
+    np.testing.assert_allclose(D, D2, rtol=1e-14)
+    scale = np.abs(S2).max(axis=1, keepdims=True)
+    assert_within(S, S2, 1e-12 * scale, 'S_j')
+    assert_within(tau, tau2, 1e-11 * (tau2 + D2), 'tau')
+
+
+def test_p2c_unmagnetised_textbook():
+    s = random_states()
+    B0 = np.zeros_like(s["B"])
+    D, S, tau, _ = va.prim_to_cons(s["rho"], s["v"], s["eps"], B0, s["alpha"], s["beta"],
+                                   s["gam"], GAM)
+    W = va.lorentz_factor(s["v"], s["gam"])
+    p = (GAM - 1) * s["rho"] * s["eps"]
+    h = 1 + s["eps"] + p / s["rho"]
+    np.testing.assert_allclose(S, (s["rho"] * h * W * W)[:, None] * va.lower(s["gam"], s["v"]),
+                               rtol=1e-12, atol=1e-300)
+    assert_within(tau, s["rho"] * h * W * W - p - s["rho"] * W, 1e-13 * (tau + D), "tau")
+
+
+def test_con2prim_round_trip():
+    s = random_states(n=1500, seed=12)
+    D, S, tau, B = va.prim_to_cons(s["rho"], s["v"], s["eps"], s["B"], s["alpha"], s["beta"],
+                                   s["gam"], GAM)
+    rho, v, eps, p, W, ok = va.con2prim(D, S, tau, B, s["gam"], GAM)
+    assert ok.all()
+    np.testing.assert_allclose(rho, s["rho"], rtol=1e-12)
+    np.testing.assert_allclose(v, s["v"], atol=1e-12)
+    # eps is recovered from tau - (kinetic + magnetic energy): its absolute error scales
+    # with (tau + D)/D
+    scale = (tau + D) / D
+    assert np.all(np.abs(eps - s["eps"]) <= 1e-12 * scale * np.maximum(1, W ** 2))
+
+
+def test_con2prim_floor():
+    """A state whose exact inversion has eps < 0: the clamped master function still has a
+    root, eps is set to the floor and the point is flagged."""
+    s = random_states(n=50, seed=13)
+    D, S, tau, B = va.prim_to_cons(s["rho"], s["v"], s["eps"], s["B"], s["alpha"], s["beta"],
+                                   s["gam"], GAM)
+    tau_bad = tau - 2.0 * s["eps"] * D - 0.1 * D
+    rho, v, eps, p, W, ok = va.con2prim(D, S, tau_bad, B, s["gam"], GAM, eps_min=1e-10)
+    assert (~ok).sum() > 25
+    assert np.all(eps >= 1e-10) and np.all(np.isfinite(v))
+    assert np.all(W >= 1.0)
+
+
+def test_stress_energy_invariants():
+    s = random_states()
+    args = (s["rho"], s["v"], s["eps"], s["B"], s["alpha"], s["beta"], s["gam"], GAM)
+    u, b, b_d, b2, W, p = va.four_vectors(*args)
+    g4 = va.metric4_from_adm(s["alpha"], s["beta"], s["gam"])
+    u_d = np.einsum("nmk,nk->nm", g4, u)
+    np.testing.assert_allclose(np.einsum("nm,nm->n", u, u_d), -1.0, atol=1e-12)
+    assert_within(np.einsum("nm,nm->n", b, u_d), 0.0, 1e-12 * np.sqrt(b2) * W * W, "b.u")
+    T = va.stress_energy(*args)
+    e = s["rho"] * (1 + s["eps"])
+    trace = np.einsum("nmk,nmk->n", g4, T)
+    assert_within(trace, 3 * p - e, 1e-12 * (e + b2) * W * W, "trace")
+    # energy density in the fluid frame: u_mu u_nu T^{mu nu} = e + b^2/2
+    assert_within(np.einsum("nm,nk,nmk->n", u_d, u_d, T), e + 0.5 * b2,
+                  1e-12 * (e + b2) * W ** 4, "u u T")
+
+
+def test_matter_terms_equal_conserved():
+    """Eulerian energy and momentum densities equal the conserved tau + D and S_j."""
+    s = random_states()
+    args = (s["rho"], s["v"], s["eps"], s["B"], s["alpha"], s["beta"], s["gam"], GAM)
+    D, S, tau, _ = va.prim_to_cons(*args)
+    T = va.stress_energy(*args)
+    rho_adm, S_d, S_dd, Str = va.matter_3p1(T, s["alpha"], s["beta"], s["gam"])
+    np.testing.assert_allclose(rho_adm, tau + D, rtol=1e-11)
+    assert_within(S_d, S, 1e-11 * np.abs(S).max(axis=1, keepdims=True), "S_i")
+    # unmagnetised: S_ij = rho h W^2 v_i v_j + p gamma_ij
+    B0 = np.zeros_like(s["B"])
+    T0 = va.stress_energy(s["rho"], s["v"], s["eps"], B0, s["alpha"], s["beta"], s["gam"], GAM)
+    _, _, S_dd0, _ = va.matter_3p1(T0, s["alpha"], s["beta"], s["gam"])
+    W = va.lorentz_factor(s["v"], s["gam"])
+    p = (GAM - 1) * s["rho"] * s["eps"]
+    h = 1 + s["eps"] + p / s["rho"]
+    vd = va.lower(s["gam"], s["v"])
+    ref = ((s["rho"] * h * W * W)[:, None, None] * np.einsum("ni,nj->nij", vd, vd)
+           + p[:, None, None] * s["gam"])
+    np.testing.assert_allclose(S_dd0, ref, rtol=1e-10, atol=1e-14 * np.abs(ref).max())
+
+
+def test_fluxes_against_stress_energy():
+    """script-F^i_{S_j} = alpha T^i_j, script-F^i_tau = alpha^2 T^{0i} - D vt^i,
+    script-F^i_D = alpha rho u^i (covariant statements of the same fluxes)."""
+    s = random_states()
+    args = (s["rho"], s["v"], s["eps"], s["B"], s["alpha"], s["beta"], s["gam"], GAM)
+    F = va.fluxes(*args)
+    T = va.stress_energy(*args)
+    u, *_ = va.four_vectors(*args)
+    g4 = va.metric4_from_adm(s["alpha"], s["beta"], s["gam"])
+    D, S, tau, _ = va.prim_to_cons(*args)
+    al = s["alpha"]
+    Tmix = np.einsum("nim,nmj->nij", T[:, 1:, :], g4[:, :, 1:])   # T^i_j
+    scale = np.abs(T).max(axis=(1, 2))[:, None, None]
+    assert_within(F[:, :, 1:4], al[:, None, None] * Tmix, 1e-11 * scale, "F_S")
+    np.testing.assert_allclose(F[:, :, 0], (al * s["rho"])[:, None] * u[:, 1:], rtol=1e-12,
+                               atol=1e-300)
+    vt = al[:, None] * s["v"] - s["beta"]
+    assert_within(F[:, :, 4], (al ** 2)[:, None] * T[:, 0, 1:] - D[:, None] * vt,
+                  1e-11 * scale[:, :, 0], "F_tau")
+    # induction fluxes are antisymmetric
+    for i in range(3):
+        np.testing.assert_allclose(F[:, i, 5 + i], 0.0, atol=1e-300)
+
+
+@pytest.mark.parametrize("a", [0.0, 0.6])
+def test_sources_3p1_equal_christoffel_form(a):
+    """On the stationary Kerr-Schild metric the 3+1 momentum/energy sources equal the
+    covariant Christoffel form of the paper's source term."""
+    rng = np.random.default_rng(21)
+    n = 100
+    r = rng.uniform(1.5, 20, n)
+    th = rng.uniform(0.3, 2.8, n)
+    M = 1.0
+    alpha, beta, gam = ks.adm(M, a, r, th)
+    X = rng.normal(size=(n, 4, 4))
+    T = X + np.swapaxes(X, 1, 2)
+    h = 1e-30
+    g4 = ks.metric4(M, a, r, th)
+    dg4 = np.zeros((n, 4, 4, 4))
+    dg4[:, 1] = np.imag(ks.metric4(M, a, r + 1j * h, th + 0j)) / h
+    dg4[:, 2] = np.imag(ks.metric4(M, a, r + 0j, th + 1j * h)) / h
+
+    def cs(fun):
+        dr = np.imag(fun(r + 1j * h, th + 0j)) / h
+        dt = np.imag(fun(r + 0j, th + 1j * h)) / h
+        return np.stack([dr, dt, np.zeros_like(dr)], axis=1)
+    dalpha = cs(lambda rr, tt: ks.adm(M, a, rr, tt)[0])
+    dbeta = cs(lambda rr, tt: ks.adm(M, a, rr, tt)[1])
+    dgam = cs(lambda rr, tt: ks.adm(M, a, rr, tt)[2])
+    Kij = ks.extrinsic_curvature(M, a, r, th)
+    S_S, S_tau = va.sources_3p1(T, alpha, beta, gam, dalpha, dbeta, dgam, Kij)
+    S_ref, S_tau_ref = va.sources_christoffel(T, g4, dg4)
+    np.testing.assert_allclose(S_S, S_ref, atol=1e-11 * np.abs(S_ref).max())
+    np.testing.assert_allclose(S_tau, S_tau_ref, atol=1e-11 * np.abs(S_tau_ref).max())
