@@ -1,0 +1,285 @@
+"""Benchmark: coupled BSSN-Valencia RHS point-updates/s on the GB300.
+
+Workload (one bench step): the 8-element Kerr-Schild torus instance, spin a = 0.9,
+r in [1.5, 100], N_r = 24, N_theta = 32, N_phi = 64 (393,216 nodes, 32 evolved
+variables), 100 SSP-RK3 time steps at CFL 0.3 recorded in one CUDA graph, FP64.
+value = nodes x RHS evaluations / second (3 RHS per step), summed over ranks.
+
+--impl reference times the FP64 numpy oracle (the project's CPU reference) on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled RHS point-updates/s (FP64)"
+UNIT = "point-updates/s"
+NSTEPS_PER_BENCH_STEP = 100
+RHS_PER_STEP = 3
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": smax or None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds_hint=True):
+    """Oracle (numpy FP64) on the host: one RHS evaluation of radial elements 0-2 of the
+    same 8-element grid (same N and element bounds)."""
+    import numpy as np
+    from oracle import solver as so
+    from workloads import config
+    cfg = config("c2")
+    E = 3
+    rb = cfg.r_min * (cfg.r_max / cfg.r_min) ** (E / cfg.n_elem)
+    sub = config("c2", n_elem=E, r_max=rb)
+    g, p, U = so.workload_state(sub)
+    t0 = time.perf_counter()
+    so.rhs(U, g, p)
+    dt = time.perf_counter() - t0
+    npts = U[0].size
+    threads = os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS")
+    return {"value": npts / dt, "unit": UNIT, "cores": int(threads) if threads else 1,
+            "kind": "oracle",
+            "sample": f"one RHS evaluation of radial elements 0-{E - 1} of the 8-element "
+                      f"grid ({npts} nodes, {dt:.1f} s); numpy, single-threaded elementwise"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    from oracle import solver as so
+    from workloads import config
+    cfg = config("c2")
+    E = 1
+    rb = cfg.r_min * (cfg.r_max / cfg.r_min) ** (E / cfg.n_elem)
+    sub = config("c2", n_elem=E, r_max=rb)
+    g, p, U = so.workload_state(sub)
+    npts = U[0].size
+    for _ in range(args.warmup):
+        so.rhs(U, g, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        so.rhs(U, g, p)
+    el = time.perf_counter() - t0
+    val = npts * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Kerr-Schild torus, splitmix64 noise)",
+            "config": {"workload": "c2 sample: radial element 0 of the 8-element a=0.9 "
+                                   "24x32x64 grid, one RHS evaluation per step",
+                       "nodes": npts},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one RHS of element 0 ({npts} nodes) per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    import paper_2508_18221_gb300 as pkg
+    from workloads import config, primitive_profiles
+
+    cfg = config("c2")
+    grid, phys, opts = pkg.make_structs(cfg)
+    stream = torch.cuda.Stream()
+    ctx = pkg.Context(grid, phys, opts, stream.cuda_stream)
+    P = ctx.n_points
+    r, t, ph = ctx.coords()
+    shp = cfg.shape
+    pr = primitive_profiles(cfg, r.reshape(shp), t.reshape(shp), ph.reshape(shp))
+    ctx.init_prims(pr["rho"], pr["p"], pr["vr"], pr["vth"], pr["vph"], pr["A_phi"])
+    U0 = torch.empty(pkg.NV * P, dtype=torch.float64, device="cuda")
+    ctx.get_state(U0, True)
+    dt = ctx.cfl_dt()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one(timed_events=None):
+        with torch.cuda.stream(stream):
+            ctx.set_state(U0, True)
+            flush.fill_(1.0)                      # evict L2 between timed steps
+            if timed_events:
+                timed_events[0].record(stream)
+            ctx.step(dt, NSTEPS_PER_BENCH_STEP)
+            if timed_events:
+                timed_events[1].record(stream)
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    launches_per_step = ctx.launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if dist_on:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            one(evs[k])
+        torch.cuda.synchronize()
+    if dist_on:
+        tdist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist_on:
+        tdist.all_reduce(ms_t, op=tdist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    units = P * RHS_PER_STEP * NSTEPS_PER_BENCH_STEP * args.steps * world
+    value = units / (ms_max * 1e-3)
+
+    # end to end through the C ABI with host buffers (pinned)
+    host_in = torch.empty(pkg.NV * P, dtype=torch.float64).pin_memory()
+    host_out = torch.empty_like(host_in)
+    host_in.copy_(U0.cpu())
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_state(host_in, False)
+        ctx.step(dt, NSTEPS_PER_BENCH_STEP)
+        ctx.get_state(host_out, False)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = P * RHS_PER_STEP * NSTEPS_PER_BENCH_STEP * e2e_steps * world / e2e_s
+
+    # live per-kernel timing (CUDA events on the library's stream)
+    ctx.set_state(U0, True)
+    kt = ctx.kernel_times(reps=5)
+    dom = max((k for k in kt if kt[k][1] > 0), key=lambda k: kt[k][0])
+    peaks = _peaks()
+    fp64_peak = 1.25  # TFLOP/s: GB300 nominal FP64 (ALU roofline)
+    dom_ms, dom_fl = kt[dom]
+    achieved = dom_fl / (dom_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+            "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (ALU bound; of nominal)",
+            "kernel_ms": {k: round(v[0], 5) for k, v in kt.items()}}
+    stats = ctx.diag()
+    if rank == 0:
+        cb = None
+        if not args.no_cpu_baseline:
+            try:
+                cb = cpu_baseline()
+            except Exception as exc:  # noqa: BLE001
+                cb = {"error": str(exc)}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded Kerr-Schild torus, splitmix64 noise)",
+                "config": {"workload": "c2: a=0.9, 8 radial elements r in [1.5,100], "
+                                       "N_r=24 N_theta=32 N_phi=64, 100 SSP-RK3 steps "
+                                       "(CFL 0.3) per bench step in one CUDA graph",
+                           "nodes": P, "rk_steps_per_bench_step": NSTEPS_PER_BENCH_STEP,
+                           "l2": "flushed (256 MB write) before every timed step",
+                           "dt": dt, "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cb,
+                "e2e": {"value": e2e_val, "unit": UNIT,
+                        "h2d_bytes_per_step": pkg.NV * P * 8,
+                        "d2h_bytes_per_step": pkg.NV * P * 8},
+                "gpu_launches": launches_per_step * args.steps,
+                "clocks": clk.summary(),
+                "final_diag": {"mass": stats[0], "c2p_floor_points": stats[3]}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist_on:
+        tdist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

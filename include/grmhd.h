@@ -1,0 +1,195 @@
+/*
+ * grmhd.h - C ABI of the GB300 coupled BSSN-Valencia spectral right-hand side.
+ *
+ * The library evolves the unsplit coupled system of the paper (arXiv 2508.18221):
+ * the Valencia form of ideal GRMHD ("GRMHD Conservative Form": conserved variables,
+ * fluxes, geometric source) together with the BSSN equations, 1+log slicing and the
+ * Gamma-driver shift (Methods: "BSSN Evolution Equations", "Gauge Conditions"), on a
+ * multi-element mapped Chebyshev (r) x Chebyshev (theta) x Fourier (phi) grid around a
+ * Kerr-Schild black hole (Methods: "Grid Discretization", "The Spectral Derivative
+ * Operators"), with the paper's modal filter ("Dealiasing and Spectral Filtering"),
+ * primitive recovery ("The Primitive Variable Recovery") and Runge-Kutta time
+ * integration ("Time Integration", SSP-RK3 by default, the printed RK4 as option).
+ *
+ * Conventions shared by every call
+ *   - Every function returns an int status: GRMHD_OK (0) or a negative error code.
+ *     No call aborts, traps or exits the process; after an error the context stays
+ *     usable and grmhd_last_error() describes the cause.
+ *   - Field arrays use the canonical layout double[nv][E][N_r][N_theta][N_phi] with phi
+ *     fastest and radial nodes ascending inside each element (adjacent elements share
+ *     their interface radius: that node is stored once per element).
+ *   - Variable order (nv = 32): 0-5 gammatilde_{rr,rth,rph,thth,thph,phph}; 6 phi;
+ *     7-12 Atilde_ij (same order); 13 K; 14-16 Gammatilde^i; 17 alpha; 18-20 beta^i;
+ *     21-23 B^i (Gamma-driver); 24 sqrt(gamma) D; 25-27 sqrt(gamma) S_i (covariant);
+ *     28 sqrt(gamma) tau; 29-31 sqrt(gamma) B^i (Eulerian field, contravariant).
+ *   - Primitive layout (7 fields): rho, v^r, v^theta, v^phi (Eulerian, contravariant),
+ *     eps, p, W.
+ *   - A pointer argument is caller-owned; it is read or written only during the call.
+ *     `on_device` = 1 means the pointer is CUDA device memory (stream-ordered on the
+ *     context's stream), 0 means host memory (the call synchronises before returning).
+ *   - All work of a context is issued on the CUDA stream given to grmhd_create
+ *     (NULL = legacy default stream).  One GPU; the device current at create time.
+ */
+#ifndef GRMHD_H
+#define GRMHD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GRMHD_OK = 0,
+    GRMHD_EINVAL = -1,        /* invalid argument (sizes, ranges, NULL pointers)       */
+    GRMHD_ENOMEM = -2,        /* device or host allocation failed                      */
+    GRMHD_ECUDA = -3,         /* a CUDA runtime call failed (message in last_error)    */
+    GRMHD_ENAN = -4,          /* a non-finite value appeared in the evolved state      */
+    GRMHD_ETIMEOUT = -5,      /* a bounded device-side wait gave up                    */
+    GRMHD_EUNSUPPORTED = -6   /* option value not built into this library              */
+};
+
+enum { GRMHD_NV = 32, GRMHD_NPRIM = 7, GRMHD_NDIAG = 8 };
+
+/* Grid (Methods, "Grid Discretization").  Radial elements [r_e, r_{e+1}] with
+ * r_e = r_min (r_max/r_min)^(e/E) (elem_map = 1) or equal widths (elem_map = 0); each
+ * element carries n_r Chebyshev-Gauss-Lobatto nodes under an affine map.  theta uses
+ * n_theta Chebyshev-Gauss nodes on [theta_min, theta_max] (no node on a pole), phi
+ * n_phi uniform nodes 2 pi l / n_phi.  Limits: 1 <= n_elem, 4 <= n_r <= 64,
+ * 4 <= n_theta <= 128, 4 <= n_phi <= 256 and even, 0 < r_min < r_max,
+ * 0 <= theta_min < theta_max <= pi. */
+typedef struct {
+    int n_elem;
+    double r_min, r_max;
+    int elem_map;
+    int n_r, n_theta, n_phi;
+    double theta_min, theta_max;
+} grmhd_grid;
+
+/* Physics: Kerr-Schild mass M and spin a (|a| < M), Gamma-law index (p = (Gamma-1) rho
+ * eps, Methods "Ideal-gas EOS"), floors of rho and eps used by primitive recovery. */
+typedef struct {
+    double M, a, gamma_eos;
+    double rho_atm, eps_atm;
+} grmhd_physics;
+
+/* Options.  precision: 0 = FP64 everywhere.  integrator: 0 SSP-RK3, 1 RK4.
+ * evolve_metric: 1 evolve BSSN + gauge, 0 keep the metric fixed (RHS of variables
+ * 0-23 is zero).  gauge: 0 1+log + Gamma-driver with damping eta, 1 frozen lapse/shift.
+ * filter: bits 0/1/2 filter the Valencia variables in r/theta/phi, bits 3/4/5 the BSSN
+ * variables in r/theta/phi (default 47: all but theta for BSSN); filt_alpha, filt_p are
+ * the exponential-filter constants (paper: 36, 8); dealias23_phi applies the 2/3 rule
+ * in phi.  cfl: Courant factor for dt <= 0.  c2p_maxit, c2p_tol: Newton iteration
+ * limit and relative tolerance of the primitive recovery. */
+typedef struct {
+    int precision;
+    int integrator;
+    int evolve_metric;
+    int gauge;
+    double eta, cfl;
+    int filter;
+    double filt_alpha, filt_p;
+    int dealias23_phi;
+    int c2p_maxit;
+    double c2p_tol;
+} grmhd_opts;
+
+typedef struct grmhd_ctx grmhd_ctx;
+typedef struct grmhd_batch grmhd_batch;
+
+/* Fill the structs with the defaults listed above (M = 1, a = 0.5, Gamma = 4/3,
+ * rho_atm = 1e-12, eps_atm = 1e-10, eta = 2, cfl = 0.3, filter = 47, 36, 8,
+ * dealias on, c2p_maxit = 60, c2p_tol = 1e-15). Any pointer may be NULL. */
+int grmhd_defaults(grmhd_grid* grid, grmhd_physics* phys, grmhd_opts* opts);
+
+/* Create a context: validates the parameters (GRMHD_EINVAL), builds the operator
+ * matrices on the host, allocates every device buffer (GRMHD_ENOMEM), and binds the
+ * CUDA stream `cuda_stream` (a cudaStream_t, or NULL).  *out receives the handle. */
+int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, const grmhd_opts* opts,
+                 void* cuda_stream, grmhd_ctx** out);
+int grmhd_destroy(grmhd_ctx* ctx);
+
+/* Number of nodes E * n_r * n_theta * n_phi. */
+long long grmhd_num_points(const grmhd_ctx* ctx);
+
+/* Node coordinates in canonical point order (3 arrays of num_points doubles: r, theta,
+ * phi).  Any of the pointers may be NULL. Host memory. */
+int grmhd_coords(const grmhd_ctx* ctx, double* r, double* theta, double* phi);
+
+/* Initial data: exact Kerr-Schild slice converted to BSSN variables (phi = ln(det
+ * gamma)/12, gammatilde = e^{-4phi} gamma, K = gamma^ij K_ij, Atilde = e^{-4phi}(K_ij -
+ * gamma_ij K/3), Gammatilde^i = gammatilde^jk Gammatilde^i_jk, Gamma-driver B = 0)
+ * plus matter given by primitives on the nodes: rho, p, v^r, v^theta, v^phi and the
+ * vector potential A_phi (6 arrays of num_points doubles, host memory).  The
+ * densitized field is sqrt(gamma) B^r = d_theta A_phi, sqrt(gamma) B^theta =
+ * -d_r A_phi, B^phi = 0 with the grid's own derivative operators.  Replaces the state
+ * and resets the primitive guess. */
+int grmhd_init_prims(grmhd_ctx* ctx, const double* rho, const double* p, const double* vr,
+                     const double* vth, const double* vph, const double* A_phi);
+
+/* Copy a full canonical state (GRMHD_NV * num_points doubles) in / out. set_state
+ * also resets the primitive guess (the next primitive recovery starts from a bracket). */
+int grmhd_set_state(grmhd_ctx* ctx, const double* state, int on_device);
+int grmhd_get_state(grmhd_ctx* ctx, double* state, int on_device);
+
+/* L(U) of the current state: one right-hand-side evaluation (one Runge-Kutta stage)
+ * without the post-step filter, written to rhs_out (GRMHD_NV * num_points doubles). */
+int grmhd_rhs(grmhd_ctx* ctx, double* rhs_out, int on_device);
+
+/* Primitive recovery of the current state into prim_out (GRMHD_NPRIM * num_points
+ * doubles); *n_failed (may be NULL) receives the number of points where the floor
+ * eps_atm was applied or the recovery did not converge.  Updates the stored guess. */
+int grmhd_con2prim(grmhd_ctx* ctx, double* prim_out, int on_device, long long* n_failed);
+
+/* Advance nsteps time steps of size dt (dt <= 0: dt from the CFL condition of the
+ * current state, computed once per call).  Each step: SSP-RK3 (3 stages) or RK4 (4),
+ * then the post-step filter.  The nsteps loop is captured in a CUDA graph (rebuilt
+ * when nsteps or the dt mode changes).  Returns GRMHD_ENAN if the state is non-finite
+ * afterwards.  *dt_used (may be NULL) receives dt. */
+int grmhd_step(grmhd_ctx* ctx, double dt, int nsteps, double* dt_used);
+
+/* dt of the CFL condition for the current state (Methods, "The Stability and
+ * Complexity"): cfl * min over nodes of min(dr, r dtheta, r sin(theta) dphi) divided
+ * by max over nodes of |beta|_gamma + max(alpha, sqrt(2 alpha)). */
+int grmhd_cfl_dt(grmhd_ctx* ctx, double* dt);
+
+/* Diagnostics (out[GRMHD_NDIAG]): 0 rest mass sum w D~, 1 entropy sum w rho s sqrt(gamma)
+ * with s = ln(p/rho^Gamma)/(Gamma-1) (Methods, "The Entropy Stability and
+ * Convergence", quadrature weights as the cell volume), 2 max |d_i(sqrt(gamma) B^i)|,
+ * 3 floor/failed points of the last recovery, 4 dt of the last step, 5-7 reserved. */
+int grmhd_diag(grmhd_ctx* ctx, double out[GRMHD_NDIAG]);
+
+/* Kernel launches issued by the last grmhd_step / grmhd_rhs call (per step / per call). */
+long long grmhd_launch_count(const grmhd_ctx* ctx);
+
+/* Profiling: time each kernel class of one right-hand-side evaluation and of the filter
+ * on the current state, `reps` launches each, with CUDA events on the context's stream.
+ * ms_out[0..n-1] (n <= GRMHD_NKT) receives the mean milliseconds per launch of:
+ * 0 prep (metric + primitive recovery + fluxes), 1-3 first-derivative contractions
+ * r/theta/phi, 4 interface mean of d_r, 5-7 second-derivative contractions r/theta/phi,
+ * 8 interface mean of d_rr, 9 rhs (BSSN + Valencia + penalty + RK), 10-12 filter
+ * contractions r/theta/phi.  flops_out (may be NULL) receives the algorithmic FP64
+ * flops of one launch of each class for the contractions (2 N per output node) and 0
+ * for the others.  The state is left unchanged. */
+enum { GRMHD_NKT = 13 };
+int grmhd_kernel_times(grmhd_ctx* ctx, int reps, double* ms_out, double* flops_out, int n);
+
+/* Independent instances advanced together (one context per instance, all sharing one
+ * stream; the step of every instance is captured into one CUDA graph).  Instances may
+ * differ in every grid, physics and option field. */
+int grmhd_batch_create(int n, const grmhd_grid* grids, const grmhd_physics* phys,
+                       const grmhd_opts* opts, void* cuda_stream, grmhd_batch** out);
+grmhd_ctx* grmhd_batch_instance(grmhd_batch* b, int i);
+int grmhd_batch_step(grmhd_batch* b, const double* dt, int nsteps);
+int grmhd_batch_destroy(grmhd_batch* b);
+
+/* Test hook: apply the first derivative along direction dir (0 r, 1 theta, 2 phi) to
+ * `nfields` canonical fields (nfields * num_points doubles) with the library's
+ * operators (radial: per element, one-sided at element ends).  Device pointers. */
+int grmhd_debug_deriv(grmhd_ctx* ctx, const double* in, double* out, int nfields, int dir);
+
+const char* grmhd_strerror(int status);
+const char* grmhd_last_error(const grmhd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRMHD_H */

@@ -1,0 +1,781 @@
+// C ABI: context management, the per-stage pipeline and the graph-captured RK driver.
+//
+// One right-hand-side evaluation (one Runge-Kutta stage) is 10 launches on the
+// context's stream:
+//   prep  | deriv r, theta, phi (first derivatives of 21 BSSN fields + flux divergence)
+//   | interface mean of d_r | deriv r, theta, phi (second derivatives of 11 fields)
+//   | interface mean of d_rr | rhs (+ RK stage combination)
+// A time step adds the filter (3 directional contractions + interface mean of the BSSN
+// copies).  grmhd_step records nsteps steps into one CUDA graph.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "grmhd_internal.h"
+#include "host_ops.h"
+
+using namespace gk;
+
+struct grmhd_ctx {
+    grmhd_grid grid;
+    grmhd_physics phys;
+    grmhd_opts opts;
+    Dims d;
+    PhysParams pp;
+    cudaStream_t stream;
+    bool own_stream;
+    // device buffers
+    double* U[3];            // U[0] = state, U[1], U[2] = stage buffers
+    double* acc;             // RK4 accumulator (allocated for integrator = 1)
+    double* prim;
+    double* flux;
+    double* tmn;
+    double* lam;
+    double* d1;
+    double* d2;
+    double* divF;
+    double* scratch;         // NV * P
+    double* Dr;              // Nr x Nr reference CGL matrix on [-1, 1]
+    double* Dt;              // Nt x Nt Gauss matrix scaled to [theta_min, theta_max]
+    double* Dp;              // circulant row
+    double* Fr;
+    double* Ft;
+    double* Fp;
+    double* r_scale;         // E
+    double* wq;              // P quadrature weights
+    double* hmin;            // 1
+    double* dt;              // 1
+    double* diag;            // 8
+    unsigned long long* nfail;
+    unsigned long long* lam_bits;
+    int* nan_flag;
+    DerivJob* jobs;          // all job lists
+    int job_first[3][3];     // [buffer][dir] offset of the first-derivative jobs
+    int job_first_n;
+    int job_second[3];       // [dir] offset of the second-derivative jobs
+    int job_second_n[3];
+    int job_filter[3][3][2]; // [buffer][dir][group] offset (8 or 24 jobs)
+    int job_dbg;
+    // host copies
+    std::vector<double> r_nodes, th_nodes, ph_nodes, rscale_h;
+    // graph
+    cudaGraphExec_t gexec;
+    int g_nsteps;
+    int g_auto_dt;
+    long long launches_per_call;
+    long long launches_tmp;
+    char err[512];
+};
+
+struct grmhd_batch {
+    int n;
+    grmhd_ctx** inst;
+    cudaStream_t stream;
+    bool own_stream;
+    cudaGraphExec_t gexec;
+    int g_nsteps;
+};
+
+static int set_err(grmhd_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return set_err(c, GRMHD_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" int grmhd_defaults(grmhd_grid* g, grmhd_physics* ph, grmhd_opts* o) {
+    if (g) {
+        g->n_elem = 2; g->r_min = 1.8; g->r_max = 20.0; g->elem_map = 1;
+        g->n_r = 12; g->n_theta = 12; g->n_phi = 16;
+        g->theta_min = M_PI / 8; g->theta_max = 7 * M_PI / 8;
+    }
+    if (ph) { ph->M = 1.0; ph->a = 0.5; ph->gamma_eos = 4.0 / 3.0; ph->rho_atm = 1e-12; ph->eps_atm = 1e-10; }
+    if (o) {
+        o->precision = 0; o->integrator = 0; o->evolve_metric = 1; o->gauge = 0;
+        o->eta = 2.0; o->cfl = 0.3; o->filter = 47; o->filt_alpha = 36.0; o->filt_p = 8.0;
+        o->dealias23_phi = 1; o->c2p_maxit = 60; o->c2p_tol = 1e-15;
+    }
+    return GRMHD_OK;
+}
+
+static int validate(const grmhd_grid* g, const grmhd_physics* ph, const grmhd_opts* o, char* msg) {
+    if (!g || !ph || !o) { strcpy(msg, "NULL parameter struct"); return GRMHD_EINVAL; }
+    if (g->n_elem < 1 || g->n_elem > 4096) { strcpy(msg, "n_elem out of range"); return GRMHD_EINVAL; }
+    if (g->n_r < 4 || g->n_r > 64) { strcpy(msg, "n_r must be in [4, 64]"); return GRMHD_EINVAL; }
+    if (g->n_theta < 4 || g->n_theta > 128) { strcpy(msg, "n_theta must be in [4, 128]"); return GRMHD_EINVAL; }
+    if (g->n_phi < 4 || g->n_phi > 256 || (g->n_phi % 2)) { strcpy(msg, "n_phi must be even in [4, 256]"); return GRMHD_EINVAL; }
+    if (!(g->r_min > 0.0) || !(g->r_max > g->r_min)) { strcpy(msg, "need 0 < r_min < r_max"); return GRMHD_EINVAL; }
+    if (!(g->theta_min >= 0.0) || !(g->theta_max > g->theta_min) || !(g->theta_max <= M_PI + 1e-12)) {
+        strcpy(msg, "need 0 <= theta_min < theta_max <= pi"); return GRMHD_EINVAL;
+    }
+    if (g->elem_map != 0 && g->elem_map != 1) { strcpy(msg, "elem_map must be 0 or 1"); return GRMHD_EINVAL; }
+    if (!(ph->M > 0.0) || !(std::fabs(ph->a) < ph->M)) { strcpy(msg, "need M > 0 and |a| < M"); return GRMHD_EINVAL; }
+    if (!(ph->gamma_eos > 1.0)) { strcpy(msg, "gamma_eos must exceed 1"); return GRMHD_EINVAL; }
+    if (!(ph->rho_atm > 0.0) || !(ph->eps_atm >= 0.0)) { strcpy(msg, "bad floors"); return GRMHD_EINVAL; }
+    if (o->precision != 0) { strcpy(msg, "precision mode not built"); return GRMHD_EUNSUPPORTED; }
+    if (o->integrator != 0 && o->integrator != 1) { strcpy(msg, "integrator must be 0 or 1"); return GRMHD_EINVAL; }
+    if (o->gauge != 0 && o->gauge != 1) { strcpy(msg, "gauge must be 0 or 1"); return GRMHD_EINVAL; }
+    if (!(o->cfl > 0.0) || o->c2p_maxit < 1 || !(o->c2p_tol > 0.0)) { strcpy(msg, "bad cfl / c2p options"); return GRMHD_EINVAL; }
+    if (o->filter < 0 || o->filter > 63) { strcpy(msg, "filter mask must be in [0, 63]"); return GRMHD_EINVAL; }
+    return GRMHD_OK;
+}
+
+static void free_ctx(grmhd_ctx* c) {
+    if (!c) return;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    double** bufs[] = {&c->U[0], &c->U[1], &c->U[2], &c->acc, &c->prim, &c->flux, &c->tmn, &c->lam,
+                       &c->d1, &c->d2, &c->divF, &c->scratch, &c->Dr, &c->Dt, &c->Dp, &c->Fr,
+                       &c->Ft, &c->Fp, &c->r_scale, &c->wq, &c->hmin, &c->dt, &c->diag};
+    for (double** b : bufs)
+        if (*b) cudaFree(*b);
+    if (c->nfail) cudaFree(c->nfail);
+    if (c->lam_bits) cudaFree(c->lam_bits);
+    if (c->nan_flag) cudaFree(c->nan_flag);
+    if (c->jobs) cudaFree(c->jobs);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+template <class T>
+static cudaError_t dalloc(T** p, size_t n) {
+    return cudaMalloc((void**)p, n * sizeof(T) + 16);
+}
+
+static cudaError_t upload(double* dst, const std::vector<double>& v, cudaStream_t s) {
+    return cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+}
+
+extern "C" int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, const grmhd_opts* opts,
+                            void* cuda_stream, grmhd_ctx** out) {
+    if (!out) return GRMHD_EINVAL;
+    *out = nullptr;
+    char msg[256] = {0};
+    int st = validate(grid, phys, opts, msg);
+    if (st != GRMHD_OK) return st;
+    // value-initialisation zeroes every plain member and constructs the vectors
+    grmhd_ctx* c = new (std::nothrow) grmhd_ctx();
+    if (!c) return GRMHD_ENOMEM;
+    c->grid = *grid;
+    c->phys = *phys;
+    c->opts = *opts;
+    const int E = grid->n_elem, Nr = grid->n_r, Nt = grid->n_theta, Np = grid->n_phi;
+    c->d.E = E; c->d.Nr = Nr; c->d.Nt = Nt; c->d.Np = Np;
+    c->d.NtNp = (long long)Nt * Np;
+    c->d.elem = c->d.NtNp * Nr;
+    c->d.P = c->d.elem * E;
+    const long long P = c->d.P;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        // capture needs a non-legacy stream; a blocking stream stays ordered with the
+        // legacy default stream the caller named
+        cudaError_t e = cudaStreamCreate(&c->stream);
+        if (e != cudaSuccess) { free_ctx(c); return GRMHD_ECUDA; }
+        c->own_stream = true;
+    }
+    // physics parameters
+    c->pp.M = phys->M; c->pp.a = phys->a; c->pp.gam = phys->gamma_eos;
+    c->pp.rho_atm = phys->rho_atm; c->pp.eps_atm = phys->eps_atm;
+    c->pp.eta = opts->eta; c->pp.gauge = opts->gauge; c->pp.evolve_metric = opts->evolve_metric;
+    c->pp.c2p_maxit = opts->c2p_maxit; c->pp.c2p_tol = opts->c2p_tol;
+    std::vector<double> wcgl = quad_weights(Nr, true);
+    c->pp.w_end = wcgl[0];
+
+    // grid
+    std::vector<double> bounds(E + 1);
+    for (int e = 0; e <= E; e++)
+        bounds[e] = grid->elem_map == 1 ? grid->r_min * std::pow(grid->r_max / grid->r_min, (double)e / E)
+                                        : grid->r_min + (grid->r_max - grid->r_min) * e / E;
+    bounds[0] = grid->r_min;
+    bounds[E] = grid->r_max;
+    std::vector<double> xr = cgl_nodes(Nr), xt = gauss_nodes(Nt);
+    c->r_nodes.resize((size_t)E * Nr);
+    c->rscale_h.resize(E);
+    for (int e = 0; e < E; e++) {
+        double a = bounds[e], b = bounds[e + 1];
+        c->rscale_h[e] = 2.0 / (b - a);
+        for (int i = 0; i < Nr; i++) c->r_nodes[(size_t)e * Nr + i] = 0.5 * (a + b) + 0.5 * (b - a) * xr[i];
+    }
+    double tscale = 2.0 / (grid->theta_max - grid->theta_min);
+    c->th_nodes.resize(Nt);
+    for (int k = 0; k < Nt; k++)
+        c->th_nodes[k] = grid->theta_min + 0.5 * (grid->theta_max - grid->theta_min) * (1.0 + xt[k]);
+    c->ph_nodes.resize(Np);
+    for (int l = 0; l < Np; l++) c->ph_nodes[l] = 2.0 * M_PI * l / Np;
+
+    std::vector<double> Dr = cheb_lobatto_D(Nr), Dt = cheb_gauss_D(Nt), Dp = fourier_D_row(Np);
+    for (double& v : Dt) v *= tscale;
+    std::vector<double> Fr = cheb_filter_matrix(Nr, true, opts->filt_alpha, opts->filt_p);
+    std::vector<double> Ft = cheb_filter_matrix(Nt, false, opts->filt_alpha, opts->filt_p);
+    std::vector<double> Fp = fourier_filter_row(Np, opts->filt_alpha, opts->filt_p, opts->dealias23_phi != 0);
+    // quadrature weights and the CFL spacing
+    std::vector<double> wt = quad_weights(Nt, false);
+    std::vector<double> wq((size_t)P);
+    double hmin = 1e300;
+    for (int e = 0; e < E; e++)
+        for (int i = 0; i < Nr; i++) {
+            const double* rn = &c->r_nodes[(size_t)e * Nr];
+            double dr = i == 0 ? rn[1] - rn[0] : (i == Nr - 1 ? rn[i] - rn[i - 1] : std::fmin(rn[i] - rn[i - 1], rn[i + 1] - rn[i]));
+            for (int k = 0; k < Nt; k++) {
+                const double* tn = c->th_nodes.data();
+                double dth = k == 0 ? tn[1] - tn[0] : (k == Nt - 1 ? tn[k] - tn[k - 1] : std::fmin(tn[k] - tn[k - 1], tn[k + 1] - tn[k]));
+                double r = rn[i];
+                double h = std::fmin(std::fmin(dr, r * dth), r * std::sin(tn[k]) * (2.0 * M_PI / Np));
+                hmin = std::fmin(hmin, h);
+                for (int l = 0; l < Np; l++)
+                    wq[(((size_t)e * Nr + i) * Nt + k) * Np + l] =
+                        wcgl[i] / c->rscale_h[e] * wt[k] / tscale * (2.0 * M_PI / Np);
+            }
+        }
+
+    // device memory
+    cudaError_t ce = cudaSuccess;
+#define AL(ptr, n) if (ce == cudaSuccess) ce = dalloc(&(ptr), (size_t)(n))
+    for (int b = 0; b < 3; b++) AL(c->U[b], NV * P);
+    if (opts->integrator == 1) AL(c->acc, NV * P);
+    AL(c->prim, N_PRIM * P);
+    AL(c->flux, N_FLUX * P);
+    AL(c->tmn, N_TMN * P);
+    AL(c->lam, P);
+    AL(c->d1, N_D1 * 3 * P);
+    AL(c->d2, N_D2 * 6 * P);
+    AL(c->divF, 8 * P);
+    AL(c->scratch, NV * P);
+    AL(c->Dr, Nr * Nr); AL(c->Dt, Nt * Nt); AL(c->Dp, Np);
+    AL(c->Fr, Nr * Nr); AL(c->Ft, Nt * Nt); AL(c->Fp, Np);
+    AL(c->r_scale, E); AL(c->wq, P); AL(c->hmin, 1); AL(c->dt, 1); AL(c->diag, 8);
+    AL(c->nfail, 1); AL(c->lam_bits, 1); AL(c->nan_flag, 1);
+#undef AL
+    if (ce != cudaSuccess) {
+        free_ctx(c);
+        return ce == cudaErrorMemoryAllocation ? GRMHD_ENOMEM : GRMHD_ECUDA;
+    }
+    // job lists
+    std::vector<DerivJob> jobs;
+    auto add = [&](const double* s, double* dd, int acc) { DerivJob j; j.src = s; j.dst = dd; j.accumulate = acc; j.pad = 0; jobs.push_back(j); };
+    for (int b = 0; b < 3; b++)
+        for (int dir = 0; dir < 3; dir++) {
+            c->job_first[b][dir] = (int)jobs.size();
+            for (int f = 0; f < N_D1; f++) add(c->U[b] + (long long)f * P, c->d1 + ((long long)f * 3 + dir) * P, 0);
+            for (int v = 0; v < 8; v++) add(c->flux + ((long long)dir * 8 + v) * P, c->divF + (long long)v * P, dir > 0);
+        }
+    c->job_first_n = N_D1 + 8;
+    const int vars2[N_D2] = {0, 1, 2, 3, 4, 5, 6, 17, 18, 19, 20};
+    // second derivatives: r: rr; theta: r-theta, theta-theta; phi: r-phi, theta-phi, phi-phi
+    c->job_second[0] = (int)jobs.size();
+    for (int s = 0; s < N_D2; s++) add(c->d1 + ((long long)vars2[s] * 3 + 0) * P, c->d2 + ((long long)s * 6 + 0) * P, 0);
+    c->job_second_n[0] = N_D2;
+    c->job_second[1] = (int)jobs.size();
+    for (int s = 0; s < N_D2; s++) {
+        add(c->d1 + ((long long)vars2[s] * 3 + 0) * P, c->d2 + ((long long)s * 6 + 1) * P, 0);
+        add(c->d1 + ((long long)vars2[s] * 3 + 1) * P, c->d2 + ((long long)s * 6 + 3) * P, 0);
+    }
+    c->job_second_n[1] = 2 * N_D2;
+    c->job_second[2] = (int)jobs.size();
+    for (int s = 0; s < N_D2; s++) {
+        add(c->d1 + ((long long)vars2[s] * 3 + 0) * P, c->d2 + ((long long)s * 6 + 2) * P, 0);
+        add(c->d1 + ((long long)vars2[s] * 3 + 1) * P, c->d2 + ((long long)s * 6 + 4) * P, 0);
+        add(c->d1 + ((long long)vars2[s] * 3 + 2) * P, c->d2 + ((long long)s * 6 + 5) * P, 0);
+    }
+    c->job_second_n[2] = 3 * N_D2;
+    // filter chains: r: U[b] -> scratch; theta: scratch -> U[b]; phi: U[b] -> U[0]
+    for (int b = 0; b < 3; b++)
+        for (int dir = 0; dir < 3; dir++)
+            for (int grp = 0; grp < 2; grp++) {
+                c->job_filter[b][dir][grp] = (int)jobs.size();
+                const double* src = dir == 0 ? c->U[b] : (dir == 1 ? c->scratch : c->U[b]);
+                double* dst = dir == 0 ? c->scratch : (dir == 1 ? c->U[b] : c->U[0]);
+                int v0 = grp == 0 ? V_D : 0, nv = grp == 0 ? 8 : N_BSSN;
+                for (int v = v0; v < v0 + nv; v++) add(src + (long long)v * P, dst + (long long)v * P, 0);
+            }
+    c->job_dbg = (int)jobs.size();
+    for (int k = 0; k < 64; k++) add(nullptr, nullptr, 0);
+    if (dalloc(&c->jobs, jobs.size()) != cudaSuccess) { free_ctx(c); return GRMHD_ENOMEM; }
+    cudaStream_t s = c->stream;
+    if (cudaMemcpyAsync(c->jobs, jobs.data(), jobs.size() * sizeof(DerivJob), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        upload(c->Dr, Dr, s) != cudaSuccess || upload(c->Dt, Dt, s) != cudaSuccess ||
+        upload(c->Dp, Dp, s) != cudaSuccess || upload(c->Fr, Fr, s) != cudaSuccess ||
+        upload(c->Ft, Ft, s) != cudaSuccess || upload(c->Fp, Fp, s) != cudaSuccess ||
+        upload(c->r_scale, c->rscale_h, s) != cudaSuccess || upload(c->wq, wq, s) != cudaSuccess ||
+        cudaMemcpyAsync(c->hmin, &hmin, sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(c->prim, 0, sizeof(double) * N_PRIM * P, s) != cudaSuccess ||
+        cudaMemsetAsync(c->U[0], 0, sizeof(double) * NV * P, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        free_ctx(c);
+        return GRMHD_ECUDA;
+    }
+    *out = c;
+    return GRMHD_OK;
+}
+
+extern "C" int grmhd_destroy(grmhd_ctx* c) {
+    if (!c) return GRMHD_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+    return GRMHD_OK;
+}
+
+extern "C" long long grmhd_num_points(const grmhd_ctx* c) { return c ? c->d.P : -1; }
+
+extern "C" int grmhd_coords(const grmhd_ctx* c, double* r, double* th, double* ph) {
+    if (!c) return GRMHD_EINVAL;
+    const Dims& d = c->d;
+    for (int e = 0; e < d.E; e++)
+        for (int i = 0; i < d.Nr; i++)
+            for (int k = 0; k < d.Nt; k++)
+                for (int l = 0; l < d.Np; l++) {
+                    size_t p = (((size_t)e * d.Nr + i) * d.Nt + k) * d.Np + l;
+                    if (r) r[p] = c->r_nodes[(size_t)e * d.Nr + i];
+                    if (th) th[p] = c->th_nodes[k];
+                    if (ph) ph[p] = c->ph_nodes[l];
+                }
+    return GRMHD_OK;
+}
+
+// ------------------------------------------------------------------ pipeline
+static int enqueue_first_derivs(grmhd_ctx* c, int b) {
+    for (int dir = 0; dir < 3; dir++) {
+        const double* M = dir == 0 ? c->Dr : (dir == 1 ? c->Dt : c->Dp);
+        CK(launch_deriv(dir, c->d, c->jobs + c->job_first[b][dir], c->job_first_n, M, c->r_scale, c->stream));
+        c->launches_tmp++;
+    }
+    CK(launch_iface_avg(c->d, c->d1, 3 * c->d.P, N_D1, c->stream));
+    c->launches_tmp++;
+    return GRMHD_OK;
+}
+
+static int enqueue_second_derivs(grmhd_ctx* c) {
+    for (int dir = 0; dir < 3; dir++) {
+        const double* M = dir == 0 ? c->Dr : (dir == 1 ? c->Dt : c->Dp);
+        CK(launch_deriv(dir, c->d, c->jobs + c->job_second[dir], c->job_second_n[dir], M, c->r_scale, c->stream));
+        c->launches_tmp++;
+    }
+    CK(launch_iface_avg(c->d, c->d2, 6 * c->d.P, N_D2, c->stream));
+    c->launches_tmp++;
+    return GRMHD_OK;
+}
+
+// one RHS evaluation on state buffer b (Us); output per RKCoef
+static int enqueue_stage(grmhd_ctx* c, int b, RKCoef co, double* out) {
+    CK(launch_prep(c->d, c->pp, c->U[b], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream));
+    c->launches_tmp++;
+    int st = enqueue_first_derivs(c, b);
+    if (st) return st;
+    if (c->opts.evolve_metric) {
+        st = enqueue_second_derivs(c);
+        if (st) return st;
+    }
+    CK(launch_rhs(c->d, c->pp, c->U[0], c->U[b], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
+                  c->divF, c->r_scale, c->dt, co, out, c->acc, c->stream));
+    c->launches_tmp++;
+    return GRMHD_OK;
+}
+
+// post-step filter from buffer b into U[0]
+static int enqueue_filter(grmhd_ctx* c, int b) {
+    const long long P = c->d.P;
+    const int m = c->opts.filter;
+    const double* mats[3] = {c->Fr, c->Ft, c->Fp};
+    for (int dir = 0; dir < 3; dir++) {
+        const double* src = dir == 0 ? c->U[b] : (dir == 1 ? c->scratch : c->U[b]);
+        double* dst = dir == 0 ? c->scratch : (dir == 1 ? c->U[b] : c->U[0]);
+        for (int grp = 0; grp < 2; grp++) {
+            int bit = (grp == 0 ? 1 : 8) << dir;
+            int v0 = grp == 0 ? V_D : 0, nv = grp == 0 ? 8 : N_BSSN;
+            if (m & bit) {
+                CK(launch_deriv(dir, c->d, c->jobs + c->job_filter[b][dir][grp], nv, mats[dir], nullptr, c->stream));
+                c->launches_tmp++;
+            } else if (src != dst) {
+                CK(cudaMemcpyAsync(dst + v0 * P, src + v0 * P, sizeof(double) * nv * P, cudaMemcpyDeviceToDevice, c->stream));
+            }
+        }
+    }
+    CK(launch_iface_avg(c->d, c->U[0], P, N_BSSN, c->stream));
+    c->launches_tmp++;
+    return GRMHD_OK;
+}
+
+static int enqueue_step(grmhd_ctx* c) {
+    int st;
+    int last;
+    if (c->opts.integrator == 0) {
+        RKCoef s1 = {0.0, 1.0, 0.0, 0.0, 0}, s2 = {0.75, 0.25, 0.0, 0.0, 0}, s3 = {1.0 / 3.0, 2.0 / 3.0, 0.0, 0.0, 0};
+        if ((st = enqueue_stage(c, 0, s1, c->U[1]))) return st;
+        if ((st = enqueue_stage(c, 1, s2, c->U[2]))) return st;
+        if ((st = enqueue_stage(c, 2, s3, c->U[1]))) return st;
+        last = 1;
+    } else {
+        RKCoef k1 = {0, 0, 0.5, 1.0 / 6.0, 1}, k2 = {0, 0, 0.5, 1.0 / 3.0, 2}, k3 = {0, 0, 1.0, 1.0 / 3.0, 2},
+               k4 = {0, 0, 0.0, 1.0 / 6.0, 3};
+        if ((st = enqueue_stage(c, 0, k1, c->U[1]))) return st;
+        if ((st = enqueue_stage(c, 1, k2, c->U[2]))) return st;
+        if ((st = enqueue_stage(c, 2, k3, c->U[1]))) return st;
+        if ((st = enqueue_stage(c, 1, k4, c->U[2]))) return st;
+        last = 2;
+    }
+    if (c->opts.filter) return enqueue_filter(c, last);
+    CK(cudaMemcpyAsync(c->U[0], c->U[last], sizeof(double) * NV * c->d.P, cudaMemcpyDeviceToDevice, c->stream));
+    return GRMHD_OK;
+}
+
+// ------------------------------------------------------------------ public calls
+static int copy_in(grmhd_ctx* c, double* dst, const double* src, size_t n, int on_device) {
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    return GRMHD_OK;
+}
+static int copy_out(grmhd_ctx* c, double* dst, const double* src, size_t n, int on_device) {
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    return GRMHD_OK;
+}
+
+extern "C" int grmhd_set_state(grmhd_ctx* c, const double* state, int on_device) {
+    if (!c || !state) return GRMHD_EINVAL;
+    CK(cudaMemsetAsync(c->prim, 0, sizeof(double) * N_PRIM * c->d.P, c->stream));
+    return copy_in(c, c->U[0], state, (size_t)NV * c->d.P, on_device);
+}
+
+extern "C" int grmhd_get_state(grmhd_ctx* c, double* state, int on_device) {
+    if (!c || !state) return GRMHD_EINVAL;
+    return copy_out(c, state, c->U[0], (size_t)NV * c->d.P, on_device);
+}
+
+extern "C" int grmhd_init_prims(grmhd_ctx* c, const double* rho, const double* p, const double* vr,
+                                const double* vth, const double* vph, const double* A_phi) {
+    if (!c || !rho || !p || !vr || !vth || !vph || !A_phi) return GRMHD_EINVAL;
+    const Dims& d = c->d;
+    const long long P = d.P;
+    std::vector<double> U((size_t)NV * P, 0.0);
+    double bssn[24];
+    // Kerr-Schild BSSN data depends on (r, theta) only
+    for (int e = 0; e < d.E; e++)
+        for (int i = 0; i < d.Nr; i++)
+            for (int k = 0; k < d.Nt; k++) {
+                ks_bssn_point(c->phys.M, c->phys.a, c->r_nodes[(size_t)e * d.Nr + i], c->th_nodes[k], bssn);
+                for (int l = 0; l < d.Np; l++) {
+                    size_t pt = (((size_t)e * d.Nr + i) * d.Nt + k) * d.Np + l;
+                    for (int v = 0; v < 24; v++) U[(size_t)v * P + pt] = bssn[v];
+                }
+            }
+    // densitized field from A_phi with the grid operators
+    std::vector<double> Dr = cheb_lobatto_D(d.Nr), Dt = cheb_gauss_D(d.Nt);
+    double tscale = 2.0 / (c->grid.theta_max - c->grid.theta_min);
+    for (int e = 0; e < d.E; e++)
+        for (int i = 0; i < d.Nr; i++)
+            for (int k = 0; k < d.Nt; k++)
+                for (int l = 0; l < d.Np; l++) {
+                    size_t pt = (((size_t)e * d.Nr + i) * d.Nt + k) * d.Np + l;
+                    double dth = 0.0, drr = 0.0;
+                    for (int j = 0; j < d.Nt; j++)
+                        dth += Dt[(size_t)k * d.Nt + j] * A_phi[(((size_t)e * d.Nr + i) * d.Nt + j) * d.Np + l];
+                    for (int j = 0; j < d.Nr; j++)
+                        drr += Dr[(size_t)i * d.Nr + j] * A_phi[(((size_t)e * d.Nr + j) * d.Nt + k) * d.Np + l];
+                    U[(size_t)V_B * P + pt] = dth * tscale;
+                    U[(size_t)(V_B + 1) * P + pt] = -drr * c->rscale_h[e];
+                    U[(size_t)(V_B + 2) * P + pt] = 0.0;
+                }
+    for (long long pt = 0; pt < P; pt++) {
+        double b[24];
+        for (int v = 0; v < 24; v++) b[v] = U[(size_t)v * P + pt];
+        double g[3][3], sqg;
+        metric_from_bssn_point(b, g, &sqg);
+        double B_u[3] = {U[(size_t)V_B * P + pt] / sqg, U[(size_t)(V_B + 1) * P + pt] / sqg, U[(size_t)(V_B + 2) * P + pt] / sqg};
+        double v_u[3] = {vr[pt], vth[pt], vph[pt]};
+        double D, S[3], tau;
+        prim_to_cons_point(rho[pt], p[pt], v_u, B_u, g, c->phys.gamma_eos, &D, S, &tau);
+        U[(size_t)V_D * P + pt] = sqg * D;
+        for (int j = 0; j < 3; j++) U[(size_t)(V_S + j) * P + pt] = sqg * S[j];
+        U[(size_t)V_TAU * P + pt] = sqg * tau;
+    }
+    return grmhd_set_state(c, U.data(), 0);
+}
+
+extern "C" int grmhd_rhs(grmhd_ctx* c, double* out, int on_device) {
+    if (!c || !out) return GRMHD_EINVAL;
+    c->launches_tmp = 0;
+    CK(cudaMemsetAsync(c->nfail, 0, sizeof(unsigned long long), c->stream));
+    RKCoef co = {0, 0, 0, 0, -1};
+    double* dst = on_device ? out : c->scratch;
+    int st = enqueue_stage(c, 0, co, dst);
+    if (st) return st;
+    c->launches_per_call = c->launches_tmp;
+    if (!on_device) return copy_out(c, out, c->scratch, (size_t)NV * c->d.P, 0);
+    return GRMHD_OK;
+}
+
+extern "C" int grmhd_con2prim(grmhd_ctx* c, double* prim_out, int on_device, long long* n_failed) {
+    if (!c) return GRMHD_EINVAL;
+    CK(cudaMemsetAsync(c->nfail, 0, sizeof(unsigned long long), c->stream));
+    CK(launch_prep(c->d, c->pp, c->U[0], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream));
+    if (prim_out) {
+        int st = copy_out(c, prim_out, c->prim, (size_t)N_PRIM * c->d.P, on_device);
+        if (st) return st;
+    }
+    if (n_failed) {
+        unsigned long long nf = 0;
+        CK(cudaMemcpyAsync(&nf, c->nfail, sizeof(nf), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        *n_failed = (long long)nf;
+    }
+    return GRMHD_OK;
+}
+
+extern "C" int grmhd_cfl_dt(grmhd_ctx* c, double* dt) {
+    if (!c || !dt) return GRMHD_EINVAL;
+    CK(launch_cfl(c->d, c->U[0], c->hmin, c->opts.cfl, c->dt, (unsigned int*)c->lam_bits, c->stream));
+    CK(cudaMemcpyAsync(dt, c->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return GRMHD_OK;
+}
+
+static int build_graph(grmhd_ctx* c, int nsteps, int auto_dt) {
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int st = GRMHD_OK;
+    c->launches_tmp = 0;
+    if (auto_dt) {
+        cudaError_t e = launch_cfl(c->d, c->U[0], c->hmin, c->opts.cfl, c->dt, (unsigned int*)c->lam_bits, c->stream);
+        if (e != cudaSuccess) st = set_err(c, GRMHD_ECUDA, "cfl: %s", cudaGetErrorString(e));
+        c->launches_tmp += 2;
+    }
+    for (int s = 0; s < nsteps && st == GRMHD_OK; s++) st = enqueue_step(c);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (st != GRMHD_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return set_err(c, GRMHD_ECUDA, "capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_err(c, GRMHD_ECUDA, "instantiate: %s", cudaGetErrorString(e));
+    c->g_nsteps = nsteps;
+    c->g_auto_dt = auto_dt;
+    c->launches_per_call = c->launches_tmp;
+    return GRMHD_OK;
+}
+
+extern "C" int grmhd_step(grmhd_ctx* c, double dt, int nsteps, double* dt_used) {
+    if (!c || nsteps < 1) return GRMHD_EINVAL;
+    int auto_dt = !(dt > 0.0);
+    if (!c->gexec || c->g_nsteps != nsteps || c->g_auto_dt != auto_dt) {
+        int st = build_graph(c, nsteps, auto_dt);
+        if (st) return st;
+    }
+    if (!auto_dt) CK(cudaMemcpyAsync(c->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->nfail, 0, sizeof(unsigned long long), c->stream));
+    CK(cudaGraphLaunch(c->gexec, c->stream));
+    CK(cudaMemsetAsync(c->nan_flag, 0, sizeof(int), c->stream));
+    CK(launch_nan_check((long long)NV * c->d.P, c->U[0], c->nan_flag, c->stream));
+    int flag = 0;
+    double dtv = dt;
+    CK(cudaMemcpyAsync(&flag, c->nan_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&dtv, c->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (dt_used) *dt_used = dtv;
+    if (flag) return set_err(c, GRMHD_ENAN, "non-finite value in the evolved state");
+    return GRMHD_OK;
+}
+
+extern "C" int grmhd_diag(grmhd_ctx* c, double out[GRMHD_NDIAG]) {
+    if (!c || !out) return GRMHD_EINVAL;
+    CK(cudaMemsetAsync(c->nfail, 0, sizeof(unsigned long long), c->stream));
+    CK(launch_prep(c->d, c->pp, c->U[0], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream));
+    // divergence of the densitized field into scratch
+    const long long P = c->d.P;
+    DerivJob jb[3];
+    for (int dir = 0; dir < 3; dir++) { jb[dir].src = c->U[0] + (V_B + dir) * P; jb[dir].dst = c->scratch; jb[dir].accumulate = dir > 0; jb[dir].pad = 0; }
+    CK(cudaMemcpyAsync(c->jobs + c->job_dbg, jb, sizeof(jb), cudaMemcpyHostToDevice, c->stream));
+    for (int dir = 0; dir < 3; dir++) {
+        const double* M = dir == 0 ? c->Dr : (dir == 1 ? c->Dt : c->Dp);
+        CK(launch_deriv(dir, c->d, c->jobs + c->job_dbg + dir, 1, M, c->r_scale, c->stream));
+    }
+    CK(cudaMemsetAsync(c->diag, 0, sizeof(double) * 8, c->stream));
+    CK(launch_diag(c->d, c->pp, c->U[0], c->prim, c->wq, c->scratch, c->diag, c->stream));
+    double h[8];
+    unsigned long long nf = 0;
+    double dtv = 0.0;
+    CK(cudaMemcpyAsync(h, c->diag, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&nf, c->nfail, sizeof(nf), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&dtv, c->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < GRMHD_NDIAG; i++) out[i] = 0.0;
+    out[0] = h[0];
+    out[1] = h[1];
+    out[2] = h[2];
+    out[3] = (double)nf;
+    out[4] = dtv;
+    return GRMHD_OK;
+}
+
+extern "C" long long grmhd_launch_count(const grmhd_ctx* c) { return c ? c->launches_per_call : -1; }
+
+extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double* flops_out, int n) {
+    if (!c || !ms_out || reps < 1 || n < 1 || n > GRMHD_NKT) return GRMHD_EINVAL;
+    const long long P = c->d.P;
+    const int Ns[3] = {c->d.Nr, c->d.Nt, c->d.Np};
+    double ms[GRMHD_NKT] = {0}, fl[GRMHD_NKT] = {0};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    // keep the state: U[1] <- U[0], work on U[1], U[2] holds the saved copy
+    CK(cudaMemcpyAsync(c->U[2], c->U[0], sizeof(double) * NV * P, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->U[1], c->U[0], sizeof(double) * NV * P, cudaMemcpyDeviceToDevice, c->stream));
+    RKCoef co = {0, 0, 0, 0, -1};
+    int st = GRMHD_OK;
+    for (int k = 0; k < GRMHD_NKT && st == GRMHD_OK; k++) {
+        // bring the buffers the kernel reads up to date (untimed)
+        if (k >= 1) { c->launches_tmp = 0; st = enqueue_stage(c, 1, co, c->scratch); if (st) break; }
+        CK(cudaEventRecord(e0, c->stream));
+        for (int r = 0; r < reps; r++) {
+            cudaError_t e = cudaSuccess;
+            if (k == 0) e = launch_prep(c->d, c->pp, c->U[1], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream);
+            else if (k >= 1 && k <= 3) {
+                int dir = k - 1;
+                const double* M = dir == 0 ? c->Dr : (dir == 1 ? c->Dt : c->Dp);
+                e = launch_deriv(dir, c->d, c->jobs + c->job_first[1][dir], c->job_first_n, M, c->r_scale, c->stream);
+                fl[k] = 2.0 * Ns[dir] * (double)P * c->job_first_n;
+            } else if (k == 4) e = launch_iface_avg(c->d, c->d1, 3 * P, N_D1, c->stream);
+            else if (k >= 5 && k <= 7) {
+                int dir = k - 5;
+                const double* M = dir == 0 ? c->Dr : (dir == 1 ? c->Dt : c->Dp);
+                e = launch_deriv(dir, c->d, c->jobs + c->job_second[dir], c->job_second_n[dir], M, c->r_scale, c->stream);
+                fl[k] = 2.0 * Ns[dir] * (double)P * c->job_second_n[dir];
+            } else if (k == 8) e = launch_iface_avg(c->d, c->d2, 6 * P, N_D2, c->stream);
+            else if (k == 9) e = launch_rhs(c->d, c->pp, c->U[0], c->U[1], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
+                                            c->divF, c->r_scale, c->dt, co, c->scratch, c->acc, c->stream);
+            else {
+                int dir = k - 10;
+                const double* mats[3] = {c->Fr, c->Ft, c->Fp};
+                // filter contraction of all 32 variables of U[1] (scratch <-> U[1] chain)
+                e = launch_deriv(dir, c->d, c->jobs + c->job_filter[1][dir][1], N_BSSN, mats[dir], nullptr, c->stream);
+                if (e == cudaSuccess)
+                    e = launch_deriv(dir, c->d, c->jobs + c->job_filter[1][dir][0], 8, mats[dir], nullptr, c->stream);
+                fl[k] = 2.0 * Ns[dir] * (double)P * NV;
+            }
+            if (e != cudaSuccess) { st = set_err(c, GRMHD_ECUDA, "kernel_times: %s", cudaGetErrorString(e)); break; }
+        }
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        ms[k] = t / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaMemcpyAsync(c->U[0], c->U[2], sizeof(double) * NV * P, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (st) return st;
+    for (int k = 0; k < n; k++) {
+        ms_out[k] = ms[k];
+        if (flops_out) flops_out[k] = fl[k];
+    }
+    return GRMHD_OK;
+}
+
+extern "C" int grmhd_debug_deriv(grmhd_ctx* c, const double* in, double* out, int nfields, int dir) {
+    if (!c || !in || !out || nfields < 1 || nfields > 64 || dir < 0 || dir > 2) return GRMHD_EINVAL;
+    const long long P = c->d.P;
+    std::vector<DerivJob> jb(nfields);
+    for (int f = 0; f < nfields; f++) { jb[f].src = in + f * P; jb[f].dst = out + f * P; jb[f].accumulate = 0; jb[f].pad = 0; }
+    CK(cudaMemcpyAsync(c->jobs + c->job_dbg, jb.data(), sizeof(DerivJob) * nfields, cudaMemcpyHostToDevice, c->stream));
+    const double* M = dir == 0 ? c->Dr : (dir == 1 ? c->Dt : c->Dp);
+    CK(launch_deriv(dir, c->d, c->jobs + c->job_dbg, nfields, M, c->r_scale, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return GRMHD_OK;
+}
+
+extern "C" const char* grmhd_strerror(int s) {
+    switch (s) {
+        case GRMHD_OK: return "ok";
+        case GRMHD_EINVAL: return "invalid argument";
+        case GRMHD_ENOMEM: return "out of memory";
+        case GRMHD_ECUDA: return "CUDA runtime error";
+        case GRMHD_ENAN: return "non-finite value in the evolved state";
+        case GRMHD_ETIMEOUT: return "device-side wait timed out";
+        case GRMHD_EUNSUPPORTED: return "option not supported by this build";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* grmhd_last_error(const grmhd_ctx* c) { return c ? c->err : "no context"; }
+
+// ------------------------------------------------------------------ batch
+extern "C" int grmhd_batch_create(int n, const grmhd_grid* grids, const grmhd_physics* phys,
+                                  const grmhd_opts* opts, void* cuda_stream, grmhd_batch** out) {
+    if (!out || n < 1 || !grids || !phys || !opts) return GRMHD_EINVAL;
+    *out = nullptr;
+    grmhd_batch* b = new (std::nothrow) grmhd_batch();
+    if (!b) return GRMHD_ENOMEM;
+    if (cuda_stream) b->stream = (cudaStream_t)cuda_stream;
+    else {
+        if (cudaStreamCreate(&b->stream) != cudaSuccess) { delete b; return GRMHD_ECUDA; }
+        b->own_stream = true;
+    }
+    b->n = n;
+    b->inst = new (std::nothrow) grmhd_ctx*[n]();
+    if (!b->inst) { grmhd_batch_destroy(b); return GRMHD_ENOMEM; }
+    for (int i = 0; i < n; i++) {
+        int st = grmhd_create(&grids[i], &phys[i], &opts[i], b->stream, &b->inst[i]);
+        if (st) { grmhd_batch_destroy(b); return st; }
+    }
+    *out = b;
+    return GRMHD_OK;
+}
+
+extern "C" grmhd_ctx* grmhd_batch_instance(grmhd_batch* b, int i) {
+    return (b && i >= 0 && i < b->n) ? b->inst[i] : nullptr;
+}
+
+extern "C" int grmhd_batch_step(grmhd_batch* b, const double* dt, int nsteps) {
+    if (!b || !dt || nsteps < 1) return GRMHD_EINVAL;
+    for (int i = 0; i < b->n; i++)
+        if (!(dt[i] > 0.0)) return GRMHD_EINVAL;
+    grmhd_ctx* c = b->inst[0];
+    if (!b->gexec || b->g_nsteps != nsteps) {
+        if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        int st = GRMHD_OK;
+        for (int s = 0; s < nsteps && st == GRMHD_OK; s++)
+            for (int i = 0; i < b->n && st == GRMHD_OK; i++) st = enqueue_step(b->inst[i]);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (st) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return set_err(c, GRMHD_ECUDA, "batch capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return set_err(c, GRMHD_ECUDA, "batch instantiate: %s", cudaGetErrorString(e));
+        b->g_nsteps = nsteps;
+    }
+    for (int i = 0; i < b->n; i++)
+        CK(cudaMemcpyAsync(b->inst[i]->dt, &dt[i], sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaGraphLaunch(b->gexec, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return GRMHD_OK;
+}
+
+extern "C" int grmhd_batch_destroy(grmhd_batch* b) {
+    if (!b) return GRMHD_EINVAL;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->inst) {
+        for (int i = 0; i < b->n; i++)
+            if (b->inst[i]) grmhd_destroy(b->inst[i]);
+        delete[] b->inst;
+    }
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return GRMHD_OK;
+}

@@ -1,0 +1,75 @@
+// Internal declarations shared by the library's translation units (host + device).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/grmhd.h"
+
+namespace gk {
+
+// canonical variable slots
+enum {
+    NV = 32,
+    V_GT = 0, V_PHI = 6, V_AT = 7, V_K = 13, V_GAM = 14, V_ALPHA = 17, V_BETA = 18, V_BG = 21,
+    V_D = 24, V_S = 25, V_TAU = 28, V_B = 29, N_BSSN = 24, N_VAL = 8,
+    // differentiated fields: canonical variables 0..20 (all BSSN + gauge but B^i)
+    N_D1 = 21,
+    // second derivatives of gammatilde_ij (0..5), phi (6), alpha (17), beta^i (18..20)
+    N_D2 = 11,
+    N_PRIM = 7,     // rho, v^r, v^th, v^ph, eps, p, W
+    N_FLUX = 24,    // sqrt(gamma) scriptF^i_v  [dir][var]
+    N_TMN = 10,     // T^{00},T^{01},T^{02},T^{03},T^{11},T^{12},T^{13},T^{22},T^{23},T^{33}
+};
+
+// d1 field f (0..20) direction d: index (f*3 + d); d2 field slot s (0..10) pair q:
+// (s*6 + q) with q = rr, rth, rph, thth, thph, phph
+__host__ __device__ inline int d2_slot_of_var(int v) {
+    return v <= 6 ? v : (v >= 17 && v <= 20 ? v - 10 : -1);
+}
+
+struct Dims {
+    int E, Nr, Nt, Np;
+    long long P;          // points
+    long long NtNp;       // points per radial shell
+    long long elem;       // points per element
+};
+
+struct PhysParams {
+    double M, a, gam, rho_atm, eps_atm;
+    double eta;
+    int gauge, evolve_metric;
+    int c2p_maxit;
+    double c2p_tol;
+    double w_end;         // Clenshaw-Curtis end weight on [-1, 1] for n_r CGL nodes
+};
+
+struct DerivJob {
+    const double* src;
+    double* dst;
+    int accumulate;       // 0: dst = D src, 1: dst += D src
+    int pad;
+};
+
+// ---- kernel launchers (defined in kernels_*.cu); all return cudaGetLastError()
+cudaError_t launch_prep(const Dims& d, const PhysParams& pp, const double* U, double* prim,
+                        double* flux, double* tmn, double* lam, unsigned long long* nfail,
+                        cudaStream_t s);
+struct RKCoef { double a, b, c, w; int acc_mode; };  // out = a U0 + b Us + c dt L (+acc)
+cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, const double* Us,
+                       const double* prim, const double* flux, const double* tmn,
+                       const double* lam, const double* d1, const double* d2,
+                       const double* divF, const double* r_scale_dev, const double* dt_dev,
+                       RKCoef co, double* out, double* acc, cudaStream_t s);
+cudaError_t launch_deriv(int dir, const Dims& d, const DerivJob* jobs_dev, int njobs,
+                         const double* mat_dev, const double* r_scale_dev, cudaStream_t s);
+cudaError_t launch_iface_avg(const Dims& d, double* base, long long field_stride, int nfields,
+                             cudaStream_t s);
+cudaError_t launch_cfl(const Dims& d, const double* U, const double* hmin_dev, double cfl,
+                       double* dt_dev, unsigned int* lam_bits, cudaStream_t s);
+cudaError_t launch_diag(const Dims& d, const PhysParams& pp, const double* U,
+                        const double* prim, const double* wq, const double* divB,
+                        double* out_dev, cudaStream_t s);
+cudaError_t launch_nan_check(long long n, const double* U, int* flag, cudaStream_t s);
+
+}  // namespace gk

@@ -1,0 +1,20 @@
+// Host-side operators and initial data (see host_ops.cpp).
+#pragma once
+#include <vector>
+
+namespace gk {
+std::vector<double> cgl_nodes(int n);
+std::vector<double> gauss_nodes(int n);
+std::vector<double> cheb_lobatto_D(int n);      // d/dx on ascending CGL nodes of [-1, 1]
+std::vector<double> cheb_gauss_D(int n);        // d/dx on ascending Gauss nodes of [-1, 1]
+std::vector<double> fourier_D_row(int n);       // circulant row of d/dphi, N even
+std::vector<double> cheb_filter_matrix(int n, bool lobatto, double alpha, double p);
+std::vector<double> fourier_filter_row(int n, double alpha, double p, bool dealias);
+std::vector<double> quad_weights(int n, bool lobatto);
+// BSSN variables 0..23 of the Kerr-Schild slice at (r, theta)
+void ks_bssn_point(double M, double a, double r, double th, double out[24]);
+void prim_to_cons_point(double rho, double p, const double v_u[3], const double B_u[3],
+                        const double g[3][3], double gam_eos, double* D, double S_d[3],
+                        double* tau);
+void metric_from_bssn_point(const double* bssn, double g[3][3], double* sqg);
+}  // namespace gk

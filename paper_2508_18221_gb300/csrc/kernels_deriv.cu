@@ -1,0 +1,200 @@
+// Spectral derivative / filter contractions and small reductions (FP64).
+//
+// A derivative along direction dir of a field u[E][Nr][Nt][Np] is the 1-D contraction
+// (D u)_i = sum_j D_ij u_j along that axis (paper: "The Spectral Derivative Operators";
+// the Chebyshev coefficient route and the Fourier (ik) multiplier are the same linear
+// maps written as matrices).  r uses the element's CGL matrix scaled by 2/(b-a), theta
+// the Chebyshev-Gauss matrix, phi the circulant Fourier matrix stored as one row.
+// r_scale == nullptr applies the matrix unscaled (modal filters).
+// One thread produces one output node; the matrix sits in shared memory and a warp
+// walks consecutive phi nodes, so every source load of the warp is one coalesced
+// 256-byte segment and every matrix load is a broadcast.
+#include <math.h>
+
+#include "grmhd_internal.h"
+
+namespace gk {
+
+template <int DIR>
+__global__ void __launch_bounds__(256) k_deriv(Dims d, const DerivJob* __restrict__ jobs,
+                                               const double* __restrict__ mat,
+                                               const double* __restrict__ r_scale) {
+    extern __shared__ double sD[];
+    const int N = DIR == 0 ? d.Nr : (DIR == 1 ? d.Nt : d.Np);
+    const int nmat = DIR == 2 ? N : N * N;
+    for (int t = threadIdx.x; t < nmat; t += blockDim.x) sD[t] = mat[t];
+    __syncthreads();
+    const DerivJob job = jobs[blockIdx.y];
+    const long long P = d.P;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+         p += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        if (DIR == 2) {
+            const int l = (int)(p % N);
+            const double* line = job.src + (p - l);
+            // (D u)_l = sum_j c[(l - j) mod N] u_j
+#pragma unroll 4
+            for (int j = 0; j < N; j++) {
+                int m = l - j;
+                m += (m < 0) ? N : 0;
+                acc = fma(sD[m], line[j], acc);
+            }
+        } else {
+            const long long stride = DIR == 0 ? d.NtNp : (long long)d.Np;
+            const int i = (int)((p / stride) % N);
+            const double* col = job.src + (p - (long long)i * stride);
+            const double* Drow = sD + i * N;
+#pragma unroll 4
+            for (int j = 0; j < N; j++) acc = fma(Drow[j], col[(long long)j * stride], acc);
+            if (DIR == 0 && r_scale != nullptr) acc *= r_scale[p / d.elem];
+        }
+        if (job.accumulate) job.dst[p] += acc;
+        else job.dst[p] = acc;
+    }
+}
+
+cudaError_t launch_deriv(int dir, const Dims& d, const DerivJob* jobs_dev, int njobs,
+                         const double* mat_dev, const double* r_scale_dev, cudaStream_t s) {
+    if (njobs <= 0) return cudaSuccess;
+    const int bs = 256;
+    long long nb = (d.P + bs - 1) / bs;
+    if (nb > 65535LL * 32) nb = 65535LL * 32;
+    dim3 grid((unsigned)nb, (unsigned)njobs);
+    const int N = dir == 0 ? d.Nr : (dir == 1 ? d.Nt : d.Np);
+    size_t sm = (size_t)(dir == 2 ? N : N * N) * sizeof(double);
+    if (sm > 48 * 1024) {
+        cudaError_t e = dir == 0 ? cudaFuncSetAttribute(k_deriv<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                                 : cudaFuncSetAttribute(k_deriv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    if (dir == 0) k_deriv<0><<<grid, bs, sm, s>>>(d, jobs_dev, mat_dev, r_scale_dev);
+    else if (dir == 1) k_deriv<1><<<grid, bs, sm, s>>>(d, jobs_dev, mat_dev, r_scale_dev);
+    else k_deriv<2><<<grid, bs, sm, s>>>(d, jobs_dev, mat_dev, r_scale_dev);
+    return cudaGetLastError();
+}
+
+// Replace both copies of each duplicated interface node by their mean.
+__global__ void k_iface_avg(Dims d, double* base, long long fstride, int nfields) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long nif = (long long)(d.E - 1) * d.NtNp;
+    if (t >= nif * nfields) return;
+    int f = (int)(t / nif);
+    long long r = t % nif;
+    int e = (int)(r / d.NtNp);
+    long long kl = r % d.NtNp;
+    double* u = base + f * fstride;
+    long long pl = (long long)e * d.elem + (long long)(d.Nr - 1) * d.NtNp + kl;
+    long long pr = pl + d.NtNp;
+    double m = 0.5 * (u[pl] + u[pr]);
+    u[pl] = m;
+    u[pr] = m;
+}
+
+cudaError_t launch_iface_avg(const Dims& d, double* base, long long fstride, int nfields,
+                             cudaStream_t s) {
+    if (d.E < 2 || nfields <= 0) return cudaSuccess;
+    long long n = (long long)(d.E - 1) * d.NtNp * nfields;
+    int bs = 256;
+    k_iface_avg<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(d, base, fstride, nfields);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- CFL time step
+// lambda = |beta|_gamma + max(alpha, sqrt(2 alpha)); max over nodes by atomicMax on the
+// bit pattern (order-preserving for non-negative doubles); dt = cfl hmin / lambda_max.
+__global__ void k_cfl_lam(Dims d, const double* __restrict__ U, unsigned long long* bits) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long P = d.P;
+    double lam = 0.0;
+    if (p < P) {
+        double e4 = exp(4.0 * U[V_PHI * P + p]);
+        double b[3] = {U[V_BETA * P + p], U[(V_BETA + 1) * P + p], U[(V_BETA + 2) * P + p]};
+        const int sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+        double bb = 0.0;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) bb += b[i] * b[j] * U[(V_GT + sidx[i][j]) * P + p];
+        double al = U[V_ALPHA * P + p];
+        lam = sqrt(e4 * bb) + fmax(al, sqrt(2.0 * al));
+        if (!(lam >= 0.0)) lam = INFINITY;
+    }
+    for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(bits, (unsigned long long)__double_as_longlong(lam));
+}
+
+__global__ void k_cfl_dt(const unsigned long long* bits, const double* hmin, double cfl,
+                         double* dt) {
+    double lam = __longlong_as_double((long long)*bits);
+    *dt = cfl * (*hmin) / lam;
+}
+
+cudaError_t launch_cfl(const Dims& d, const double* U, const double* hmin_dev, double cfl,
+                       double* dt_dev, unsigned int* lam_bits, cudaStream_t s) {
+    unsigned long long* bits = reinterpret_cast<unsigned long long*>(lam_bits);
+    cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    int bs = 256;
+    k_cfl_lam<<<(unsigned)((d.P + bs - 1) / bs), bs, 0, s>>>(d, U, bits);
+    k_cfl_dt<<<1, 1, 0, s>>>(bits, hmin_dev, cfl, dt_dev);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- diagnostics
+// out[0] += w D~, out[1] += w rho s sqrt(gamma), out[2] = max |divB| (bits)
+__global__ void k_diag(Dims d, PhysParams pp, const double* __restrict__ U,
+                       const double* __restrict__ prim, const double* __restrict__ wq,
+                       const double* __restrict__ divB, double* out) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long P = d.P;
+    double m = 0.0, s = 0.0, db = 0.0;
+    if (p < P) {
+        double e4 = exp(4.0 * U[V_PHI * P + p]);
+        const int sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+        double g[3][3];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) g[i][j] = e4 * U[(V_GT + sidx[i][j]) * P + p];
+        double det = g[0][0] * (g[1][1] * g[2][2] - g[1][2] * g[2][1]) -
+                     g[0][1] * (g[1][0] * g[2][2] - g[1][2] * g[2][0]) +
+                     g[0][2] * (g[1][0] * g[2][1] - g[1][1] * g[2][0]);
+        double rho = prim[p], pr = prim[5 * P + p];
+        m = wq[p] * U[V_D * P + p];
+        s = wq[p] * rho * (log(pr / pow(rho, pp.gam)) / (pp.gam - 1.0)) * sqrt(det);
+        db = fabs(divB[p]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m += __shfl_xor_sync(0xffffffffu, m, o);
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        db = fmax(db, __shfl_xor_sync(0xffffffffu, db, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], m);
+        atomicAdd(&out[1], s);
+        atomicMax(reinterpret_cast<unsigned long long*>(&out[2]),
+                  (unsigned long long)__double_as_longlong(db));
+    }
+}
+
+cudaError_t launch_diag(const Dims& d, const PhysParams& pp, const double* U,
+                        const double* prim, const double* wq, const double* divB,
+                        double* out_dev, cudaStream_t s) {
+    int bs = 256;
+    k_diag<<<(unsigned)((d.P + bs - 1) / bs), bs, 0, s>>>(d, pp, U, prim, wq, divB, out_dev);
+    return cudaGetLastError();
+}
+
+__global__ void k_nan(long long n, const double* __restrict__ U, int* flag) {
+    int bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        bad |= !isfinite(U[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+cudaError_t launch_nan_check(long long n, const double* U, int* flag, cudaStream_t s) {
+    int bs = 256;
+    long long nb = (n + bs - 1) / bs;
+    if (nb > 4096) nb = 4096;
+    k_nan<<<(unsigned)nb, bs, 0, s>>>(n, U, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace gk

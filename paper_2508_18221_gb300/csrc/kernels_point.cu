@@ -1,0 +1,667 @@
+// Pointwise kernels of the right-hand side (one thread per grid node, FP64).
+//
+//   k_prep  metric reconstruction -> primitive recovery -> densitized Valencia fluxes,
+//           stress-energy tensor, radial light-cone speed          (paper: "The Primitive
+//           Variable Recovery", "The Conserved Fluxes and Geometric Source Terms")
+//   k_rhs   BSSN + gauge right-hand side, Valencia flux divergence + geometric sources,
+//           interface penalty, outer-boundary freeze, Runge-Kutta stage combination
+//           (paper: "BSSN Evolution Equations", "Gauge Conditions", "Time Integration")
+//
+// Field arrays are structure-of-arrays double[field][P], P = E*Nr*Nt*Np, phi fastest, so
+// consecutive threads of a warp touch consecutive doubles of every field.
+#include <math.h>
+
+#include "grmhd_internal.h"
+
+namespace gk {
+
+#define SI(i, j) c_sidx[i][j]
+__device__ __constant__ int c_sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+
+// --------------------------------------------------------------------------- helpers
+__device__ __forceinline__ double det3(const double g[3][3]) {
+    return g[0][0] * (g[1][1] * g[2][2] - g[1][2] * g[2][1]) -
+           g[0][1] * (g[1][0] * g[2][2] - g[1][2] * g[2][0]) +
+           g[0][2] * (g[1][0] * g[2][1] - g[1][1] * g[2][0]);
+}
+
+// inverse of a symmetric 3x3 matrix by cofactors; returns the determinant
+__device__ __forceinline__ double inv3sym(const double g[3][3], double gi[3][3]) {
+    double c00 = g[1][1] * g[2][2] - g[1][2] * g[1][2];
+    double c01 = g[0][2] * g[1][2] - g[0][1] * g[2][2];
+    double c02 = g[0][1] * g[1][2] - g[0][2] * g[1][1];
+    double c11 = g[0][0] * g[2][2] - g[0][2] * g[0][2];
+    double c12 = g[0][1] * g[0][2] - g[0][0] * g[1][2];
+    double c22 = g[0][0] * g[1][1] - g[0][1] * g[0][1];
+    double det = g[0][0] * c00 + g[0][1] * c01 + g[0][2] * c02;
+    double id = 1.0 / det;
+    gi[0][0] = c00 * id; gi[0][1] = gi[1][0] = c01 * id; gi[0][2] = gi[2][0] = c02 * id;
+    gi[1][1] = c11 * id; gi[1][2] = gi[2][1] = c12 * id; gi[2][2] = c22 * id;
+    return det;
+}
+
+// forward-mode dual number (value, d/dmu) for the Newton derivative of the master function
+struct Dual {
+    double v, d;
+};
+__device__ __forceinline__ Dual mk(double v, double d = 0.0) { Dual r; r.v = v; r.d = d; return r; }
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return mk(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return mk(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return mk(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
+    double iv = 1.0 / b.v;
+    double q = a.v * iv;
+    return mk(q, (a.d - q * b.d) * iv);
+}
+__device__ __forceinline__ Dual operator+(Dual a, double b) { return mk(a.v + b, a.d); }
+__device__ __forceinline__ Dual operator+(double a, Dual b) { return mk(a + b.v, b.d); }
+__device__ __forceinline__ Dual operator-(Dual a, double b) { return mk(a.v - b, a.d); }
+__device__ __forceinline__ Dual operator-(double a, Dual b) { return mk(a - b.v, -b.d); }
+__device__ __forceinline__ Dual operator*(Dual a, double b) { return mk(a.v * b, a.d * b); }
+__device__ __forceinline__ Dual operator*(double a, Dual b) { return mk(a * b.v, a * b.d); }
+__device__ __forceinline__ Dual operator/(double a, Dual b) {
+    double q = a / b.v;
+    return mk(q, -q * b.d / b.v);
+}
+__device__ __forceinline__ Dual dsqrt(Dual a) {
+    double s = sqrt(a.v);
+    return mk(s, a.d * 0.5 / s);
+}
+__device__ __forceinline__ Dual dmin(Dual a, Dual b) { return a.v <= b.v ? a : b; }
+__device__ __forceinline__ Dual dmax(Dual a, Dual b) { return a.v >= b.v ? a : b; }
+__device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ double dmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ double dmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ double val(double a) { return a; }
+__device__ __forceinline__ double val(Dual a) { return a.v; }
+
+// Scalar invariants of the conserved state entering the one-variable master function
+// in mu = 1/(h W) (Kastaun, Kalinani & Ciolfi 2021): q = tau/D, r^2 = S^2/D^2,
+// bb = B^2/D, rb2 = (S.B)^2/D^3.
+struct C2PScal {
+    double D, q, r2, bb, rb2, gam, eps_min;
+};
+
+template <class T>
+__device__ __forceinline__ T master(T mu, const C2PScal& c, T* W_o, T* eps_o, T* x_o) {
+    T x = 1.0 / (1.0 + mu * c.bb);
+    T rbar2 = c.r2 * x * x + mu * x * (1.0 + x) * c.rb2;
+    T qbar = c.q - 0.5 * c.bb - 0.5 * mu * mu * x * x * (c.bb * c.r2 - c.rb2);
+    T v2 = dmin(mu * mu * rbar2, T(c.r2 / (1.0 + c.r2)) + 0.0 * mu);
+    T W = 1.0 / dsqrt(1.0 - v2);
+    T eps = W * (qbar - mu * rbar2) + v2 * W * W / (1.0 + W);
+    T eps_c = dmax(eps, T(c.eps_min) + 0.0 * mu);
+    T ahat = (c.gam - 1.0) * eps_c / (1.0 + eps_c);
+    T h = (1.0 + eps_c) * (1.0 + ahat);
+    T nu = dmax(h / W, (1.0 + ahat) * (1.0 + qbar - mu * rbar2));
+    if (W_o) *W_o = W;
+    if (eps_o) *eps_o = eps;
+    if (x_o) *x_o = x;
+    return mu - 1.0 / (nu + mu * rbar2);
+}
+template <> __device__ __forceinline__ Dual master<Dual>(Dual mu, const C2PScal& c, Dual* W_o,
+                                                         Dual* eps_o, Dual* x_o) {
+    Dual x = 1.0 / (1.0 + mu * c.bb);
+    Dual rbar2 = c.r2 * x * x + mu * x * (1.0 + x) * c.rb2;
+    Dual qbar = c.q - 0.5 * c.bb - 0.5 * mu * mu * x * x * (c.bb * c.r2 - c.rb2);
+    Dual v2 = dmin(mu * mu * rbar2, mk(c.r2 / (1.0 + c.r2)));
+    Dual W = 1.0 / dsqrt(1.0 - v2);
+    Dual eps = W * (qbar - mu * rbar2) + v2 * W * W / (1.0 + W);
+    Dual eps_c = dmax(eps, mk(c.eps_min));
+    Dual ahat = (c.gam - 1.0) * eps_c / (1.0 + eps_c);
+    Dual h = (1.0 + eps_c) * (1.0 + ahat);
+    Dual nu = dmax(h / W, (1.0 + ahat) * (1.0 + qbar - mu * rbar2));
+    if (W_o) *W_o = W;
+    if (eps_o) *eps_o = eps;
+    if (x_o) *x_o = x;
+    return mu - 1.0 / (nu + mu * rbar2);
+}
+
+// Primitive recovery at one point: safeguarded Newton-Raphson on the master function,
+// bracket [0, 1] (h >= 1), started from the previous primitives.  Returns 1 on success
+// without floor, 0 if eps was floored or the iteration did not converge.
+__device__ int con2prim_point(double D, const double S_d[3], double tau, const double B_u[3],
+                              const double g[3][3], const double gi[3][3], double gam,
+                              double eps_min, int maxit, double tol, double guess_mu,
+                              double* rho, double v_u[3], double* eps, double* pr, double* Wout) {
+    double S_u[3];
+    for (int i = 0; i < 3; i++) S_u[i] = gi[i][0] * S_d[0] + gi[i][1] * S_d[1] + gi[i][2] * S_d[2];
+    double iD = 1.0 / D;
+    double S2 = S_d[0] * S_u[0] + S_d[1] * S_u[1] + S_d[2] * S_u[2];
+    double B2 = 0.0;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) B2 += g[i][j] * B_u[i] * B_u[j];
+    double SB = S_d[0] * B_u[0] + S_d[1] * B_u[1] + S_d[2] * B_u[2];
+    C2PScal c;
+    c.D = D;
+    c.q = tau * iD;
+    c.r2 = S2 * iD * iD;
+    c.bb = B2 * iD;
+    c.rb2 = SB * SB * iD * iD * iD;
+    c.gam = gam;
+    c.eps_min = eps_min;
+
+    double lo = 0.0, hi = 1.0;
+    int ok = 1;
+    double fhi = master<double>(1.0, c, nullptr, nullptr, nullptr);
+    if (!(fhi >= 0.0)) ok = 0;
+    double mu = (guess_mu > 0.0 && guess_mu < 1.0) ? guess_mu : 0.5;
+    int conv = 0;
+    for (int it = 0; it < maxit; it++) {
+        Dual f = master<Dual>(mk(mu, 1.0), c, nullptr, nullptr, nullptr);
+        if (f.v == 0.0) { conv = 1; break; }
+        if (f.v < 0.0) lo = mu; else hi = mu;
+        double mn = mu - f.v / f.d;
+        if (!(mn > lo && mn < hi)) mn = 0.5 * (lo + hi);
+        if (fabs(mn - mu) <= tol * mn) { mu = mn; conv = 1; break; }
+        mu = mn;
+        if (hi - lo <= tol * hi) { conv = 1; break; }
+    }
+    if (!conv) ok = 0;
+    double W, e, x;
+    master<double>(mu, c, &W, &e, &x);
+    *Wout = W;
+    *rho = D / W;
+    if (!(e >= eps_min)) ok = 0;
+    e = fmax(e, eps_min);
+    *eps = e;
+    *pr = (gam - 1.0) * (*rho) * e;
+    // v_i = mu x (S_i/D + mu (S.B) B_i / D^2)
+    double B_d[3];
+    for (int i = 0; i < 3; i++) B_d[i] = g[i][0] * B_u[0] + g[i][1] * B_u[1] + g[i][2] * B_u[2];
+    double v_d[3];
+    double fac = mu * SB * iD * iD;
+    for (int i = 0; i < 3; i++) v_d[i] = mu * x * (S_d[i] * iD + fac * B_d[i]);
+    for (int i = 0; i < 3; i++) v_u[i] = gi[i][0] * v_d[0] + gi[i][1] * v_d[1] + gi[i][2] * v_d[2];
+    return ok;
+}
+
+// --------------------------------------------------------------------------- k_prep
+__global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const double* __restrict__ U,
+                                              double* __restrict__ prim, double* __restrict__ flux,
+                                              double* __restrict__ tmn, double* __restrict__ lam,
+                                              unsigned long long* __restrict__ nfail) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long P = d.P;
+    int bad = 0;
+    if (p < P) {
+        double e4 = exp(4.0 * U[V_PHI * P + p]);
+        double g[3][3], gi[3][3];
+        for (int i = 0; i < 3; i++)
+            for (int j = i; j < 3; j++) g[i][j] = g[j][i] = e4 * U[(V_GT + SI(i, j)) * P + p];
+        double det = inv3sym(g, gi);
+        double sqg = sqrt(det);
+        double isq = 1.0 / sqg;
+        double alpha = U[V_ALPHA * P + p];
+        double beta[3] = {U[V_BETA * P + p], U[(V_BETA + 1) * P + p], U[(V_BETA + 2) * P + p]};
+        double Dc = U[V_D * P + p] * isq;
+        double S_d[3], B_u[3];
+        for (int i = 0; i < 3; i++) {
+            S_d[i] = U[(V_S + i) * P + p] * isq;
+            B_u[i] = U[(V_B + i) * P + p] * isq;
+        }
+        double tau = U[V_TAU * P + p] * isq;
+
+        // guess mu = 1/(h W) from the stored primitives
+        double Wg = prim[6 * P + p], eg = prim[4 * P + p];
+        double mu0 = 1.0 / ((1.0 + pp.gam * eg) * Wg);
+        double rho, v[3], eps, pr, W;
+        int ok;
+        if (Dc > pp.rho_atm && isfinite(Dc) && isfinite(tau)) {
+            ok = con2prim_point(Dc, S_d, tau, B_u, g, gi, pp.gam, pp.eps_atm, pp.c2p_maxit,
+                                pp.c2p_tol, mu0, &rho, v, &eps, &pr, &W);
+        } else {
+            ok = 0;
+            rho = pp.rho_atm; v[0] = v[1] = v[2] = 0.0; eps = pp.eps_atm;
+            pr = (pp.gam - 1.0) * rho * eps; W = 1.0;
+        }
+        bad = !ok;
+        prim[0 * P + p] = rho;
+        prim[1 * P + p] = v[0];
+        prim[2 * P + p] = v[1];
+        prim[3 * P + p] = v[2];
+        prim[4 * P + p] = eps;
+        prim[5 * P + p] = pr;
+        prim[6 * P + p] = W;
+
+        // ---- four-vectors
+        double v_d[3];
+        for (int i = 0; i < 3; i++) v_d[i] = g[i][0] * v[0] + g[i][1] * v[1] + g[i][2] * v[2];
+        double ia = 1.0 / alpha;
+        double u0 = W * ia;
+        double uu[3];
+        for (int i = 0; i < 3; i++) uu[i] = W * (v[i] - beta[i] * ia);
+        double b0 = W * (v_d[0] * B_u[0] + v_d[1] * B_u[1] + v_d[2] * B_u[2]) * ia;
+        double iW = 1.0 / W;
+        double bu[3];
+        for (int i = 0; i < 3; i++) bu[i] = (B_u[i] + alpha * b0 * uu[i]) * iW;
+        double beta_d[3];
+        for (int i = 0; i < 3; i++)
+            beta_d[i] = g[i][0] * beta[0] + g[i][1] * beta[1] + g[i][2] * beta[2];
+        double bb_ = beta_d[0] * beta[0] + beta_d[1] * beta[1] + beta_d[2] * beta[2];
+        double g00 = -alpha * alpha + bb_;
+        double bd0 = g00 * b0 + beta_d[0] * bu[0] + beta_d[1] * bu[1] + beta_d[2] * bu[2];
+        double bd[3];
+        for (int i = 0; i < 3; i++)
+            bd[i] = beta_d[i] * b0 + g[i][0] * bu[0] + g[i][1] * bu[1] + g[i][2] * bu[2];
+        double b2 = b0 * bd0 + bu[0] * bd[0] + bu[1] * bd[1] + bu[2] * bd[2];
+        double pstar = pr + 0.5 * b2;
+        double rhohs = rho * (1.0 + eps) + pr + b2;   // rho h*
+        // conserved variables from the primitives (undensitized)
+        double Dp = rho * W;
+        double Sp[3];
+        for (int j = 0; j < 3; j++) Sp[j] = rhohs * W * W * v_d[j] - alpha * b0 * bd[j];
+        double taup = rhohs * W * W - pstar - alpha * alpha * b0 * b0 - Dp;
+        // ---- densitized fluxes [dir][var]
+        double vt[3];
+        for (int i = 0; i < 3; i++) vt[i] = alpha * v[i] - beta[i];
+        for (int i = 0; i < 3; i++) {
+            double* F = flux + (long long)(i * 8) * P + p;
+            F[0 * P] = sqg * (Dp * vt[i]);
+            for (int j = 0; j < 3; j++)
+                F[(1 + j) * P] = sqg * (Sp[j] * vt[i] + (i == j ? alpha * pstar : 0.0) -
+                                        alpha * bd[j] * B_u[i] * iW);
+            F[4 * P] = sqg * (taup * vt[i] + alpha * pstar * v[i] -
+                              alpha * alpha * b0 * B_u[i] * iW);
+            for (int k = 0; k < 3; k++) F[(5 + k) * P] = sqg * (vt[i] * B_u[k] - vt[k] * B_u[i]);
+        }
+        // ---- T^{mu nu}
+        double ia2 = ia * ia;
+        double gu[4][4];
+        gu[0][0] = -ia2;
+        for (int i = 0; i < 3; i++) gu[0][i + 1] = gu[i + 1][0] = beta[i] * ia2;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) gu[i + 1][j + 1] = gi[i][j] - beta[i] * beta[j] * ia2;
+        double u4[4] = {u0, uu[0], uu[1], uu[2]};
+        double b4[4] = {b0, bu[0], bu[1], bu[2]};
+        int n = 0;
+        for (int m = 0; m < 4; m++)
+            for (int k = m; k < 4; k++, n++)
+                tmn[n * P + p] = rhohs * u4[m] * u4[k] + pstar * gu[m][k] - b4[m] * b4[k];
+        lam[p] = fabs(beta[0]) + alpha * sqrt(gi[0][0]);
+    }
+    // warp-aggregated failure count
+    unsigned m = __ballot_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(nfail, (unsigned long long)__popc(m));
+}
+
+// --------------------------------------------------------------------------- k_rhs
+// indices of the 6 second-derivative pairs
+__device__ __constant__ int c_pair[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+
+__global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double* __restrict__ U0,
+                                             const double* __restrict__ Us,
+                                             const double* __restrict__ prim,
+                                             const double* __restrict__ flux,
+                                             const double* __restrict__ tmn,
+                                             const double* __restrict__ lam,
+                                             const double* __restrict__ d1,
+                                             const double* __restrict__ d2,
+                                             const double* __restrict__ divF,
+                                             const double* __restrict__ r_scale,
+                                             const double* __restrict__ dt_dev, RKCoef co,
+                                             double* __restrict__ out, double* __restrict__ acc) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long P = d.P;
+    if (p >= P) return;
+    const double PI = 3.141592653589793;
+    double rhs[NV];
+
+    // ------------------------------------------------------------ state and metric
+    double gt[3][3], At[3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = i; j < 3; j++) {
+            gt[i][j] = gt[j][i] = Us[(V_GT + SI(i, j)) * P + p];
+            At[i][j] = At[j][i] = Us[(V_AT + SI(i, j)) * P + p];
+        }
+    const double phi = Us[V_PHI * P + p];
+    const double K = Us[V_K * P + p];
+    const double alpha = Us[V_ALPHA * P + p];
+    double Gam[3], beta[3], Bg[3];
+    for (int i = 0; i < 3; i++) {
+        Gam[i] = Us[(V_GAM + i) * P + p];
+        beta[i] = Us[(V_BETA + i) * P + p];
+        Bg[i] = Us[(V_BG + i) * P + p];
+    }
+    const double e4 = exp(4.0 * phi);
+    const double e4m = 1.0 / e4;
+    double g[3][3], gi[3][3], gti[3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) g[i][j] = e4 * gt[i][j];
+    double detg = inv3sym(g, gi);
+    double sqg = sqrt(detg);
+    inv3sym(gt, gti);
+
+    // first derivatives: field f, direction dd -> d1[(f*3+dd)*P + p]
+#define D1(f, dd) d1[((long long)(f) * 3 + (dd)) * P + p]
+    double dgt[3][3][3], dAt[3][3][3], dphi[3], dK[3], dGam[3][3], dal[3], dbe[3][3];
+    for (int k = 0; k < 3; k++) {
+        for (int i = 0; i < 3; i++)
+            for (int j = i; j < 3; j++) {
+                dgt[k][i][j] = dgt[k][j][i] = D1(V_GT + SI(i, j), k);
+                dAt[k][i][j] = dAt[k][j][i] = D1(V_AT + SI(i, j), k);
+            }
+        dphi[k] = D1(V_PHI, k);
+        dK[k] = D1(V_K, k);
+        dal[k] = D1(V_ALPHA, k);
+        for (int i = 0; i < 3; i++) {
+            dGam[k][i] = D1(V_GAM + i, k);
+            dbe[k][i] = D1(V_BETA + i, k);
+        }
+    }
+#undef D1
+
+    // ------------------------------------------------------------ Valencia
+    {
+        double T00 = tmn[0 * P + p];
+        double T0i[3] = {tmn[1 * P + p], tmn[2 * P + p], tmn[3 * P + p]};
+        double Tij[3][3];
+        Tij[0][0] = tmn[4 * P + p]; Tij[0][1] = Tij[1][0] = tmn[5 * P + p];
+        Tij[0][2] = Tij[2][0] = tmn[6 * P + p]; Tij[1][1] = tmn[7 * P + p];
+        Tij[1][2] = Tij[2][1] = tmn[8 * P + p]; Tij[2][2] = tmn[9 * P + p];
+        double beta_d[3];
+        for (int i = 0; i < 3; i++)
+            beta_d[i] = g[i][0] * beta[0] + g[i][1] * beta[1] + g[i][2] * beta[2];
+        double T0_d[3];
+        for (int i = 0; i < 3; i++)
+            T0_d[i] = beta_d[i] * T00 + g[i][0] * T0i[0] + g[i][1] * T0i[1] + g[i][2] * T0i[2];
+        double Kij[3][3];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) Kij[i][j] = e4 * (At[i][j] + gt[i][j] * K / 3.0);
+        double asg = alpha * sqg;
+        for (int jd = 0; jd < 3; jd++) {
+            // d_j gamma_kl = e^{4phi} (d_j gammatilde_kl + 4 gammatilde_kl d_j phi)
+            double dg[3][3];
+            for (int k = 0; k < 3; k++)
+                for (int l = 0; l < 3; l++) dg[k][l] = e4 * (dgt[jd][k][l] + 4.0 * gt[k][l] * dphi[jd]);
+            double bbdg = 0.0, t0dg = 0.0, tdg = 0.0;
+            for (int k = 0; k < 3; k++)
+                for (int l = 0; l < 3; l++) {
+                    bbdg += beta[k] * beta[l] * dg[k][l];
+                    t0dg += T0i[k] * beta[l] * dg[k][l];
+                    tdg += Tij[k][l] * dg[k][l];
+                }
+            double t0db = T0_d[0] * dbe[jd][0] + T0_d[1] * dbe[jd][1] + T0_d[2] * dbe[jd][2];
+            double SS = T00 * (0.5 * bbdg - alpha * dal[jd]) + t0dg + t0db + 0.5 * tdg;
+            rhs[V_S + jd] = -divF[(1 + jd) * P + p] + asg * SS;
+        }
+        double bbK = 0.0, TK = 0.0, t0 = 0.0;
+        for (int i = 0; i < 3; i++) {
+            double bK = 0.0;
+            for (int j = 0; j < 3; j++) {
+                bbK += beta[i] * beta[j] * Kij[i][j];
+                TK += Tij[i][j] * Kij[i][j];
+                bK += beta[j] * Kij[i][j];
+            }
+            t0 += T0i[i] * (2.0 * bK - dal[i]);
+        }
+        double bda = beta[0] * dal[0] + beta[1] * dal[1] + beta[2] * dal[2];
+        double Stau = T00 * (bbK - bda) + t0 + TK;
+        rhs[V_D] = -divF[0 * P + p];
+        rhs[V_TAU] = -divF[4 * P + p] + asg * Stau;
+        for (int k = 0; k < 3; k++) rhs[V_B + k] = -divF[(5 + k) * P + p];
+
+        // interface penalty (Rusanov flux, strong form) at duplicated element-end nodes
+        const long long shell = d.NtNp;
+        const long long ir = (p / shell) % d.Nr;
+        const int e = (int)(p / d.elem);
+        int side = 0;
+        if (ir == d.Nr - 1 && e < d.E - 1) side = +1;
+        if (ir == 0 && e > 0) side = -1;
+        if (side != 0) {
+            long long pl = side > 0 ? p : p - shell;
+            long long pr_ = side > 0 ? p + shell : p;
+            double lmax = fmax(lam[pl], lam[pr_]);
+            double J = 1.0 / r_scale[e];
+            double fac = 1.0 / (pp.w_end * J);
+            for (int v = 0; v < 8; v++) {
+                double FL = flux[(0 * 8 + v) * P + pl];
+                double FR = flux[(0 * 8 + v) * P + pr_];
+                double UL = Us[(V_D + v) * P + pl];
+                double UR = Us[(V_D + v) * P + pr_];
+                double Fs = 0.5 * (FL + FR) - 0.5 * lmax * (UR - UL);
+                if (side > 0) rhs[V_D + v] += (FL - Fs) * fac;
+                else rhs[V_D + v] -= (FR - Fs) * fac;
+            }
+        }
+
+        // matter terms for BSSN: rho = alpha^2 T^00, S_i = alpha T^0_i,
+        // S_ij = g_{i mu} g_{j nu} T^{mu nu}
+        if (pp.evolve_metric) {
+            double rho_m = alpha * alpha * T00;
+            double S_i[3];
+            for (int i = 0; i < 3; i++) S_i[i] = alpha * T0_d[i];
+            double Sij[3][3], Str = 0.0;
+            double gT[3][3];  // gamma_ik T^{kj}
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++)
+                    gT[i][j] = g[i][0] * Tij[0][j] + g[i][1] * Tij[1][j] + g[i][2] * Tij[2][j];
+            double gT0[3];
+            for (int i = 0; i < 3; i++) gT0[i] = g[i][0] * T0i[0] + g[i][1] * T0i[1] + g[i][2] * T0i[2];
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) {
+                    double s = beta_d[i] * beta_d[j] * T00 + beta_d[i] * gT0[j] + beta_d[j] * gT0[i] +
+                               gT[i][0] * g[0][j] + gT[i][1] * g[1][j] + gT[i][2] * g[2][j];
+                    Sij[i][j] = s;
+                }
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) Str += gi[i][j] * Sij[i][j];
+
+            // -------------------------------------------------------- BSSN
+#define D2(f, q) d2[((long long)(f) * 6 + (q)) * P + p]
+            // Christoffels of gammatilde: lower Cl[k][i][j] = Gamma_{k ij}, upper Cu[k][i][j]
+            double Cl[3][3][3], Cu[3][3][3];
+            for (int k = 0; k < 3; k++)
+                for (int i = 0; i < 3; i++)
+                    for (int j = i; j < 3; j++)
+                        Cl[k][i][j] = Cl[k][j][i] =
+                            0.5 * (dgt[i][k][j] + dgt[j][k][i] - dgt[k][i][j]);
+            for (int k = 0; k < 3; k++)
+                for (int i = 0; i < 3; i++)
+                    for (int j = i; j < 3; j++)
+                        Cu[k][i][j] = Cu[k][j][i] =
+                            gti[k][0] * Cl[0][i][j] + gti[k][1] * Cl[1][i][j] + gti[k][2] * Cl[2][i][j];
+            double Gd[3];
+            for (int i = 0; i < 3; i++) {
+                double s = 0.0;
+                for (int j = 0; j < 3; j++)
+                    for (int k = 0; k < 3; k++) s += gti[j][k] * Cu[i][j][k];
+                Gd[i] = s;
+            }
+            double divb = dbe[0][0] + dbe[1][1] + dbe[2][2];
+            // A[k][i][m] = gti^{lm} Cu[k][l][i];  Bt[k][j][m] = gti^{lm} Cl[k][l][j]
+            double Ar[3][3][3], Bt[3][3][3];
+            for (int k = 0; k < 3; k++)
+                for (int i = 0; i < 3; i++)
+                    for (int m = 0; m < 3; m++) {
+                        Ar[k][i][m] = gti[0][m] * Cu[k][0][i] + gti[1][m] * Cu[k][1][i] + gti[2][m] * Cu[k][2][i];
+                        Bt[k][i][m] = gti[0][m] * Cl[k][0][i] + gti[1][m] * Cl[k][1][i] + gti[2][m] * Cl[k][2][i];
+                    }
+            double ddphi[3][3], ddal[3][3];
+            for (int i = 0; i < 3; i++)
+                for (int j = i; j < 3; j++) {
+                    int q = c_pair[i][j];
+                    ddphi[i][j] = ddphi[j][i] = D2(6, q);
+                    ddal[i][j] = ddal[j][i] = D2(7, q);
+                }
+            double DDphi[3][3], DDal[3][3];
+            double gdphi2 = 0.0;
+            double gradphi_u[3];
+            for (int k = 0; k < 3; k++)
+                gradphi_u[k] = gti[k][0] * dphi[0] + gti[k][1] * dphi[1] + gti[k][2] * dphi[2];
+            gdphi2 = gradphi_u[0] * dphi[0] + gradphi_u[1] * dphi[1] + gradphi_u[2] * dphi[2];
+            double gdphida = gradphi_u[0] * dal[0] + gradphi_u[1] * dal[1] + gradphi_u[2] * dal[2];
+            for (int i = 0; i < 3; i++)
+                for (int j = i; j < 3; j++) {
+                    double cp = Cu[0][i][j] * dphi[0] + Cu[1][i][j] * dphi[1] + Cu[2][i][j] * dphi[2];
+                    double ca = Cu[0][i][j] * dal[0] + Cu[1][i][j] * dal[1] + Cu[2][i][j] * dal[2];
+                    DDphi[i][j] = DDphi[j][i] = ddphi[i][j] - cp;
+                    // physical Christoffels: + 2(d_i a d_j phi + d_j a d_i phi - gt_ij gt^kl d_l phi d_k a)
+                    double cphys = ca + 2.0 * (dal[i] * dphi[j] + dal[j] * dphi[i] - gt[i][j] * gdphida);
+                    DDal[i][j] = DDal[j][i] = ddal[i][j] - cphys;
+                }
+            double lapphi = 0.0, trDDal = 0.0;
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) {
+                    lapphi += gti[i][j] * DDphi[i][j];
+                    trDDal += gti[i][j] * DDal[i][j];
+                }
+            trDDal *= e4m;
+            // Atilde with raised indices
+            double Aud[3][3], Auu[3][3];
+            for (int k = 0; k < 3; k++)
+                for (int j = 0; j < 3; j++)
+                    Aud[k][j] = gti[k][0] * At[0][j] + gti[k][1] * At[1][j] + gti[k][2] * At[2][j];
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++)
+                    Auu[i][j] = Aud[i][0] * gti[0][j] + Aud[i][1] * gti[1][j] + Aud[i][2] * gti[2][j];
+            double AA = 0.0;
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) AA += At[i][j] * Auu[i][j];
+
+            // X_ij = -D_i D_j alpha + alpha (R_ij - 8 pi S_ij)
+            double X[3][3];
+            for (int i = 0; i < 3; i++)
+                for (int j = i; j < 3; j++) {
+                    int sij = SI(i, j);
+                    double lapg = 0.0;
+                    for (int l = 0; l < 3; l++)
+                        for (int m = l; m < 3; m++) {
+                            double w = (l == m) ? gti[l][m] : 2.0 * gti[l][m];
+                            lapg += w * D2(sij, c_pair[l][m]);
+                        }
+                    double R = -0.5 * lapg;
+                    for (int k = 0; k < 3; k++)
+                        R += 0.5 * (gt[k][i] * dGam[j][k] + gt[k][j] * dGam[i][k]) +
+                             0.5 * Gd[k] * (Cl[i][j][k] + Cl[j][i][k]);
+                    double t = 0.0;
+                    for (int k = 0; k < 3; k++)
+                        for (int m = 0; m < 3; m++)
+                            t += Ar[k][i][m] * Cl[j][k][m] + Ar[k][j][m] * Cl[i][k][m] +
+                                 Cu[k][i][m] * Bt[k][j][m];
+                    R += t;
+                    R += -2.0 * DDphi[i][j] - 2.0 * gt[i][j] * lapphi + 4.0 * dphi[i] * dphi[j] -
+                         4.0 * gt[i][j] * gdphi2;
+                    X[i][j] = X[j][i] = -DDal[i][j] + alpha * (R - 8.0 * PI * Sij[i][j]);
+                }
+            double trX = 0.0;
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) trX += gti[i][j] * X[i][j];
+            for (int i = 0; i < 3; i++)
+                for (int j = i; j < 3; j++) {
+                    int sij = SI(i, j);
+                    double adv_g = beta[0] * dgt[0][i][j] + beta[1] * dgt[1][i][j] + beta[2] * dgt[2][i][j];
+                    double adv_a = beta[0] * dAt[0][i][j] + beta[1] * dAt[1][i][j] + beta[2] * dAt[2][i][j];
+                    double lg = 0.0, la = 0.0, AAd = 0.0;
+                    for (int k = 0; k < 3; k++) {
+                        lg += gt[i][k] * dbe[j][k] + gt[j][k] * dbe[i][k];
+                        la += At[i][k] * dbe[j][k] + At[j][k] * dbe[i][k];
+                        AAd += At[i][k] * Aud[k][j];
+                    }
+                    rhs[V_GT + sij] = -2.0 * alpha * At[i][j] + adv_g + lg - (2.0 / 3.0) * gt[i][j] * divb;
+                    double XTF = X[i][j] - gt[i][j] * trX / 3.0;
+                    rhs[V_AT + sij] = e4m * XTF + alpha * (K * At[i][j] - 2.0 * AAd) + adv_a + la -
+                                      (2.0 / 3.0) * At[i][j] * divb;
+                }
+            rhs[V_PHI] = -alpha * K / 6.0 + (beta[0] * dphi[0] + beta[1] * dphi[1] + beta[2] * dphi[2]) +
+                         divb / 6.0;
+            rhs[V_K] = -trDDal + alpha * (AA + K * K / 3.0) + 4.0 * PI * alpha * (rho_m + Str) +
+                       (beta[0] * dK[0] + beta[1] * dK[1] + beta[2] * dK[2]);
+            // Gammatilde
+            double ddb[3][3][3];  // [q pair via j,k][i]
+            for (int j = 0; j < 3; j++)
+                for (int k = j; k < 3; k++)
+                    for (int i = 0; i < 3; i++)
+                        ddb[j][k][i] = ddb[k][j][i] = D2(7 + 1 + i, c_pair[j][k]);
+            double ddbk[3];  // d_j d_k beta^k
+            for (int j = 0; j < 3; j++) ddbk[j] = ddb[j][0][0] + ddb[j][1][1] + ddb[j][2][2];
+            for (int i = 0; i < 3; i++) {
+                double s = 0.0;
+                for (int j = 0; j < 3; j++)
+                    for (int k = 0; k < 3; k++) s += gti[j][k] * ddb[j][k][i];
+                double s2 = gti[i][0] * ddbk[0] + gti[i][1] * ddbk[1] + gti[i][2] * ddbk[2];
+                double adv = beta[0] * dGam[0][i] + beta[1] * dGam[1][i] + beta[2] * dGam[2][i];
+                double gdb = Gam[0] * dbe[0][i] + Gam[1] * dbe[1][i] + Gam[2] * dbe[2][i];
+                double Ada = Auu[i][0] * dal[0] + Auu[i][1] * dal[1] + Auu[i][2] * dal[2];
+                double CA = 0.0;
+                for (int j = 0; j < 3; j++)
+                    for (int k = 0; k < 3; k++) CA += Cu[i][j][k] * Auu[j][k];
+                double Adp = Auu[i][0] * dphi[0] + Auu[i][1] * dphi[1] + Auu[i][2] * dphi[2];
+                double gdK = gti[i][0] * dK[0] + gti[i][1] * dK[1] + gti[i][2] * dK[2];
+                double gS = gti[i][0] * S_i[0] + gti[i][1] * S_i[1] + gti[i][2] * S_i[2];
+                rhs[V_GAM + i] = s + s2 / 3.0 + adv - gdb + (2.0 / 3.0) * Gam[i] * divb - 2.0 * Ada +
+                                 2.0 * alpha * (CA + 6.0 * Adp - (2.0 / 3.0) * gdK) -
+                                 16.0 * PI * alpha * gS;
+            }
+#undef D2
+            if (pp.gauge == 0) {
+                rhs[V_ALPHA] = -2.0 * alpha * K + beta[0] * dal[0] + beta[1] * dal[1] + beta[2] * dal[2];
+                for (int i = 0; i < 3; i++) {
+                    rhs[V_BETA + i] = 0.75 * Bg[i];
+                    rhs[V_BG + i] = rhs[V_GAM + i] - pp.eta * Bg[i];
+                }
+            } else {
+                rhs[V_ALPHA] = 0.0;
+                for (int i = 0; i < 3; i++) rhs[V_BETA + i] = rhs[V_BG + i] = 0.0;
+            }
+        } else {
+            for (int v = 0; v < N_BSSN; v++) rhs[v] = 0.0;
+        }
+    }
+
+    // frozen outer boundary node
+    {
+        const long long ir = (p / d.NtNp) % d.Nr;
+        const int e = (int)(p / d.elem);
+        if (e == d.E - 1 && ir == d.Nr - 1)
+            for (int v = 0; v < NV; v++) rhs[v] = 0.0;
+    }
+
+    // ------------------------------------------------------------ output
+    const double dt = dt_dev ? *dt_dev : 0.0;
+    if (co.acc_mode < 0) {
+        for (int v = 0; v < NV; v++) out[v * P + p] = rhs[v];
+        return;
+    }
+    for (int v = 0; v < NV; v++) {
+        long long ix = v * P + p;
+        double L = rhs[v];
+        double o;
+        if (co.acc_mode == 0) {
+            // SSP-RK3 (Shu-Osher): a U0 + b (Us + dt L)
+            o = (co.a != 0.0 ? co.a * U0[ix] : 0.0) + co.b * (Us[ix] + dt * L);
+        } else {
+            // RK4: next stage input U0 + c dt L, accumulator acc (+)= w dt L;
+            // final stage (acc_mode 3): U0 + acc + w dt L
+            double wl = co.w * dt * L;
+            if (co.acc_mode == 1) { acc[ix] = wl; o = U0[ix] + co.c * dt * L; }
+            else if (co.acc_mode == 2) { acc[ix] += wl; o = U0[ix] + co.c * dt * L; }
+            else { o = U0[ix] + (acc[ix] + wl); }
+        }
+        out[ix] = o;
+    }
+}
+
+// --------------------------------------------------------------------------- launchers
+cudaError_t launch_prep(const Dims& d, const PhysParams& pp, const double* U, double* prim,
+                        double* flux, double* tmn, double* lam, unsigned long long* nfail,
+                        cudaStream_t s) {
+    int bs = 128;
+    long long nb = (d.P + bs - 1) / bs;
+    k_prep<<<(unsigned)nb, bs, 0, s>>>(d, pp, U, prim, flux, tmn, lam, nfail);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, const double* Us,
+                       const double* prim, const double* flux, const double* tmn,
+                       const double* lam, const double* d1, const double* d2,
+                       const double* divF, const double* r_scale_dev, const double* dt_dev,
+                       RKCoef co, double* out, double* acc, cudaStream_t s) {
+    int bs = 128;
+    long long nb = (d.P + bs - 1) / bs;
+    k_rhs<<<(unsigned)nb, bs, 0, s>>>(d, pp, U0, Us, prim, flux, tmn, lam, d1, d2, divF,
+                                      r_scale_dev, dt_dev, co, out, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace gk

@@ -1,0 +1,241 @@
+"""GPU path vs FP64 oracle, element by element, on identical seeded inputs.
+
+Every case builds the state with the oracle's initial data (exact Kerr-Schild BSSN
+slice + primitive profiles of the workload generator), hands the same array to the
+C-ABI library (grmhd_set_state) and compares.
+
+Tolerance (FP64 bar 1e-11): per variable v, max|gpu_v - oracle_v| <= 1e-11 * s_v with
+s_v = max(max|oracle_v|, max|U| over v's tensor, 1e-6 * group maximum); see
+assert_parity.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import solver as so
+from workloads import config
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2508_18221_gb300 as pkg
+    if not os.path.exists(pkg.LIB_PATH):
+        from paper_2508_18221_gb300 import _build
+        _build.build()
+    pkg.load()
+    torch.cuda.init()
+    return pkg
+
+
+def _ctx(pkg, cfg, **kw):
+    import torch
+    opt_keys = ("evolve_metric", "gauge", "integrator", "filter")
+    grid, phys, opts = pkg.make_structs(cfg, **{k: v for k, v in kw.items() if k in opt_keys})
+    return pkg.Context(grid, phys, opts, torch.cuda.current_stream().cuda_stream)
+
+
+def _oracle(cfg, **kw):
+    pk = {k: v for k, v in kw.items() if k in ("evolve_metric", "gauge", "integrator")}
+    if "filter" in kw:
+        pk["filter_mask"] = kw["filter"]
+    return so.workload_state(cfg, **pk)
+
+
+# canonical variables grouped by the tensor they are components of
+TENSORS = [range(0, 6), [6], range(7, 13), [13], range(14, 17), [17], range(18, 21),
+           range(21, 24), [24], range(25, 28), [28], range(29, 32)]
+TENSOR_OF = {v: list(t) for t in TENSORS for v in t}
+
+
+def assert_parity(got, ref, what, tol=TOL, U=None, groups=((0, 24), (24, 32))):
+    """Per-variable normwise check: max|got_v - ref_v| <= tol * s_v with
+    s_v = max(max|ref_v|, max over the components of v's tensor of max|U|,
+              1e-6 * max over the variable group (BSSN / Valencia) of max|U| and max|ref|).
+
+    The state term matters for the Kerr-Schild metric variables, whose right-hand side
+    is a spectral truncation residue orders of magnitude below the terms that cancel
+    in it (so rounding in the derivative operators, not the method, sets the
+    difference).  It is taken over the whole tensor because a component can vanish in
+    these coordinates (gammatilde_{r theta}, beta^phi) while its right-hand side is
+    built from the others; the group term covers tensors that are identically zero."""
+    worst = 0.0
+    for lo, hi in groups:
+        gU = max(np.abs(U[v]).max() for v in range(lo, hi)) if U is not None else 0.0
+        gR = max(np.abs(ref[v]).max() for v in range(lo, hi))
+        floor = 1e-6 * max(gU, gR)
+        for v in range(lo, hi):
+            sU = max(np.abs(U[w]).max() for w in TENSOR_OF[v]) if U is not None else 0.0
+            s = max(np.abs(ref[v]).max(), sU, floor)
+            err = np.abs(got[v] - ref[v]).max()
+            rel = err / s if s > 0 else err
+            worst = max(worst, rel)
+            assert rel <= tol, f"{what}: variable {v} error {err:.3e} (scale {s:.3e}) rel {rel:.3e}"
+    return worst
+
+
+def _gpu_rhs(pkg, ctx, U):
+    import torch
+    Ud = torch.from_numpy(U.reshape(-1).copy()).cuda()
+    ctx.set_state(Ud, True)
+    out = torch.empty_like(Ud)
+    ctx.rhs(out, True)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().reshape(U.shape)
+
+
+CASES = [
+    ("c1", {}),                                             # 2 elements, 12 x 12 x 16
+    ("c1", {"evolve_metric": 0}),                           # fixed Kerr-Schild metric
+    ("c1", {"gauge": 1}),                                   # frozen gauge
+    ("c1:ragged", {}),                                      # odd sizes, 3 elements
+    ("c1:single", {}),                                      # one element (no interface)
+    ("c1:wide", {}),                                        # full-width theta range
+]
+
+
+def _cfg(name):
+    if name == "c1":
+        return config("c1")
+    if name == "c1:ragged":
+        return config("c1", n_elem=3, n_r=9, n_theta=11, n_phi=6)
+    if name == "c1:single":
+        return config("c1", n_elem=1, n_r=7, n_theta=5, n_phi=4)
+    if name == "c1:wide":
+        return config("c1", theta_min=0.05, theta_max=np.pi - 0.05, n_theta=10)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name,kw", CASES)
+def test_rhs_parity(pkg, name, kw):
+    cfg = _cfg(name)
+    g, p, U = _oracle(cfg, **kw)
+    ctx = _ctx(pkg, cfg, **kw)
+    R = _gpu_rhs(pkg, ctx, U)
+    Rref = so.rhs(U, g, p)
+    assert_parity(R, Rref, f"rhs {name} {kw}", U=U)
+    ctx.close()
+
+
+def test_derivative_operators(pkg):
+    import torch
+    cfg = config("c1", n_elem=3, n_r=10, n_theta=9, n_phi=8)
+    g, p, U = _oracle(cfg)
+    ctx = _ctx(pkg, cfg)
+    src = torch.from_numpy(U.reshape(-1).copy()).cuda()
+    dst = torch.empty_like(src)
+    for d, op in enumerate((g.d_r, g.d_t, g.d_p)):
+        ctx.debug_deriv(src, dst, 32, d)
+        D = dst.cpu().numpy().reshape(U.shape)
+        ref = op(U)
+        for v in range(32):
+            den = np.abs(ref[v]).max()
+            if den > 0:
+                assert np.abs(D[v] - ref[v]).max() <= 1e-12 * den + 1e-13 * np.abs(U[v]).max(), (d, v)
+    ctx.close()
+
+
+def test_con2prim_parity(pkg):
+    import torch
+    cfg = config("c1")
+    g, p, U = _oracle(cfg)
+    prim = so.primitives(U, p)
+    ctx = _ctx(pkg, cfg)
+    ctx.set_state(torch.from_numpy(U.reshape(-1).copy()).cuda(), True)
+    out = torch.empty(7 * U[0].size, dtype=torch.float64, device="cuda")
+    nf = ctx.con2prim(out, True)
+    P = out.cpu().numpy().reshape((7,) + U.shape[1:])
+    assert nf == int(np.sum(~prim["ok"]))
+    ref = [prim["rho"], prim["v"][..., 0], prim["v"][..., 1], prim["v"][..., 2], prim["eps"],
+           prim["p"], prim["W"]]
+    vmax = max(np.abs(ref[i]).max() for i in (1, 2, 3))
+    for i in range(7):
+        sc = vmax if i in (1, 2, 3) else np.abs(ref[i]).max()
+        assert np.abs(P[i] - ref[i]).max() <= 1e-12 * sc, i
+    ctx.close()
+
+
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_step_parity(pkg, integrator):
+    import torch
+    cfg = config("c1", n_elem=3, n_r=9, n_theta=10, n_phi=8)
+    g, p, U = _oracle(cfg, integrator=integrator)
+    ctx = _ctx(pkg, cfg, integrator=integrator)
+    ctx.set_state(torch.from_numpy(U.reshape(-1).copy()).cuda(), True)
+    dt = 2e-3
+    ctx.step(dt, 2)
+    got = np.empty(U.size)
+    ctx.get_state(got, False)
+    ref = so.rk_step(so.rk_step(U, dt, g, p), dt, g, p)
+    assert_parity(got.reshape(U.shape), ref, f"2 steps integrator {integrator}", U=U)
+    ctx.close()
+
+
+def test_init_prims_matches_oracle(pkg):
+    cfg = config("c1", n_elem=2, n_r=8, n_theta=8, n_phi=8)
+    g, p, U = _oracle(cfg)
+    from workloads import primitive_profiles
+    ctx = _ctx(pkg, cfg)
+    r, t, ph = ctx.coords()
+    np.testing.assert_allclose(r.reshape(g.shape), g.R, rtol=1e-15)
+    np.testing.assert_allclose(t.reshape(g.shape), g.T, rtol=1e-15)
+    pr = primitive_profiles(cfg, r.reshape(g.shape), t.reshape(g.shape), ph.reshape(g.shape))
+    ctx.init_prims(pr["rho"], pr["p"], pr["vr"], pr["vth"], pr["vph"], pr["A_phi"])
+    got = np.empty(U.size)
+    ctx.get_state(got, False)
+    got = got.reshape(U.shape)
+    for v in range(32):
+        sc = max(np.abs(U[w]).max() for w in TENSOR_OF[v])
+        assert np.abs(got[v] - U[v]).max() <= 1e-12 * sc, v
+    ctx.close()
+
+
+def test_cfl_and_diagnostics(pkg):
+    import torch
+    cfg = config("c1")
+    g, p, U = _oracle(cfg)
+    ctx = _ctx(pkg, cfg)
+    ctx.set_state(torch.from_numpy(U.reshape(-1).copy()).cuda(), True)
+    np.testing.assert_allclose(ctx.cfl_dt(), so.cfl_dt(U, g, p), rtol=1e-13)
+    dg = ctx.diag()
+    ref = so.diagnostics(U, g, p)
+    np.testing.assert_allclose(dg[0], ref[0], rtol=1e-13)
+    np.testing.assert_allclose(dg[1], ref[1], rtol=1e-12)
+    assert dg[2] <= 1e-12 * np.abs(U[so.I_B:so.I_B + 3]).max() * 100
+    ctx.close()
+
+
+def test_invalid_and_nan(pkg):
+    import torch
+    cfg = config("c1", n_elem=1, n_r=6, n_theta=6, n_phi=4)
+    g, p, U = _oracle(cfg)
+    ctx = _ctx(pkg, cfg)
+    bad = U.copy()
+    bad[so.I_TAU, 0, 2, 2, 1] = np.nan
+    ctx.set_state(torch.from_numpy(bad.reshape(-1).copy()).cuda(), True)
+    with pytest.raises(pkg.GrmhdError, match="-4"):
+        ctx.step(1e-3, 1)
+    with pytest.raises(pkg.GrmhdError, match="-1"):
+        ctx.step(1e-3, 0)
+    ctx.close()
+
+
+@pytest.mark.slow
+def test_rhs_parity_full_size(pkg):
+    """The benchmarked 8-element 24 x 32 x 64 instance (393,216 nodes) in the launch
+    configuration the benchmark uses: every node of one RHS evaluation against the
+    oracle."""
+    cfg = config("c2")
+    g, p, U = _oracle(cfg)
+    ctx = _ctx(pkg, cfg)
+    R = _gpu_rhs(pkg, ctx, U)
+    Rref = so.rhs(U, g, p)
+    assert_parity(R, Rref, "rhs c2 full size", U=U)
+    ctx.close()
