@@ -186,6 +186,26 @@ int grmhd_batch_destroy(grmhd_batch* b);
  * operators (radial: per element, one-sided at element ends).  Device pointers. */
 int grmhd_debug_deriv(grmhd_ctx* ctx, const double* in, double* out, int nfields, int dir);
 
+/* Allocation-free CFL time step (the paper has no counterpart: this is a service of the
+ * library).  Some callers cannot call cudaMalloc: hosts that own every byte of device
+ * memory through their own pool allocator and forbid outside allocations, and
+ * latency-bound loops where an allocation (which can synchronise the whole device) is
+ * not acceptable.  They cannot create a context either, since grmhd_create allocates.
+ * This entry point computes the same dt as grmhd_cfl_dt from a caller-owned canonical
+ * state (device pointer, GRMHD_NV * n_points doubles) and the grid's smallest node
+ * spacing hmin = min over nodes of min(dr, r dtheta, r sin(theta) dphi), writing dt to
+ * the device pointer dt_out, stream-ordered on cuda_stream (NULL = legacy default).
+ * It allocates nothing: its reduction scratch is a fixed 512 KiB array in the library's
+ * device memory, which every GPU that loads the library holds until the process exits.
+ * Limits: n_points <= 16,777,216 (larger inputs return GRMHD_EINVAL before any work);
+ * hmin > 0, cfl > 0.  The first call on a device looks up that array's device address
+ * (with the device current): make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents (every call overwrites
+ * what it reads, so nothing needs clearing); calls that overlap on the GPU (several
+ * streams, threads or devices' work in flight on the same device at once) race. */
+int grmhd_cfl_dt_noalloc(const double* state, long long n_points, double hmin, double cfl,
+                         double* dt_out, void* cuda_stream);
+
 const char* grmhd_strerror(int status);
 const char* grmhd_last_error(const grmhd_ctx* ctx);
 

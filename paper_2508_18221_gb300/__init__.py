@@ -62,6 +62,7 @@ SIGNATURES = {
     "grmhd_batch_step": (C.c_int, [_P, _D, C.c_int]),
     "grmhd_batch_destroy": (C.c_int, [_P]),
     "grmhd_debug_deriv": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
+    "grmhd_cfl_dt_noalloc": (C.c_int, [_P, C.c_longlong, C.c_double, C.c_double, _P, _P]),
     "grmhd_strerror": (C.c_char_p, [C.c_int]),
     "grmhd_last_error": (C.c_char_p, [_P]),
 }
