@@ -167,8 +167,9 @@ long long grmhd_launch_count(const grmhd_ctx* ctx);
  * r/theta/phi, 4 interface mean of d_r, 5-7 second-derivative contractions r/theta/phi,
  * 8 interface mean of d_rr, 9 rhs (BSSN + Valencia + penalty + RK), 10-12 filter
  * contractions r/theta/phi.  flops_out (may be NULL) receives the algorithmic FP64
- * flops of one launch of each class for the contractions (2 N per output node) and 0
- * for the others.  The state is left unchanged. */
+ * flops of one launch of each class for the contractions (2 N per output node for a
+ * dense row; about N per output node for the reflection-split form, counted exactly)
+ * and 0 for the others.  The state is left unchanged. */
 enum { GRMHD_NKT = 13 };
 int grmhd_kernel_times(grmhd_ctx* ctx, int reps, double* ms_out, double* flops_out, int n);
 

@@ -46,6 +46,8 @@ struct grmhd_ctx {
     double* Fr;
     double* Ft;
     double* Fp;
+    double* Ds[3];           // reflection-split derivative operators (nullptr: dense only)
+    double* Fs[3];           // reflection-split filter operators
     double* r_scale;         // E
     double* wq;              // P quadrature weights
     double* hmin;            // 1
@@ -143,6 +145,10 @@ static void free_ctx(grmhd_ctx* c) {
                        &c->Ft, &c->Fp, &c->r_scale, &c->wq, &c->hmin, &c->dt, &c->diag};
     for (double** b : bufs)
         if (*b) cudaFree(*b);
+    for (int k = 0; k < 3; k++) {
+        if (c->Ds[k]) cudaFree(c->Ds[k]);
+        if (c->Fs[k]) cudaFree(c->Fs[k]);
+    }
     if (c->nfail) cudaFree(c->nfail);
     if (c->lam_bits) cudaFree(c->lam_bits);
     if (c->nan_flag) cudaFree(c->nan_flag);
@@ -319,6 +325,23 @@ extern "C" int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, c
         free_ctx(c);
         return GRMHD_ECUDA;
     }
+    // reflection-split copies of the six operators
+    {
+        const int Ns[3] = {Nr, Nt, Np};
+        std::vector<double> dense_d[3] = {Dr, Dt, circulant(Dp)};
+        std::vector<double> dense_f[3] = {Fr, Ft, circulant(Fp)};
+        for (int k = 0; k < 3; k++) {
+            if (!eo_supported(k, Ns[k])) continue;
+            std::vector<double> sd = split_operator(dense_d[k], Ns[k], k == 2 ? 1 : 0);
+            std::vector<double> sf = split_operator(dense_f[k], Ns[k], k == 2 ? 1 : 0);
+            if (dalloc(&c->Ds[k], sd.size()) != cudaSuccess || dalloc(&c->Fs[k], sf.size()) != cudaSuccess ||
+                upload(c->Ds[k], sd, s) != cudaSuccess || upload(c->Fs[k], sf, s) != cudaSuccess) {
+                free_ctx(c);
+                return GRMHD_ENOMEM;
+            }
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) { free_ctx(c); return GRMHD_ECUDA; }
+    }
     *out = c;
     return GRMHD_OK;
 }
@@ -348,10 +371,21 @@ extern "C" int grmhd_coords(const grmhd_ctx* c, double* r, double* th, double* p
 }
 
 // ------------------------------------------------------------------ pipeline
+// One directional contraction of `njobs` fields: the reflection-split kernel when the
+// size has a compiled instance, the dense kernel otherwise.  filter = 1 uses the modal
+// filter operator (unscaled), 0 the derivative (radial: scaled per element).
+static cudaError_t contract(grmhd_ctx* c, int dir, int filter, const DerivJob* jobs, int njobs) {
+    const double* split = filter ? c->Fs[dir] : c->Ds[dir];
+    const double* rs = filter ? nullptr : c->r_scale;
+    if (split) return launch_deriv_eo(dir, c->d, jobs, njobs, split, filter ? 1 : -1, rs, c->stream);
+    const double* dense = filter ? (dir == 0 ? c->Fr : (dir == 1 ? c->Ft : c->Fp))
+                                 : (dir == 0 ? c->Dr : (dir == 1 ? c->Dt : c->Dp));
+    return launch_deriv(dir, c->d, jobs, njobs, dense, rs, c->stream);
+}
+
 static int enqueue_first_derivs(grmhd_ctx* c, int b) {
     for (int dir = 0; dir < 3; dir++) {
-        const double* M = dir == 0 ? c->Dr : (dir == 1 ? c->Dt : c->Dp);
-        CK(launch_deriv(dir, c->d, c->jobs + c->job_first[b][dir], c->job_first_n, M, c->r_scale, c->stream));
+        CK(contract(c, dir, 0, c->jobs + c->job_first[b][dir], c->job_first_n));
         c->launches_tmp++;
     }
     CK(launch_iface_avg(c->d, c->d1, 3 * c->d.P, N_D1, c->stream));
@@ -361,8 +395,7 @@ static int enqueue_first_derivs(grmhd_ctx* c, int b) {
 
 static int enqueue_second_derivs(grmhd_ctx* c) {
     for (int dir = 0; dir < 3; dir++) {
-        const double* M = dir == 0 ? c->Dr : (dir == 1 ? c->Dt : c->Dp);
-        CK(launch_deriv(dir, c->d, c->jobs + c->job_second[dir], c->job_second_n[dir], M, c->r_scale, c->stream));
+        CK(contract(c, dir, 0, c->jobs + c->job_second[dir], c->job_second_n[dir]));
         c->launches_tmp++;
     }
     CK(launch_iface_avg(c->d, c->d2, 6 * c->d.P, N_D2, c->stream));
@@ -390,7 +423,6 @@ static int enqueue_stage(grmhd_ctx* c, int b, RKCoef co, double* out) {
 static int enqueue_filter(grmhd_ctx* c, int b) {
     const long long P = c->d.P;
     const int m = c->opts.filter;
-    const double* mats[3] = {c->Fr, c->Ft, c->Fp};
     for (int dir = 0; dir < 3; dir++) {
         const double* src = dir == 0 ? c->U[b] : (dir == 1 ? c->scratch : c->U[b]);
         double* dst = dir == 0 ? c->scratch : (dir == 1 ? c->U[b] : c->U[0]);
@@ -398,7 +430,7 @@ static int enqueue_filter(grmhd_ctx* c, int b) {
             int bit = (grp == 0 ? 1 : 8) << dir;
             int v0 = grp == 0 ? V_D : 0, nv = grp == 0 ? 8 : N_BSSN;
             if (m & bit) {
-                CK(launch_deriv(dir, c->d, c->jobs + c->job_filter[b][dir][grp], nv, mats[dir], nullptr, c->stream));
+                CK(contract(c, dir, 1, c->jobs + c->job_filter[b][dir][grp], nv));
                 c->launches_tmp++;
             } else if (src != dst) {
                 CK(cudaMemcpyAsync(dst + v0 * P, src + v0 * P, sizeof(double) * nv * P, cudaMemcpyDeviceToDevice, c->stream));
@@ -599,10 +631,7 @@ extern "C" int grmhd_diag(grmhd_ctx* c, double out[GRMHD_NDIAG]) {
     DerivJob jb[3];
     for (int dir = 0; dir < 3; dir++) { jb[dir].src = c->U[0] + (V_B + dir) * P; jb[dir].dst = c->scratch; jb[dir].accumulate = dir > 0; jb[dir].pad = 0; }
     CK(cudaMemcpyAsync(c->jobs + c->job_dbg, jb, sizeof(jb), cudaMemcpyHostToDevice, c->stream));
-    for (int dir = 0; dir < 3; dir++) {
-        const double* M = dir == 0 ? c->Dr : (dir == 1 ? c->Dt : c->Dp);
-        CK(launch_deriv(dir, c->d, c->jobs + c->job_dbg + dir, 1, M, c->r_scale, c->stream));
-    }
+    for (int dir = 0; dir < 3; dir++) CK(contract(c, dir, 0, c->jobs + c->job_dbg + dir, 1));
     CK(cudaMemsetAsync(c->diag, 0, sizeof(double) * 8, c->stream));
     CK(launch_diag(c->d, c->pp, c->U[0], c->prim, c->wq, c->scratch, c->diag, c->stream));
     double h[8];
@@ -623,10 +652,23 @@ extern "C" int grmhd_diag(grmhd_ctx* c, double out[GRMHD_NDIAG]) {
 
 extern "C" long long grmhd_launch_count(const grmhd_ctx* c) { return c ? c->launches_per_call : -1; }
 
+// Algorithmic FP64 flops of one contraction of one field over the whole grid: dense
+// rows 2 N per output; reflection split per line 2 np (s, a) + np (4 np + 2 nf + 5)
+// (pair outputs) + nf (2 np + 2 nf + 1) (fixed-point outputs), np pairs, nf fixed points.
+static double contraction_flops(const grmhd_ctx* c, int dir, int filter) {
+    const int Ns[3] = {c->d.Nr, c->d.Nt, c->d.Np};
+    const int N = Ns[dir];
+    const double P = (double)c->d.P;
+    const double* split = filter ? c->Fs[dir] : c->Ds[dir];
+    if (!split) return 2.0 * N * P;
+    double np = dir == 2 ? N / 2 - 1 : N / 2, nf = dir == 2 ? 2 : N % 2;
+    double per_line = 2 * np + np * (4 * np + 2 * nf + 5) + nf * (2 * np + 2 * nf + 1);
+    return per_line * P / N;
+}
+
 extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double* flops_out, int n) {
     if (!c || !ms_out || reps < 1 || n < 1 || n > GRMHD_NKT) return GRMHD_EINVAL;
     const long long P = c->d.P;
-    const int Ns[3] = {c->d.Nr, c->d.Nt, c->d.Np};
     double ms[GRMHD_NKT] = {0}, fl[GRMHD_NKT] = {0};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -645,26 +687,22 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
             if (k == 0) e = launch_prep(c->d, c->pp, c->U[1], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream);
             else if (k >= 1 && k <= 3) {
                 int dir = k - 1;
-                const double* M = dir == 0 ? c->Dr : (dir == 1 ? c->Dt : c->Dp);
-                e = launch_deriv(dir, c->d, c->jobs + c->job_first[1][dir], c->job_first_n, M, c->r_scale, c->stream);
-                fl[k] = 2.0 * Ns[dir] * (double)P * c->job_first_n;
+                e = contract(c, dir, 0, c->jobs + c->job_first[1][dir], c->job_first_n);
+                fl[k] = contraction_flops(c, dir, 0) * c->job_first_n;
             } else if (k == 4) e = launch_iface_avg(c->d, c->d1, 3 * P, N_D1, c->stream);
             else if (k >= 5 && k <= 7) {
                 int dir = k - 5;
-                const double* M = dir == 0 ? c->Dr : (dir == 1 ? c->Dt : c->Dp);
-                e = launch_deriv(dir, c->d, c->jobs + c->job_second[dir], c->job_second_n[dir], M, c->r_scale, c->stream);
-                fl[k] = 2.0 * Ns[dir] * (double)P * c->job_second_n[dir];
+                e = contract(c, dir, 0, c->jobs + c->job_second[dir], c->job_second_n[dir]);
+                fl[k] = contraction_flops(c, dir, 0) * c->job_second_n[dir];
             } else if (k == 8) e = launch_iface_avg(c->d, c->d2, 6 * P, N_D2, c->stream);
             else if (k == 9) e = launch_rhs(c->d, c->pp, c->U[0], c->U[1], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
                                             c->divF, c->r_scale, c->dt, co, c->scratch, c->acc, c->stream);
             else {
                 int dir = k - 10;
-                const double* mats[3] = {c->Fr, c->Ft, c->Fp};
                 // filter contraction of all 32 variables of U[1] (scratch <-> U[1] chain)
-                e = launch_deriv(dir, c->d, c->jobs + c->job_filter[1][dir][1], N_BSSN, mats[dir], nullptr, c->stream);
-                if (e == cudaSuccess)
-                    e = launch_deriv(dir, c->d, c->jobs + c->job_filter[1][dir][0], 8, mats[dir], nullptr, c->stream);
-                fl[k] = 2.0 * Ns[dir] * (double)P * NV;
+                e = contract(c, dir, 1, c->jobs + c->job_filter[1][dir][1], N_BSSN);
+                if (e == cudaSuccess) e = contract(c, dir, 1, c->jobs + c->job_filter[1][dir][0], 8);
+                fl[k] = contraction_flops(c, dir, 1) * NV;
             }
             if (e != cudaSuccess) { st = set_err(c, GRMHD_ECUDA, "kernel_times: %s", cudaGetErrorString(e)); break; }
         }
@@ -692,8 +730,7 @@ extern "C" int grmhd_debug_deriv(grmhd_ctx* c, const double* in, double* out, in
     std::vector<DerivJob> jb(nfields);
     for (int f = 0; f < nfields; f++) { jb[f].src = in + f * P; jb[f].dst = out + f * P; jb[f].accumulate = 0; jb[f].pad = 0; }
     CK(cudaMemcpyAsync(c->jobs + c->job_dbg, jb.data(), sizeof(DerivJob) * nfields, cudaMemcpyHostToDevice, c->stream));
-    const double* M = dir == 0 ? c->Dr : (dir == 1 ? c->Dt : c->Dp);
-    CK(launch_deriv(dir, c->d, c->jobs + c->job_dbg, nfields, M, c->r_scale, c->stream));
+    CK(contract(c, dir, 0, c->jobs + c->job_dbg, nfields));
     CK(cudaStreamSynchronize(c->stream));
     return GRMHD_OK;
 }

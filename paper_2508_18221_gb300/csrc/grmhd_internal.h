@@ -63,6 +63,12 @@ cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, co
                        RKCoef co, double* out, double* acc, cudaStream_t s);
 cudaError_t launch_deriv(int dir, const Dims& d, const DerivJob* jobs_dev, int njobs,
                          const double* mat_dev, const double* r_scale_dev, cudaStream_t s);
+// reflection-split contraction (kernels_eo.cu): cudaErrorNotSupported when N has no
+// compiled instance; sign -1 for derivatives, +1 for filters
+bool eo_supported(int dir, int N);
+cudaError_t launch_deriv_eo(int dir, const Dims& d, const DerivJob* jobs, int njobs,
+                            const double* op_split, int sign, const double* r_scale,
+                            cudaStream_t s);
 cudaError_t launch_iface_avg(const Dims& d, double* base, long long field_stride, int nfields,
                              cudaStream_t s);
 cudaError_t launch_cfl(const Dims& d, const double* U, const double* hmin_dev, double cfl,

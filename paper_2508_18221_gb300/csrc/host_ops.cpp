@@ -125,6 +125,49 @@ std::vector<double> quad_weights(int n, bool lobatto) {
     return w;
 }
 
+// ---------------------------------------------------------------- reflection split
+// Index pairs and fixed points of the node reflection (see kernels_eo.cu):
+// kind 0 (Chebyshev nodes): pairs (ip, N-1-ip), ip < N/2; fixed N/2 when N is odd.
+// kind 1 (Fourier nodes):   pairs (ip+1, N-1-ip), ip < N/2-1; fixed 0 and N/2.
+static void split_sets(int N, int kind, std::vector<int>& lo, std::vector<int>& hi, std::vector<int>& fx) {
+    lo.clear(); hi.clear(); fx.clear();
+    int np = kind == 0 ? N / 2 : N / 2 - 1;
+    for (int ip = 0; ip < np; ip++) {
+        lo.push_back(kind == 0 ? ip : ip + 1);
+        hi.push_back(N - 1 - ip);
+    }
+    if (kind == 0) { if (N % 2) fx.push_back(N / 2); }
+    else { fx.push_back(0); fx.push_back(N / 2); }
+}
+
+std::vector<double> split_operator(const std::vector<double>& M, int N, int kind) {
+    std::vector<int> lo, hi, fx;
+    split_sets(N, kind, lo, hi, fx);
+    int np = (int)lo.size(), nf = (int)fx.size();
+    std::vector<double> out;
+    out.reserve((size_t)2 * np * np + 2 * np * nf + nf * nf);
+    auto m = [&](int i, int j) { return M[(size_t)i * N + j]; };
+    for (int i = 0; i < np; i++)      // E
+        for (int j = 0; j < np; j++) out.push_back(0.5 * (m(lo[i], lo[j]) + m(lo[i], hi[j])));
+    for (int i = 0; i < np; i++)      // O
+        for (int j = 0; j < np; j++) out.push_back(0.5 * (m(lo[i], lo[j]) - m(lo[i], hi[j])));
+    for (int i = 0; i < np; i++)      // C: fixed-point columns of the pair rows
+        for (int f = 0; f < nf; f++) out.push_back(m(lo[i], fx[f]));
+    for (int f = 0; f < nf; f++)      // F: fixed-point rows against the pair columns
+        for (int j = 0; j < np; j++) out.push_back(m(fx[f], lo[j]));
+    for (int f = 0; f < nf; f++)      // G: fixed-point block
+        for (int g = 0; g < nf; g++) out.push_back(m(fx[f], fx[g]));
+    return out;
+}
+
+std::vector<double> circulant(const std::vector<double>& row) {
+    int n = (int)row.size();
+    std::vector<double> M((size_t)n * n);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) M[(size_t)i * n + j] = row[((i - j) % n + n) % n];
+    return M;
+}
+
 // ---------------------------------------------------------------- Kerr-Schild data
 // forward-mode dual number for derivatives of the closed-form Kerr-Schild 3+1 fields
 struct Dn {

@@ -11,6 +11,10 @@ std::vector<double> fourier_D_row(int n);       // circulant row of d/dphi, N ev
 std::vector<double> cheb_filter_matrix(int n, bool lobatto, double alpha, double p);
 std::vector<double> fourier_filter_row(int n, double alpha, double p, bool dealias);
 std::vector<double> quad_weights(int n, bool lobatto);
+// reflection-split packing [E | O | C | F | G] of a dense N x N operator (kernels_eo.cu);
+// kind 0 Chebyshev node set, 1 Fourier node set
+std::vector<double> split_operator(const std::vector<double>& M, int N, int kind);
+std::vector<double> circulant(const std::vector<double>& row);
 // BSSN variables 0..23 of the Kerr-Schild slice at (r, theta)
 void ks_bssn_point(double M, double a, double r, double th, double out[24]);
 void prim_to_cons_point(double rho, double p, const double v_u[3], const double B_u[3],
