@@ -57,6 +57,12 @@ struct grmhd_ctx {
     unsigned long long* lam_bits;
     int* nan_flag;
     DerivJob* jobs;          // all job lists
+    // mixed-precision (tensor-core) contractions
+    uint8_t* tc_img[3];      // operator images r / theta / phi
+    TcJob* tcjobs;
+    int tc_first[3][3];      // [buffer][dir]
+    int tc_second[3];
+    int* tc_err;
     int job_first[3][3];     // [buffer][dir] offset of the first-derivative jobs
     int job_first_n;
     int job_second[3];       // [dir] offset of the second-derivative jobs
@@ -129,7 +135,11 @@ static int validate(const grmhd_grid* g, const grmhd_physics* ph, const grmhd_op
     if (!(ph->M > 0.0) || !(std::fabs(ph->a) < ph->M)) { strcpy(msg, "need M > 0 and |a| < M"); return GRMHD_EINVAL; }
     if (!(ph->gamma_eos > 1.0)) { strcpy(msg, "gamma_eos must exceed 1"); return GRMHD_EINVAL; }
     if (!(ph->rho_atm > 0.0) || !(ph->eps_atm >= 0.0)) { strcpy(msg, "bad floors"); return GRMHD_EINVAL; }
-    if (o->precision != 0) { strcpy(msg, "precision mode not built"); return GRMHD_EUNSUPPORTED; }
+    if (o->precision < 0 || o->precision > 2) { strcpy(msg, "precision must be 0, 1 or 2"); return GRMHD_EUNSUPPORTED; }
+    if (o->precision > 0 && (g->n_r > 128 || g->n_theta > 128 || g->n_phi > 128)) {
+        strcpy(msg, "tensor-core contractions support at most 128 nodes per direction");
+        return GRMHD_EUNSUPPORTED;
+    }
     if (o->integrator != 0 && o->integrator != 1) { strcpy(msg, "integrator must be 0 or 1"); return GRMHD_EINVAL; }
     if (o->gauge != 0 && o->gauge != 1) { strcpy(msg, "gauge must be 0 or 1"); return GRMHD_EINVAL; }
     if (!(o->cfl > 0.0) || o->c2p_maxit < 1 || !(o->c2p_tol > 0.0)) { strcpy(msg, "bad cfl / c2p options"); return GRMHD_EINVAL; }
@@ -153,6 +163,10 @@ static void free_ctx(grmhd_ctx* c) {
     if (c->lam_bits) cudaFree(c->lam_bits);
     if (c->nan_flag) cudaFree(c->nan_flag);
     if (c->jobs) cudaFree(c->jobs);
+    for (int k = 0; k < 3; k++)
+        if (c->tc_img[k]) cudaFree(c->tc_img[k]);
+    if (c->tcjobs) cudaFree(c->tcjobs);
+    if (c->tc_err) cudaFree(c->tc_err);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -342,6 +356,53 @@ extern "C" int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, c
         }
         if (cudaStreamSynchronize(s) != cudaSuccess) { free_ctx(c); return GRMHD_ECUDA; }
     }
+    if (kernels_init() != cudaSuccess) { free_ctx(c); return GRMHD_ECUDA; }
+    // tensor-core operator images and job lists (mixed-precision modes)
+    if (opts->precision > 0) {
+        const int tf32 = opts->precision == 2;
+        const int Ns[3] = {Nr, Nt, Np};
+        std::vector<double> dense_d[3] = {Dr, Dt, circulant(Dp)};
+        for (int k = 0; k < 3; k++) {
+            std::vector<uint8_t> img = tc_operator_image(dense_d[k], Ns[k], tf32);
+            if (cudaMalloc(&c->tc_img[k], img.size()) != cudaSuccess ||
+                cudaMemcpyAsync(c->tc_img[k], img.data(), img.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+                free_ctx(c);
+                return GRMHD_ENOMEM;
+            }
+        }
+        float* d1f = reinterpret_cast<float*>(c->d1);
+        float* d2f = reinterpret_cast<float*>(c->d2);
+        float* dFf = reinterpret_cast<float*>(c->divF);
+        std::vector<TcJob> tj;
+        auto addt = [&](const void* src, float* dst, int acc) { TcJob j; j.src = src; j.dst = dst; j.accumulate = acc; j.pad = 0; tj.push_back(j); };
+        for (int b = 0; b < 3; b++)
+            for (int dir = 0; dir < 3; dir++) {
+                c->tc_first[b][dir] = (int)tj.size();
+                for (int f = 0; f < N_D1; f++) addt(c->U[b] + (long long)f * P, d1f + ((long long)f * 3 + dir) * P, 0);
+                for (int v = 0; v < 8; v++) addt(c->flux + ((long long)dir * 8 + v) * P, dFf + (long long)v * P, dir > 0);
+            }
+        const int vars2[N_D2] = {0, 1, 2, 3, 4, 5, 6, 17, 18, 19, 20};
+        c->tc_second[0] = (int)tj.size();
+        for (int q = 0; q < N_D2; q++) addt(d1f + ((long long)vars2[q] * 3 + 0) * P, d2f + ((long long)q * 6 + 0) * P, 0);
+        c->tc_second[1] = (int)tj.size();
+        for (int q = 0; q < N_D2; q++) {
+            addt(d1f + ((long long)vars2[q] * 3 + 0) * P, d2f + ((long long)q * 6 + 1) * P, 0);
+            addt(d1f + ((long long)vars2[q] * 3 + 1) * P, d2f + ((long long)q * 6 + 3) * P, 0);
+        }
+        c->tc_second[2] = (int)tj.size();
+        for (int q = 0; q < N_D2; q++) {
+            addt(d1f + ((long long)vars2[q] * 3 + 0) * P, d2f + ((long long)q * 6 + 2) * P, 0);
+            addt(d1f + ((long long)vars2[q] * 3 + 1) * P, d2f + ((long long)q * 6 + 4) * P, 0);
+            addt(d1f + ((long long)vars2[q] * 3 + 2) * P, d2f + ((long long)q * 6 + 5) * P, 0);
+        }
+        if (cudaMalloc(&c->tcjobs, tj.size() * sizeof(TcJob)) != cudaSuccess ||
+            cudaMalloc(&c->tc_err, sizeof(int)) != cudaSuccess ||
+            cudaMemcpyAsync(c->tcjobs, tj.data(), tj.size() * sizeof(TcJob), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(c->tc_err, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+            free_ctx(c);
+            return GRMHD_ENOMEM;
+        }
+    }
     *out = c;
     return GRMHD_OK;
 }
@@ -384,6 +445,17 @@ static cudaError_t contract(grmhd_ctx* c, int dir, int filter, const DerivJob* j
 }
 
 static int enqueue_first_derivs(grmhd_ctx* c, int b) {
+    if (c->opts.precision > 0) {
+        const int tf32 = c->opts.precision == 2;
+        for (int dir = 0; dir < 3; dir++) {
+            CK(launch_contract_tc(dir, 0, c->d, c->tcjobs + c->tc_first[b][dir], N_D1 + 8, c->tc_img[dir], tf32,
+                                  c->r_scale, c->tc_err, c->stream));
+            c->launches_tmp++;
+        }
+        CK(launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d1), 3 * c->d.P, N_D1, c->stream));
+        c->launches_tmp++;
+        return GRMHD_OK;
+    }
     for (int dir = 0; dir < 3; dir++) {
         CK(contract(c, dir, 0, c->jobs + c->job_first[b][dir], c->job_first_n));
         c->launches_tmp++;
@@ -394,6 +466,18 @@ static int enqueue_first_derivs(grmhd_ctx* c, int b) {
 }
 
 static int enqueue_second_derivs(grmhd_ctx* c) {
+    if (c->opts.precision > 0) {
+        const int tf32 = c->opts.precision == 2;
+        const int n[3] = {N_D2, 2 * N_D2, 3 * N_D2};
+        for (int dir = 0; dir < 3; dir++) {
+            CK(launch_contract_tc(dir, 1, c->d, c->tcjobs + c->tc_second[dir], n[dir], c->tc_img[dir], tf32,
+                                  c->r_scale, c->tc_err, c->stream));
+            c->launches_tmp++;
+        }
+        CK(launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d2), 6 * c->d.P, N_D2, c->stream));
+        c->launches_tmp++;
+        return GRMHD_OK;
+    }
     for (int dir = 0; dir < 3; dir++) {
         CK(contract(c, dir, 0, c->jobs + c->job_second[dir], c->job_second_n[dir]));
         c->launches_tmp++;
@@ -414,7 +498,7 @@ static int enqueue_stage(grmhd_ctx* c, int b, RKCoef co, double* out) {
         if (st) return st;
     }
     CK(launch_rhs(c->d, c->pp, c->U[0], c->U[b], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
-                  c->divF, c->r_scale, c->dt, co, out, c->acc, c->stream));
+                  c->divF, c->opts.precision > 0, c->r_scale, c->dt, co, out, c->acc, c->stream));
     c->launches_tmp++;
     return GRMHD_OK;
 }
@@ -618,6 +702,14 @@ extern "C" int grmhd_step(grmhd_ctx* c, double dt, int nsteps, double* dt_used) 
     CK(cudaMemcpyAsync(&dtv, c->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (dt_used) *dt_used = dtv;
+    if (c->tc_err) {
+        int te = 0;
+        CK(cudaMemcpy(&te, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (te) {
+            CK(cudaMemset(c->tc_err, 0, sizeof(int)));
+            return set_err(c, GRMHD_ETIMEOUT, "a tensor-core contraction wait timed out");
+        }
+    }
     if (flag) return set_err(c, GRMHD_ENAN, "non-finite value in the evolved state");
     return GRMHD_OK;
 }
@@ -696,7 +788,8 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
                 fl[k] = contraction_flops(c, dir, 0) * c->job_second_n[dir];
             } else if (k == 8) e = launch_iface_avg(c->d, c->d2, 6 * P, N_D2, c->stream);
             else if (k == 9) e = launch_rhs(c->d, c->pp, c->U[0], c->U[1], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
-                                            c->divF, c->r_scale, c->dt, co, c->scratch, c->acc, c->stream);
+                                            c->divF, c->opts.precision > 0, c->r_scale, c->dt, co, c->scratch,
+                                            c->acc, c->stream);
             else {
                 int dir = k - 10;
                 // filter contraction of all 32 variables of U[1] (scratch <-> U[1] chain)

@@ -51,16 +51,31 @@ struct DerivJob {
     int pad;
 };
 
+// tensor-core contraction job: src is double (state, fluxes) or float (first derivatives)
+struct TcJob {
+    const void* src;
+    float* dst;
+    int accumulate;
+    int pad;
+};
+
 // ---- kernel launchers (defined in kernels_*.cu); all return cudaGetLastError()
+// one-time function-attribute setup (shared-memory opt-in); call outside stream capture
+cudaError_t kernels_init();
 cudaError_t launch_prep(const Dims& d, const PhysParams& pp, const double* U, double* prim,
                         double* flux, double* tmn, double* lam, unsigned long long* nfail,
                         cudaStream_t s);
 struct RKCoef { double a, b, c, w; int acc_mode; };  // out = a U0 + b Us + c dt L (+acc)
+// d1, d2, divF are double (FP64 mode) or float (deriv_fp32 = 1, mixed modes)
 cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, const double* Us,
                        const double* prim, const double* flux, const double* tmn,
-                       const double* lam, const double* d1, const double* d2,
-                       const double* divF, const double* r_scale_dev, const double* dt_dev,
-                       RKCoef co, double* out, double* acc, cudaStream_t s);
+                       const double* lam, const void* d1, const void* d2,
+                       const void* divF, int deriv_fp32, const double* r_scale_dev,
+                       const double* dt_dev, RKCoef co, double* out, double* acc, cudaStream_t s);
+// tensor-core contraction (kernels_tc.cu); op_img in the kernel's shared-memory layout
+cudaError_t launch_contract_tc(int dir, int in_fp32, const Dims& d, const TcJob* jobs, int njobs,
+                               const uint8_t* op_img, int tf32, const double* r_scale, int* err,
+                               cudaStream_t s);
 cudaError_t launch_deriv(int dir, const Dims& d, const DerivJob* jobs_dev, int njobs,
                          const double* mat_dev, const double* r_scale_dev, cudaStream_t s);
 // reflection-split contraction (kernels_eo.cu): cudaErrorNotSupported when N has no
@@ -71,6 +86,8 @@ cudaError_t launch_deriv_eo(int dir, const Dims& d, const DerivJob* jobs, int nj
                             cudaStream_t s);
 cudaError_t launch_iface_avg(const Dims& d, double* base, long long field_stride, int nfields,
                              cudaStream_t s);
+cudaError_t launch_iface_avg_f(const Dims& d, float* base, long long field_stride, int nfields,
+                               cudaStream_t s);
 cudaError_t launch_cfl(const Dims& d, const double* U, const double* hmin_dev, double cfl,
                        double* dt_dev, unsigned int* lam_bits, cudaStream_t s);
 cudaError_t launch_diag(const Dims& d, const PhysParams& pp, const double* U,

@@ -10,6 +10,8 @@
 #include "host_ops.h"
 
 #include <cmath>
+#include <cstdint>
+#include <cstring>
 #include <vector>
 
 namespace gk {
@@ -158,6 +160,53 @@ std::vector<double> split_operator(const std::vector<double>& M, int N, int kind
     for (int f = 0; f < nf; f++)      // G: fixed-point block
         for (int g = 0; g < nf; g++) out.push_back(m(fx[f], fx[g]));
     return out;
+}
+
+// ---------------------------------------------------------------- tensor-core images
+static uint16_t bf16_rne(double x) {
+    float f = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+static double bf16_val(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return (double)f;
+}
+static uint32_t tf32_rne(double x) {
+    float f = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0xFFFu + ((u >> 13) & 1u);
+    return u & ~0x1FFFu;
+}
+
+std::vector<uint8_t> tc_operator_image(const std::vector<double>& D, int N, int tf32) {
+    const int Kp = (N + 15) / 16 * 16, Np = Kp;
+    const int es = tf32 ? 4 : 2, per = 16 / es, kcores = Kp * es / 16, nsl = tf32 ? 1 : 3;
+    const size_t slice = (size_t)Np * Kp * es;
+    std::vector<uint8_t> img(slice * nsl, 0);
+    for (int n = 0; n < N; n++)
+        for (int k = 0; k < N; k++) {
+            size_t off = (size_t)((n >> 3) * kcores + k / per) * 128 + (n & 7) * 16 + (k % per) * es;
+            double x = D[(size_t)n * N + k];
+            if (tf32) {
+                uint32_t u = tf32_rne(x);
+                std::memcpy(&img[off], &u, 4);
+            } else {
+                uint16_t b1 = bf16_rne(x);
+                double r1 = x - bf16_val(b1);
+                uint16_t b2 = bf16_rne(r1);
+                uint16_t b3 = bf16_rne(r1 - bf16_val(b2));
+                std::memcpy(&img[off], &b1, 2);
+                std::memcpy(&img[slice + off], &b2, 2);
+                std::memcpy(&img[2 * slice + off], &b3, 2);
+            }
+        }
+    return img;
 }
 
 std::vector<double> circulant(const std::vector<double>& row) {

@@ -1,5 +1,6 @@
 // Host-side operators and initial data (see host_ops.cpp).
 #pragma once
+#include <cstdint>
 #include <vector>
 
 namespace gk {
@@ -15,6 +16,9 @@ std::vector<double> quad_weights(int n, bool lobatto);
 // kind 0 Chebyshev node set, 1 Fourier node set
 std::vector<double> split_operator(const std::vector<double>& M, int N, int kind);
 std::vector<double> circulant(const std::vector<double>& row);
+// operator D (N x N, row = output node) in the tensor-core kernel's shared-memory image:
+// K-major core-matrix layout padded to 16 in both dims; 3 BF16 slices or 1 TF32 copy
+std::vector<uint8_t> tc_operator_image(const std::vector<double>& D, int N, int tf32);
 // BSSN variables 0..23 of the Kerr-Schild slice at (r, theta)
 void ks_bssn_point(double M, double a, double r, double th, double out[24]);
 void prim_to_cons_point(double rho, double p, const double v_u[3], const double B_u[3],

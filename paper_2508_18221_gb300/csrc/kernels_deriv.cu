@@ -62,19 +62,27 @@ cudaError_t launch_deriv(int dir, const Dims& d, const DerivJob* jobs_dev, int n
     dim3 grid((unsigned)nb, (unsigned)njobs);
     const int N = dir == 0 ? d.Nr : (dir == 1 ? d.Nt : d.Np);
     size_t sm = (size_t)(dir == 2 ? N : N * N) * sizeof(double);
-    if (sm > 48 * 1024) {
-        cudaError_t e = dir == 0 ? cudaFuncSetAttribute(k_deriv<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                                 : cudaFuncSetAttribute(k_deriv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-    }
     if (dir == 0) k_deriv<0><<<grid, bs, sm, s>>>(d, jobs_dev, mat_dev, r_scale_dev);
     else if (dir == 1) k_deriv<1><<<grid, bs, sm, s>>>(d, jobs_dev, mat_dev, r_scale_dev);
     else k_deriv<2><<<grid, bs, sm, s>>>(d, jobs_dev, mat_dev, r_scale_dev);
     return cudaGetLastError();
 }
 
+cudaError_t eo_init();
+cudaError_t tc_init();
+
+cudaError_t kernels_init() {
+    cudaError_t e;
+    // dense contractions: theta matrices up to 128 x 128 doubles (128 KB)
+    if ((e = cudaFuncSetAttribute(k_deriv<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * 8)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_deriv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8)) != cudaSuccess) return e;
+    if ((e = eo_init()) != cudaSuccess) return e;
+    return tc_init();
+}
+
 // Replace both copies of each duplicated interface node by their mean.
-__global__ void k_iface_avg(Dims d, double* base, long long fstride, int nfields) {
+template <typename T>
+__global__ void k_iface_avg(Dims d, T* base, long long fstride, int nfields) {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long nif = (long long)(d.E - 1) * d.NtNp;
     if (t >= nif * nfields) return;
@@ -82,10 +90,10 @@ __global__ void k_iface_avg(Dims d, double* base, long long fstride, int nfields
     long long r = t % nif;
     int e = (int)(r / d.NtNp);
     long long kl = r % d.NtNp;
-    double* u = base + f * fstride;
+    T* u = base + f * fstride;
     long long pl = (long long)e * d.elem + (long long)(d.Nr - 1) * d.NtNp + kl;
     long long pr = pl + d.NtNp;
-    double m = 0.5 * (u[pl] + u[pr]);
+    T m = (T)0.5 * (u[pl] + u[pr]);
     u[pl] = m;
     u[pr] = m;
 }
@@ -95,7 +103,16 @@ cudaError_t launch_iface_avg(const Dims& d, double* base, long long fstride, int
     if (d.E < 2 || nfields <= 0) return cudaSuccess;
     long long n = (long long)(d.E - 1) * d.NtNp * nfields;
     int bs = 256;
-    k_iface_avg<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(d, base, fstride, nfields);
+    k_iface_avg<double><<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(d, base, fstride, nfields);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iface_avg_f(const Dims& d, float* base, long long fstride, int nfields,
+                               cudaStream_t s) {
+    if (d.E < 2 || nfields <= 0) return cudaSuccess;
+    long long n = (long long)(d.E - 1) * d.NtNp * nfields;
+    int bs = 256;
+    k_iface_avg<float><<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(d, base, fstride, nfields);
     return cudaGetLastError();
 }
 

@@ -118,11 +118,6 @@ static cudaError_t launch_one(const Dims& d, const DerivJob* jobs, int njobs, co
     long long nb = (nlines + bs - 1) / bs;
     if (nb > 65535LL * 16) nb = 65535LL * 16;
     size_t sm = (size_t)S::SIZE * sizeof(double);
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_deriv_eo<DIR, KIND, N>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-    }
     k_deriv_eo<DIR, KIND, N><<<dim3((unsigned)nb, (unsigned)njobs), bs, sm, s>>>(d, jobs, op, sign, r_scale);
     return cudaGetLastError();
 }
@@ -148,6 +143,12 @@ static cudaError_t dispatch(int N, const Dims& d, const DerivJob* jobs, int njob
             default: return cudaErrorNotSupported;
         }
     }
+}
+
+cudaError_t eo_init() {
+    // the only instance above the default 48 KB: Fourier N = 128 (65.5 KB)
+    return cudaFuncSetAttribute(k_deriv_eo<2, 1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(Split<1, 128>::SIZE * sizeof(double)));
 }
 
 bool eo_supported(int dir, int N) {

@@ -289,15 +289,16 @@ __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const doubl
 // indices of the 6 second-derivative pairs
 __device__ __constant__ int c_pair[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
 
+template <typename DT>
 __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double* __restrict__ U0,
                                              const double* __restrict__ Us,
                                              const double* __restrict__ prim,
                                              const double* __restrict__ flux,
                                              const double* __restrict__ tmn,
                                              const double* __restrict__ lam,
-                                             const double* __restrict__ d1,
-                                             const double* __restrict__ d2,
-                                             const double* __restrict__ divF,
+                                             const DT* __restrict__ d1,
+                                             const DT* __restrict__ d2,
+                                             const DT* __restrict__ divF,
                                              const double* __restrict__ r_scale,
                                              const double* __restrict__ dt_dev, RKCoef co,
                                              double* __restrict__ out, double* __restrict__ acc) {
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
     inv3sym(gt, gti);
 
     // first derivatives: field f, direction dd -> d1[(f*3+dd)*P + p]
-#define D1(f, dd) d1[((long long)(f) * 3 + (dd)) * P + p]
+#define D1(f, dd) ((double)d1[((long long)(f) * 3 + (dd)) * P + p])
     double dgt[3][3][3], dAt[3][3][3], dphi[3], dK[3], dGam[3][3], dal[3], dbe[3][3];
     for (int k = 0; k < 3; k++) {
         for (int i = 0; i < 3; i++)
@@ -383,7 +384,7 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
                 }
             double t0db = T0_d[0] * dbe[jd][0] + T0_d[1] * dbe[jd][1] + T0_d[2] * dbe[jd][2];
             double SS = T00 * (0.5 * bbdg - alpha * dal[jd]) + t0dg + t0db + 0.5 * tdg;
-            rhs[V_S + jd] = -divF[(1 + jd) * P + p] + asg * SS;
+            rhs[V_S + jd] = -(double)divF[(1 + jd) * P + p] + asg * SS;
         }
         double bbK = 0.0, TK = 0.0, t0 = 0.0;
         for (int i = 0; i < 3; i++) {
@@ -397,9 +398,9 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
         }
         double bda = beta[0] * dal[0] + beta[1] * dal[1] + beta[2] * dal[2];
         double Stau = T00 * (bbK - bda) + t0 + TK;
-        rhs[V_D] = -divF[0 * P + p];
-        rhs[V_TAU] = -divF[4 * P + p] + asg * Stau;
-        for (int k = 0; k < 3; k++) rhs[V_B + k] = -divF[(5 + k) * P + p];
+        rhs[V_D] = -(double)divF[0 * P + p];
+        rhs[V_TAU] = -(double)divF[4 * P + p] + asg * Stau;
+        for (int k = 0; k < 3; k++) rhs[V_B + k] = -(double)divF[(5 + k) * P + p];
 
         // interface penalty (Rusanov flux, strong form) at duplicated element-end nodes
         const long long shell = d.NtNp;
@@ -448,7 +449,7 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
                 for (int j = 0; j < 3; j++) Str += gi[i][j] * Sij[i][j];
 
             // -------------------------------------------------------- BSSN
-#define D2(f, q) d2[((long long)(f) * 6 + (q)) * P + p]
+#define D2(f, q) ((double)d2[((long long)(f) * 6 + (q)) * P + p])
             // Christoffels of gammatilde: lower Cl[k][i][j] = Gamma_{k ij}, upper Cu[k][i][j]
             double Cl[3][3][3], Cu[3][3][3];
             for (int k = 0; k < 3; k++)
@@ -654,13 +655,19 @@ cudaError_t launch_prep(const Dims& d, const PhysParams& pp, const double* U, do
 
 cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, const double* Us,
                        const double* prim, const double* flux, const double* tmn,
-                       const double* lam, const double* d1, const double* d2,
-                       const double* divF, const double* r_scale_dev, const double* dt_dev,
-                       RKCoef co, double* out, double* acc, cudaStream_t s) {
+                       const double* lam, const void* d1, const void* d2,
+                       const void* divF, int deriv_fp32, const double* r_scale_dev,
+                       const double* dt_dev, RKCoef co, double* out, double* acc, cudaStream_t s) {
     int bs = 128;
     long long nb = (d.P + bs - 1) / bs;
-    k_rhs<<<(unsigned)nb, bs, 0, s>>>(d, pp, U0, Us, prim, flux, tmn, lam, d1, d2, divF,
-                                      r_scale_dev, dt_dev, co, out, acc);
+    if (deriv_fp32)
+        k_rhs<float><<<(unsigned)nb, bs, 0, s>>>(d, pp, U0, Us, prim, flux, tmn, lam, (const float*)d1,
+                                                 (const float*)d2, (const float*)divF, r_scale_dev, dt_dev,
+                                                 co, out, acc);
+    else
+        k_rhs<double><<<(unsigned)nb, bs, 0, s>>>(d, pp, U0, Us, prim, flux, tmn, lam, (const double*)d1,
+                                                  (const double*)d2, (const double*)divF, r_scale_dev,
+                                                  dt_dev, co, out, acc);
     return cudaGetLastError();
 }
 

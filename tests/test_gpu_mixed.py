@@ -1,0 +1,143 @@
+"""Mixed-precision modes on the GPU: derivative contractions on the tensor cores
+(precision 1: split BF16 x3 with FP32 accumulation; precision 2: TF32), primitive
+recovery, metric, RK sums and the filter in FP64.
+
+Tolerances follow from the arithmetic: the split-BF16 contraction keeps about 24
+significant bits (an FP32 contraction: relative error ~ K 2^-24 ~ 1e-6 of |D||u|), TF32
+keeps 11 (~5e-4 per contraction, compounded by the second derivatives taken from TF32
+first derivatives and by ||D|| ~ N^2: measured 1.2e-2); the right-hand side inherits that
+relative to the scale s_v of the FP64 parity test (max |rhs_v|, state / dx_min over the
+tensor).  n steps of size dt move the state by at most n dt tol_rhs / dx_min relative."""
+import os
+import numpy as np
+import pytest
+
+from oracle import solver as so
+from workloads import config
+
+from test_gpu_parity import _ctx, _oracle, _gpu_rhs, assert_parity, pkg  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+TOL_RHS = {1: 2e-6, 2: 5e-2}
+
+
+@pytest.mark.parametrize("precision,tol", [(1, TOL_RHS[1]), (2, TOL_RHS[2])])
+@pytest.mark.parametrize("name", ["c1", "c1:ragged"])
+def test_mixed_rhs_against_oracle(pkg, precision, tol, name):
+    cfg = config("c1") if name == "c1" else config("c1", n_elem=3, n_r=9, n_theta=11, n_phi=6)
+    g, p, U = _oracle(cfg)
+    grid, phys, opts = pkg.make_structs(cfg, precision=precision)
+    import torch
+    ctx = pkg.Context(grid, phys, opts, torch.cuda.current_stream().cuda_stream)
+    R = _gpu_rhs(pkg, ctx, U)
+    Rref = so.rhs(U, g, p)
+    worst = assert_parity(R, Rref, f"mixed {precision} rhs {name}", tol=tol, U=U, g=g)
+    assert worst > 1e-12          # the tensor-core path really ran (not the FP64 one)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_step_close_to_fp64(pkg, precision):
+    """10 SSP-RK3 steps: mixed vs FP64 GPU (the FP64 path is tied to the oracle by the
+    parity tests); the state difference stays at the contraction accuracy times dt."""
+    import torch
+    cfg = config("c1", n_elem=3, n_r=9, n_theta=10, n_phi=8)
+    g, p, U = _oracle(cfg)
+    out = []
+    for prec in (0, precision):
+        grid, phys, opts = pkg.make_structs(cfg, precision=prec)
+        ctx = pkg.Context(grid, phys, opts, torch.cuda.current_stream().cuda_stream)
+        ctx.set_state(torch.from_numpy(U.reshape(-1).copy()).cuda(), True)
+        ctx.step(2e-3, 10)
+        s = np.empty(U.size)
+        ctx.get_state(s, False)
+        out.append(s.reshape(U.shape))
+        ctx.close()
+    from test_gpu_parity import min_spacing
+    tol = 10 * 2e-3 * TOL_RHS[precision] / min_spacing(g)
+    assert_parity(out[1], out[0], f"10 steps precision {precision}", tol=tol, U=U)
+
+
+def truncation_estimate(U, g):
+    """Per variable: the spectral truncation level of the state, taken as the largest
+    modal coefficient at the resolution limit the post-step filter sets (the first mode it
+    damps by about one half: Chebyshev index 2(N-1)/3 in r per element and in theta,
+    Fourier |k| = N/3 in phi), over all lines, relative to max |u|."""
+    from oracle import spectral as sp
+    est = np.zeros(U.shape[0])
+    nr, nt, npf = U.shape[2], U.shape[3], U.shape[4]
+    kr, kt, kp = 2 * (nr - 1) // 3, 2 * (nt - 1) // 3, npf // 3
+    for v in range(U.shape[0]):
+        u = U[v]
+        sc = np.abs(u).max()
+        if sc == 0:
+            continue
+        cr = np.stack([sp.cheb_coeffs(u[e], g.xr, axis=0) for e in range(u.shape[0])])
+        ct = sp.cheb_coeffs(u, g.xt, axis=2)
+        uh = np.abs(sp.dft(u, axis=3)) / npf
+        tr = max(np.abs(cr[:, kr]).max(), np.abs(ct[:, :, kt]).max(), 2 * uh[..., kp].max())
+        est[v] = tr / sc
+    return est
+
+
+@pytest.mark.slow
+def test_precision_variant_report(pkg, capsys):
+    """The 2-element 12 x 12 x 16 instance: relative L2 / Linf errors of every evolved
+    variable against the FP64 oracle after 1 and 100 SSP-RK3 steps, for the FP64,
+    split-BF16 x3 and TF32 paths.  The split-BF16 form must stay within the spectral
+    truncation level of the state after 100 steps, per tensor (relative L2 over the
+    tensor's components against the tensor's truncation level); TF32 is reported."""
+    import json
+    import torch
+    from test_gpu_parity import TENSORS
+    cfg = config("c3")
+    g, p, U = _oracle(cfg)
+    dt = so.cfl_dt(U, g, p)
+    ref = {1: so.rk_step(U, dt, g, p)}
+    V = ref[1]
+    for _ in range(99):
+        V = so.rk_step(V, dt, g, p)
+    ref[100] = V
+    trunc = truncation_estimate(ref[100], g)
+    report = {"dt": dt, "truncation": trunc.tolist(), "tensors": [list(t) for t in TENSORS]}
+    for prec in (0, 1, 2):
+        grid, phys, opts = pkg.make_structs(cfg, precision=prec)
+        ctx = pkg.Context(grid, phys, opts, torch.cuda.current_stream().cuda_stream)
+        for n in (1, 100):
+            ctx.set_state(torch.from_numpy(U.reshape(-1).copy()).cuda(), True)
+            ctx.step(dt, n)
+            got = np.empty(U.size)
+            ctx.get_state(got, False)
+            got = got.reshape(U.shape)
+            l2, linf, l2t, trt = [], [], [], []
+            for v in range(32):
+                r = ref[n][v]
+                d = got[v] - r
+                sc2 = np.sqrt(np.mean(r * r))
+                scm = np.abs(r).max()
+                l2.append(float(np.sqrt(np.mean(d * d)) / sc2) if sc2 > 0 else float(np.sqrt(np.mean(d * d))))
+                linf.append(float(np.abs(d).max() / scm) if scm > 0 else float(np.abs(d).max()))
+            for t in TENSORS:
+                t = list(t)
+                num = np.sqrt(sum(np.sum((got[v] - ref[n][v]) ** 2) for v in t))
+                den = np.sqrt(sum(np.sum(ref[n][v] ** 2) for v in t))
+                l2t.append(float(num / den) if den > 0 else float(num))
+                mx = max(np.abs(ref[n][v]).max() for v in t)
+                trt.append(float(max(trunc[v] * np.abs(ref[n][v]).max() for v in t) / mx) if mx > 0 else 0.0)
+            report[f"p{prec}_n{n}"] = {"l2": l2, "linf": linf, "l2_tensor": l2t, "trunc_tensor": trt}
+        ctx.close()
+    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(out):
+        with open(os.path.join(out, "precision_report_c3.json"), "w") as fh:
+            json.dump(report, fh)
+    with capsys.disabled():
+        for key in ("p0_n1", "p1_n1", "p2_n1", "p0_n100", "p1_n100", "p2_n100"):
+            print(key, "max L2", max(report[key]["l2_tensor"]), "max Linf", max(report[key]["linf"]))
+    for n in (1, 100):
+        assert max(report[f"p0_n{n}"]["l2"]) <= 1e-9
+    r = report["p1_n100"]
+    for i, t in enumerate(TENSORS):
+        if r["trunc_tensor"][i] > 0:
+            assert r["l2_tensor"][i] <= r["trunc_tensor"][i], (list(t), r["l2_tensor"][i], r["trunc_tensor"][i])
