@@ -228,7 +228,7 @@ def run_gpu(args):
     # times per filter, and takes most of a step; its roofline is the algorithmic FP64
     # work of all its launches in one step over their summed time.
     ctx.set_state(U0, True)
-    kt = ctx.kernel_times(reps=5)
+    kt = {k: v[:2] for k, v in ctx.kernel_times(reps=5).items()}
     per_step = {k: (1 if k.startswith("filter") else RHS_PER_STEP) for k in kt}
     contr = [k for k in kt if kt[k][1] > 0]
     t_contr = sum(kt[k][0] * per_step[k] for k in contr)

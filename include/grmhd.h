@@ -166,12 +166,16 @@ long long grmhd_launch_count(const grmhd_ctx* ctx);
  * 0 prep (metric + primitive recovery + fluxes), 1-3 first-derivative contractions
  * r/theta/phi, 4 interface mean of d_r, 5-7 second-derivative contractions r/theta/phi,
  * 8 interface mean of d_rr, 9 rhs (BSSN + Valencia + penalty + RK), 10-12 filter
- * contractions r/theta/phi.  flops_out (may be NULL) receives the algorithmic FP64
- * flops of one launch of each class for the contractions (2 N per output node for a
- * dense row; about N per output node for the reflection-split form, counted exactly)
- * and 0 for the others.  The state is left unchanged. */
+ * contractions r/theta/phi.  For the contraction classes, flops_out (may be NULL)
+ * receives the algorithmic flops of one launch (FP64 modes: 2 N per output node for a
+ * dense row, about N for the reflection-split form, counted exactly; mixed modes: the
+ * tensor-core MMA flops of the padded tiles and slice products) and bytes_out (may be
+ * NULL) the algorithmic HBM bytes (each source element read once, each result written
+ * once, accumulated results read too); 0 for the other classes.  The state is left
+ * unchanged. */
 enum { GRMHD_NKT = 13 };
-int grmhd_kernel_times(grmhd_ctx* ctx, int reps, double* ms_out, double* flops_out, int n);
+int grmhd_kernel_times(grmhd_ctx* ctx, int reps, double* ms_out, double* flops_out,
+                       double* bytes_out, int n);
 
 /* Independent instances advanced together (one context per instance, all sharing one
  * stream; the step of every instance is captured into one CUDA graph).  Instances may

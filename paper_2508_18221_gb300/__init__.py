@@ -55,7 +55,7 @@ SIGNATURES = {
     "grmhd_cfl_dt": (C.c_int, [_P, _D]),
     "grmhd_diag": (C.c_int, [_P, _D]),
     "grmhd_launch_count": (C.c_longlong, [_P]),
-    "grmhd_kernel_times": (C.c_int, [_P, C.c_int, _D, _D, C.c_int]),
+    "grmhd_kernel_times": (C.c_int, [_P, C.c_int, _D, _D, _D, C.c_int]),
     "grmhd_batch_create": (C.c_int, [C.c_int, C.POINTER(Grid), C.POINTER(Physics),
                                      C.POINTER(Opts), _P, C.POINTER(_P)]),
     "grmhd_batch_instance": (_P, [_P, C.c_int]),
@@ -192,12 +192,13 @@ class Context:
                       "d2_phi", "iface_d2", "rhs", "filter_r", "filter_theta", "filter_phi")
 
     def kernel_times(self, reps: int = 5):
-        """{class: (ms per launch, algorithmic FP64 flops per launch)}"""
+        """{class: (ms per launch, algorithmic flops per launch, algorithmic bytes)}"""
         n = len(self.KERNEL_CLASSES)
         ms = (C.c_double * n)()
         fl = (C.c_double * n)()
-        self._chk(self.lib.grmhd_kernel_times(self.h, int(reps), ms, fl, n))
-        return {k: (ms[i], fl[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
+        by = (C.c_double * n)()
+        self._chk(self.lib.grmhd_kernel_times(self.h, int(reps), ms, fl, by, n))
+        return {k: (ms[i], fl[i], by[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
 
     def debug_deriv(self, src, dst, nfields: int, direction: int):
         self._chk(self.lib.grmhd_debug_deriv(self.h, _ptr(src), _ptr(dst), nfields, direction))

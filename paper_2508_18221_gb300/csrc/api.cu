@@ -758,10 +758,22 @@ static double contraction_flops(const grmhd_ctx* c, int dir, int filter) {
     return per_line * P / N;
 }
 
-extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double* flops_out, int n) {
+// Tensor-core contraction of one field: 128-line tiles x (Np x Kp) x slice products x 2.
+static double tc_flops(const grmhd_ctx* c, int dir) {
+    const int Ns[3] = {c->d.Nr, c->d.Nt, c->d.Np};
+    const int N = Ns[dir];
+    const double K = (N + 15) / 16 * 16;
+    const double lines = dir == 0 ? (double)c->d.E * c->d.NtNp : (dir == 1 ? (double)c->d.E * c->d.Nr * c->d.Np : (double)c->d.P / N);
+    const double tiles = std::ceil(lines / 128.0);
+    return tiles * 128.0 * K * K * 2.0 * (c->opts.precision == 2 ? 1 : 6);
+}
+
+extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double* flops_out,
+                                  double* bytes_out, int n) {
     if (!c || !ms_out || reps < 1 || n < 1 || n > GRMHD_NKT) return GRMHD_EINVAL;
     const long long P = c->d.P;
-    double ms[GRMHD_NKT] = {0}, fl[GRMHD_NKT] = {0};
+    const int mixed = c->opts.precision > 0, tf32 = c->opts.precision == 2;
+    double ms[GRMHD_NKT] = {0}, fl[GRMHD_NKT] = {0}, by[GRMHD_NKT] = {0};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -779,14 +791,36 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
             if (k == 0) e = launch_prep(c->d, c->pp, c->U[1], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream);
             else if (k >= 1 && k <= 3) {
                 int dir = k - 1;
-                e = contract(c, dir, 0, c->jobs + c->job_first[1][dir], c->job_first_n);
-                fl[k] = contraction_flops(c, dir, 0) * c->job_first_n;
-            } else if (k == 4) e = launch_iface_avg(c->d, c->d1, 3 * P, N_D1, c->stream);
-            else if (k >= 5 && k <= 7) {
+                if (mixed) {
+                    e = launch_contract_tc(dir, 0, c->d, c->tcjobs + c->tc_first[1][dir], N_D1 + 8, c->tc_img[dir], tf32,
+                                           c->r_scale, c->tc_err, c->stream);
+                    fl[k] = tc_flops(c, dir) * (N_D1 + 8);
+                    by[k] = (double)P * (N_D1 + 8) * (8.0 + 4.0) + (dir > 0 ? 8.0 * 4.0 * P : 0.0);
+                } else {
+                    e = contract(c, dir, 0, c->jobs + c->job_first[1][dir], c->job_first_n);
+                    fl[k] = contraction_flops(c, dir, 0) * c->job_first_n;
+                    by[k] = (double)P * c->job_first_n * 16.0 + (dir > 0 ? 8.0 * 8.0 * P : 0.0);
+                }
+            } else if (k == 4) {
+                e = mixed ? launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d1), 3 * P, N_D1, c->stream)
+                          : launch_iface_avg(c->d, c->d1, 3 * P, N_D1, c->stream);
+            } else if (k >= 5 && k <= 7) {
                 int dir = k - 5;
-                e = contract(c, dir, 0, c->jobs + c->job_second[dir], c->job_second_n[dir]);
-                fl[k] = contraction_flops(c, dir, 0) * c->job_second_n[dir];
-            } else if (k == 8) e = launch_iface_avg(c->d, c->d2, 6 * P, N_D2, c->stream);
+                const int nj[3] = {N_D2, 2 * N_D2, 3 * N_D2};
+                if (mixed) {
+                    e = launch_contract_tc(dir, 1, c->d, c->tcjobs + c->tc_second[dir], nj[dir], c->tc_img[dir], tf32,
+                                           c->r_scale, c->tc_err, c->stream);
+                    fl[k] = tc_flops(c, dir) * nj[dir];
+                    by[k] = (double)P * nj[dir] * 8.0;
+                } else {
+                    e = contract(c, dir, 0, c->jobs + c->job_second[dir], c->job_second_n[dir]);
+                    fl[k] = contraction_flops(c, dir, 0) * c->job_second_n[dir];
+                    by[k] = (double)P * c->job_second_n[dir] * 16.0;
+                }
+            } else if (k == 8) {
+                e = mixed ? launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d2), 6 * P, N_D2, c->stream)
+                          : launch_iface_avg(c->d, c->d2, 6 * P, N_D2, c->stream);
+            }
             else if (k == 9) e = launch_rhs(c->d, c->pp, c->U[0], c->U[1], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
                                             c->divF, c->opts.precision > 0, c->r_scale, c->dt, co, c->scratch,
                                             c->acc, c->stream);
@@ -796,6 +830,7 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
                 e = contract(c, dir, 1, c->jobs + c->job_filter[1][dir][1], N_BSSN);
                 if (e == cudaSuccess) e = contract(c, dir, 1, c->jobs + c->job_filter[1][dir][0], 8);
                 fl[k] = contraction_flops(c, dir, 1) * NV;
+                by[k] = (double)P * NV * 16.0;
             }
             if (e != cudaSuccess) { st = set_err(c, GRMHD_ECUDA, "kernel_times: %s", cudaGetErrorString(e)); break; }
         }
@@ -813,6 +848,7 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
     for (int k = 0; k < n; k++) {
         ms_out[k] = ms[k];
         if (flops_out) flops_out[k] = fl[k];
+        if (bytes_out) bytes_out[k] = by[k];
     }
     return GRMHD_OK;
 }

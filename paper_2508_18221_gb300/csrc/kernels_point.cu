@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const doubl
 // indices of the 6 second-derivative pairs
 __device__ __constant__ int c_pair[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
 
-template <typename DT>
+template <typename DT, typename R>
 __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double* __restrict__ U0,
                                              const double* __restrict__ Us,
                                              const double* __restrict__ prim,
@@ -305,37 +305,49 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long P = d.P;
     if (p >= P) return;
-    const double PI = 3.141592653589793;
-    double rhs[NV];
+    const R PI = R(3.141592653589793);
+    R rhs[NV];
 
     // ------------------------------------------------------------ state and metric
-    double gt[3][3], At[3][3];
+    R gt[3][3], At[3][3];
+    double gt64[3][3];
     for (int i = 0; i < 3; i++)
         for (int j = i; j < 3; j++) {
-            gt[i][j] = gt[j][i] = Us[(V_GT + SI(i, j)) * P + p];
-            At[i][j] = At[j][i] = Us[(V_AT + SI(i, j)) * P + p];
+            gt64[i][j] = gt64[j][i] = Us[(V_GT + SI(i, j)) * P + p];
+            gt[i][j] = gt[j][i] = (R)gt64[i][j];
+            At[i][j] = At[j][i] = (R)Us[(V_AT + SI(i, j)) * P + p];
         }
     const double phi = Us[V_PHI * P + p];
-    const double K = Us[V_K * P + p];
-    const double alpha = Us[V_ALPHA * P + p];
-    double Gam[3], beta[3], Bg[3];
+    const R K = (R)Us[V_K * P + p];
+    const R alpha = (R)Us[V_ALPHA * P + p];
+    R Gam[3], beta[3], Bg[3];
     for (int i = 0; i < 3; i++) {
-        Gam[i] = Us[(V_GAM + i) * P + p];
-        beta[i] = Us[(V_BETA + i) * P + p];
-        Bg[i] = Us[(V_BG + i) * P + p];
+        Gam[i] = (R)Us[(V_GAM + i) * P + p];
+        beta[i] = (R)Us[(V_BETA + i) * P + p];
+        Bg[i] = (R)Us[(V_BG + i) * P + p];
     }
+    // conformal factor, physical metric, its determinant and inverse, conformal inverse:
+    // FP64 in every mode; the algebra below runs in R
     const double e4 = exp(4.0 * phi);
     const double e4m = 1.0 / e4;
-    double g[3][3], gi[3][3], gti[3][3];
+    const R e4r = (R)e4, e4mr = (R)e4m;
+    double g64[3][3], gi64[3][3], gti64[3][3];
     for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++) g[i][j] = e4 * gt[i][j];
-    double detg = inv3sym(g, gi);
-    double sqg = sqrt(detg);
-    inv3sym(gt, gti);
+        for (int j = 0; j < 3; j++) g64[i][j] = e4 * gt64[i][j];
+    double detg = inv3sym(g64, gi64);
+    const R sqg = (R)sqrt(detg);
+    inv3sym(gt64, gti64);
+    R g[3][3], gi[3][3], gti[3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            g[i][j] = (R)g64[i][j];
+            gi[i][j] = (R)gi64[i][j];
+            gti[i][j] = (R)gti64[i][j];
+        }
 
     // first derivatives: field f, direction dd -> d1[(f*3+dd)*P + p]
-#define D1(f, dd) ((double)d1[((long long)(f) * 3 + (dd)) * P + p])
-    double dgt[3][3][3], dAt[3][3][3], dphi[3], dK[3], dGam[3][3], dal[3], dbe[3][3];
+#define D1(f, dd) ((R)d1[((long long)(f) * 3 + (dd)) * P + p])
+    R dgt[3][3][3], dAt[3][3][3], dphi[3], dK[3], dGam[3][3], dal[3], dbe[3][3];
     for (int k = 0; k < 3; k++) {
         for (int i = 0; i < 3; i++)
             for (int j = i; j < 3; j++) {
@@ -354,53 +366,53 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
 
     // ------------------------------------------------------------ Valencia
     {
-        double T00 = tmn[0 * P + p];
-        double T0i[3] = {tmn[1 * P + p], tmn[2 * P + p], tmn[3 * P + p]};
-        double Tij[3][3];
+        R T00 = tmn[0 * P + p];
+        R T0i[3] = {tmn[1 * P + p], tmn[2 * P + p], tmn[3 * P + p]};
+        R Tij[3][3];
         Tij[0][0] = tmn[4 * P + p]; Tij[0][1] = Tij[1][0] = tmn[5 * P + p];
         Tij[0][2] = Tij[2][0] = tmn[6 * P + p]; Tij[1][1] = tmn[7 * P + p];
         Tij[1][2] = Tij[2][1] = tmn[8 * P + p]; Tij[2][2] = tmn[9 * P + p];
-        double beta_d[3];
+        R beta_d[3];
         for (int i = 0; i < 3; i++)
             beta_d[i] = g[i][0] * beta[0] + g[i][1] * beta[1] + g[i][2] * beta[2];
-        double T0_d[3];
+        R T0_d[3];
         for (int i = 0; i < 3; i++)
             T0_d[i] = beta_d[i] * T00 + g[i][0] * T0i[0] + g[i][1] * T0i[1] + g[i][2] * T0i[2];
-        double Kij[3][3];
+        R Kij[3][3];
         for (int i = 0; i < 3; i++)
-            for (int j = 0; j < 3; j++) Kij[i][j] = e4 * (At[i][j] + gt[i][j] * K / 3.0);
-        double asg = alpha * sqg;
+            for (int j = 0; j < 3; j++) Kij[i][j] = e4r * (At[i][j] + gt[i][j] * K / R(3.0));
+        R asg = alpha * sqg;
         for (int jd = 0; jd < 3; jd++) {
             // d_j gamma_kl = e^{4phi} (d_j gammatilde_kl + 4 gammatilde_kl d_j phi)
-            double dg[3][3];
+            R dg[3][3];
             for (int k = 0; k < 3; k++)
-                for (int l = 0; l < 3; l++) dg[k][l] = e4 * (dgt[jd][k][l] + 4.0 * gt[k][l] * dphi[jd]);
-            double bbdg = 0.0, t0dg = 0.0, tdg = 0.0;
+                for (int l = 0; l < 3; l++) dg[k][l] = e4r * (dgt[jd][k][l] + R(4.0) * gt[k][l] * dphi[jd]);
+            R bbdg = R(0.0), t0dg = R(0.0), tdg = R(0.0);
             for (int k = 0; k < 3; k++)
                 for (int l = 0; l < 3; l++) {
                     bbdg += beta[k] * beta[l] * dg[k][l];
                     t0dg += T0i[k] * beta[l] * dg[k][l];
                     tdg += Tij[k][l] * dg[k][l];
                 }
-            double t0db = T0_d[0] * dbe[jd][0] + T0_d[1] * dbe[jd][1] + T0_d[2] * dbe[jd][2];
-            double SS = T00 * (0.5 * bbdg - alpha * dal[jd]) + t0dg + t0db + 0.5 * tdg;
-            rhs[V_S + jd] = -(double)divF[(1 + jd) * P + p] + asg * SS;
+            R t0db = T0_d[0] * dbe[jd][0] + T0_d[1] * dbe[jd][1] + T0_d[2] * dbe[jd][2];
+            R SS = T00 * (R(0.5) * bbdg - alpha * dal[jd]) + t0dg + t0db + R(0.5) * tdg;
+            rhs[V_S + jd] = -(R)divF[(1 + jd) * P + p] + asg * SS;
         }
-        double bbK = 0.0, TK = 0.0, t0 = 0.0;
+        R bbK = R(0.0), TK = R(0.0), t0 = R(0.0);
         for (int i = 0; i < 3; i++) {
-            double bK = 0.0;
+            R bK = R(0.0);
             for (int j = 0; j < 3; j++) {
                 bbK += beta[i] * beta[j] * Kij[i][j];
                 TK += Tij[i][j] * Kij[i][j];
                 bK += beta[j] * Kij[i][j];
             }
-            t0 += T0i[i] * (2.0 * bK - dal[i]);
+            t0 += T0i[i] * (R(2.0) * bK - dal[i]);
         }
-        double bda = beta[0] * dal[0] + beta[1] * dal[1] + beta[2] * dal[2];
-        double Stau = T00 * (bbK - bda) + t0 + TK;
-        rhs[V_D] = -(double)divF[0 * P + p];
-        rhs[V_TAU] = -(double)divF[4 * P + p] + asg * Stau;
-        for (int k = 0; k < 3; k++) rhs[V_B + k] = -(double)divF[(5 + k) * P + p];
+        R bda = beta[0] * dal[0] + beta[1] * dal[1] + beta[2] * dal[2];
+        R Stau = T00 * (bbK - bda) + t0 + TK;
+        rhs[V_D] = -(R)divF[0 * P + p];
+        rhs[V_TAU] = -(R)divF[4 * P + p] + asg * Stau;
+        for (int k = 0; k < 3; k++) rhs[V_B + k] = -(R)divF[(5 + k) * P + p];
 
         // interface penalty (Rusanov flux, strong form) at duplicated element-end nodes
         const long long shell = d.NtNp;
@@ -421,27 +433,27 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
                 double UL = Us[(V_D + v) * P + pl];
                 double UR = Us[(V_D + v) * P + pr_];
                 double Fs = 0.5 * (FL + FR) - 0.5 * lmax * (UR - UL);
-                if (side > 0) rhs[V_D + v] += (FL - Fs) * fac;
-                else rhs[V_D + v] -= (FR - Fs) * fac;
+                if (side > 0) rhs[V_D + v] += (R)((FL - Fs) * fac);
+                else rhs[V_D + v] -= (R)((FR - Fs) * fac);
             }
         }
 
         // matter terms for BSSN: rho = alpha^2 T^00, S_i = alpha T^0_i,
         // S_ij = g_{i mu} g_{j nu} T^{mu nu}
         if (pp.evolve_metric) {
-            double rho_m = alpha * alpha * T00;
-            double S_i[3];
+            R rho_m = alpha * alpha * T00;
+            R S_i[3];
             for (int i = 0; i < 3; i++) S_i[i] = alpha * T0_d[i];
-            double Sij[3][3], Str = 0.0;
-            double gT[3][3];  // gamma_ik T^{kj}
+            R Sij[3][3], Str = R(0.0);
+            R gT[3][3];  // gamma_ik T^{kj}
             for (int i = 0; i < 3; i++)
                 for (int j = 0; j < 3; j++)
                     gT[i][j] = g[i][0] * Tij[0][j] + g[i][1] * Tij[1][j] + g[i][2] * Tij[2][j];
-            double gT0[3];
+            R gT0[3];
             for (int i = 0; i < 3; i++) gT0[i] = g[i][0] * T0i[0] + g[i][1] * T0i[1] + g[i][2] * T0i[2];
             for (int i = 0; i < 3; i++)
                 for (int j = 0; j < 3; j++) {
-                    double s = beta_d[i] * beta_d[j] * T00 + beta_d[i] * gT0[j] + beta_d[j] * gT0[i] +
+                    R s = beta_d[i] * beta_d[j] * T00 + beta_d[i] * gT0[j] + beta_d[j] * gT0[i] +
                                gT[i][0] * g[0][j] + gT[i][1] * g[1][j] + gT[i][2] * g[2][j];
                     Sij[i][j] = s;
                 }
@@ -449,164 +461,164 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
                 for (int j = 0; j < 3; j++) Str += gi[i][j] * Sij[i][j];
 
             // -------------------------------------------------------- BSSN
-#define D2(f, q) ((double)d2[((long long)(f) * 6 + (q)) * P + p])
+#define D2(f, q) ((R)d2[((long long)(f) * 6 + (q)) * P + p])
             // Christoffels of gammatilde: lower Cl[k][i][j] = Gamma_{k ij}, upper Cu[k][i][j]
-            double Cl[3][3][3], Cu[3][3][3];
+            R Cl[3][3][3], Cu[3][3][3];
             for (int k = 0; k < 3; k++)
                 for (int i = 0; i < 3; i++)
                     for (int j = i; j < 3; j++)
                         Cl[k][i][j] = Cl[k][j][i] =
-                            0.5 * (dgt[i][k][j] + dgt[j][k][i] - dgt[k][i][j]);
+                            R(0.5) * (dgt[i][k][j] + dgt[j][k][i] - dgt[k][i][j]);
             for (int k = 0; k < 3; k++)
                 for (int i = 0; i < 3; i++)
                     for (int j = i; j < 3; j++)
                         Cu[k][i][j] = Cu[k][j][i] =
                             gti[k][0] * Cl[0][i][j] + gti[k][1] * Cl[1][i][j] + gti[k][2] * Cl[2][i][j];
-            double Gd[3];
+            R Gd[3];
             for (int i = 0; i < 3; i++) {
-                double s = 0.0;
+                R s = R(0.0);
                 for (int j = 0; j < 3; j++)
                     for (int k = 0; k < 3; k++) s += gti[j][k] * Cu[i][j][k];
                 Gd[i] = s;
             }
-            double divb = dbe[0][0] + dbe[1][1] + dbe[2][2];
+            R divb = dbe[0][0] + dbe[1][1] + dbe[2][2];
             // A[k][i][m] = gti^{lm} Cu[k][l][i];  Bt[k][j][m] = gti^{lm} Cl[k][l][j]
-            double Ar[3][3][3], Bt[3][3][3];
+            R Ar[3][3][3], Bt[3][3][3];
             for (int k = 0; k < 3; k++)
                 for (int i = 0; i < 3; i++)
                     for (int m = 0; m < 3; m++) {
                         Ar[k][i][m] = gti[0][m] * Cu[k][0][i] + gti[1][m] * Cu[k][1][i] + gti[2][m] * Cu[k][2][i];
                         Bt[k][i][m] = gti[0][m] * Cl[k][0][i] + gti[1][m] * Cl[k][1][i] + gti[2][m] * Cl[k][2][i];
                     }
-            double ddphi[3][3], ddal[3][3];
+            R ddphi[3][3], ddal[3][3];
             for (int i = 0; i < 3; i++)
                 for (int j = i; j < 3; j++) {
                     int q = c_pair[i][j];
                     ddphi[i][j] = ddphi[j][i] = D2(6, q);
                     ddal[i][j] = ddal[j][i] = D2(7, q);
                 }
-            double DDphi[3][3], DDal[3][3];
-            double gdphi2 = 0.0;
-            double gradphi_u[3];
+            R DDphi[3][3], DDal[3][3];
+            R gdphi2 = R(0.0);
+            R gradphi_u[3];
             for (int k = 0; k < 3; k++)
                 gradphi_u[k] = gti[k][0] * dphi[0] + gti[k][1] * dphi[1] + gti[k][2] * dphi[2];
             gdphi2 = gradphi_u[0] * dphi[0] + gradphi_u[1] * dphi[1] + gradphi_u[2] * dphi[2];
-            double gdphida = gradphi_u[0] * dal[0] + gradphi_u[1] * dal[1] + gradphi_u[2] * dal[2];
+            R gdphida = gradphi_u[0] * dal[0] + gradphi_u[1] * dal[1] + gradphi_u[2] * dal[2];
             for (int i = 0; i < 3; i++)
                 for (int j = i; j < 3; j++) {
-                    double cp = Cu[0][i][j] * dphi[0] + Cu[1][i][j] * dphi[1] + Cu[2][i][j] * dphi[2];
-                    double ca = Cu[0][i][j] * dal[0] + Cu[1][i][j] * dal[1] + Cu[2][i][j] * dal[2];
+                    R cp = Cu[0][i][j] * dphi[0] + Cu[1][i][j] * dphi[1] + Cu[2][i][j] * dphi[2];
+                    R ca = Cu[0][i][j] * dal[0] + Cu[1][i][j] * dal[1] + Cu[2][i][j] * dal[2];
                     DDphi[i][j] = DDphi[j][i] = ddphi[i][j] - cp;
                     // physical Christoffels: + 2(d_i a d_j phi + d_j a d_i phi - gt_ij gt^kl d_l phi d_k a)
-                    double cphys = ca + 2.0 * (dal[i] * dphi[j] + dal[j] * dphi[i] - gt[i][j] * gdphida);
+                    R cphys = ca + R(2.0) * (dal[i] * dphi[j] + dal[j] * dphi[i] - gt[i][j] * gdphida);
                     DDal[i][j] = DDal[j][i] = ddal[i][j] - cphys;
                 }
-            double lapphi = 0.0, trDDal = 0.0;
+            R lapphi = R(0.0), trDDal = R(0.0);
             for (int i = 0; i < 3; i++)
                 for (int j = 0; j < 3; j++) {
                     lapphi += gti[i][j] * DDphi[i][j];
                     trDDal += gti[i][j] * DDal[i][j];
                 }
-            trDDal *= e4m;
+            trDDal *= e4mr;
             // Atilde with raised indices
-            double Aud[3][3], Auu[3][3];
+            R Aud[3][3], Auu[3][3];
             for (int k = 0; k < 3; k++)
                 for (int j = 0; j < 3; j++)
                     Aud[k][j] = gti[k][0] * At[0][j] + gti[k][1] * At[1][j] + gti[k][2] * At[2][j];
             for (int i = 0; i < 3; i++)
                 for (int j = 0; j < 3; j++)
                     Auu[i][j] = Aud[i][0] * gti[0][j] + Aud[i][1] * gti[1][j] + Aud[i][2] * gti[2][j];
-            double AA = 0.0;
+            R AA = R(0.0);
             for (int i = 0; i < 3; i++)
                 for (int j = 0; j < 3; j++) AA += At[i][j] * Auu[i][j];
 
             // X_ij = -D_i D_j alpha + alpha (R_ij - 8 pi S_ij)
-            double X[3][3];
+            R X[3][3];
             for (int i = 0; i < 3; i++)
                 for (int j = i; j < 3; j++) {
                     int sij = SI(i, j);
-                    double lapg = 0.0;
+                    R lapg = R(0.0);
                     for (int l = 0; l < 3; l++)
                         for (int m = l; m < 3; m++) {
-                            double w = (l == m) ? gti[l][m] : 2.0 * gti[l][m];
+                            R w = (l == m) ? gti[l][m] : R(2.0) * gti[l][m];
                             lapg += w * D2(sij, c_pair[l][m]);
                         }
-                    double R = -0.5 * lapg;
+                    R Ric = -R(0.5) * lapg;
                     for (int k = 0; k < 3; k++)
-                        R += 0.5 * (gt[k][i] * dGam[j][k] + gt[k][j] * dGam[i][k]) +
-                             0.5 * Gd[k] * (Cl[i][j][k] + Cl[j][i][k]);
-                    double t = 0.0;
+                        Ric += R(0.5) * (gt[k][i] * dGam[j][k] + gt[k][j] * dGam[i][k]) +
+                               R(0.5) * Gd[k] * (Cl[i][j][k] + Cl[j][i][k]);
+                    R t = R(0.0);
                     for (int k = 0; k < 3; k++)
                         for (int m = 0; m < 3; m++)
                             t += Ar[k][i][m] * Cl[j][k][m] + Ar[k][j][m] * Cl[i][k][m] +
                                  Cu[k][i][m] * Bt[k][j][m];
-                    R += t;
-                    R += -2.0 * DDphi[i][j] - 2.0 * gt[i][j] * lapphi + 4.0 * dphi[i] * dphi[j] -
-                         4.0 * gt[i][j] * gdphi2;
-                    X[i][j] = X[j][i] = -DDal[i][j] + alpha * (R - 8.0 * PI * Sij[i][j]);
+                    Ric += t;
+                    Ric += -R(2.0) * DDphi[i][j] - R(2.0) * gt[i][j] * lapphi + R(4.0) * dphi[i] * dphi[j] -
+                           R(4.0) * gt[i][j] * gdphi2;
+                    X[i][j] = X[j][i] = -DDal[i][j] + alpha * (Ric - R(8.0) * PI * Sij[i][j]);
                 }
-            double trX = 0.0;
+            R trX = R(0.0);
             for (int i = 0; i < 3; i++)
                 for (int j = 0; j < 3; j++) trX += gti[i][j] * X[i][j];
             for (int i = 0; i < 3; i++)
                 for (int j = i; j < 3; j++) {
                     int sij = SI(i, j);
-                    double adv_g = beta[0] * dgt[0][i][j] + beta[1] * dgt[1][i][j] + beta[2] * dgt[2][i][j];
-                    double adv_a = beta[0] * dAt[0][i][j] + beta[1] * dAt[1][i][j] + beta[2] * dAt[2][i][j];
-                    double lg = 0.0, la = 0.0, AAd = 0.0;
+                    R adv_g = beta[0] * dgt[0][i][j] + beta[1] * dgt[1][i][j] + beta[2] * dgt[2][i][j];
+                    R adv_a = beta[0] * dAt[0][i][j] + beta[1] * dAt[1][i][j] + beta[2] * dAt[2][i][j];
+                    R lg = R(0.0), la = R(0.0), AAd = R(0.0);
                     for (int k = 0; k < 3; k++) {
                         lg += gt[i][k] * dbe[j][k] + gt[j][k] * dbe[i][k];
                         la += At[i][k] * dbe[j][k] + At[j][k] * dbe[i][k];
                         AAd += At[i][k] * Aud[k][j];
                     }
-                    rhs[V_GT + sij] = -2.0 * alpha * At[i][j] + adv_g + lg - (2.0 / 3.0) * gt[i][j] * divb;
-                    double XTF = X[i][j] - gt[i][j] * trX / 3.0;
-                    rhs[V_AT + sij] = e4m * XTF + alpha * (K * At[i][j] - 2.0 * AAd) + adv_a + la -
-                                      (2.0 / 3.0) * At[i][j] * divb;
+                    rhs[V_GT + sij] = -R(2.0) * alpha * At[i][j] + adv_g + lg - (R(2.0) / R(3.0)) * gt[i][j] * divb;
+                    R XTF = X[i][j] - gt[i][j] * trX / R(3.0);
+                    rhs[V_AT + sij] = e4mr * XTF + alpha * (K * At[i][j] - R(2.0) * AAd) + adv_a + la -
+                                      (R(2.0) / R(3.0)) * At[i][j] * divb;
                 }
-            rhs[V_PHI] = -alpha * K / 6.0 + (beta[0] * dphi[0] + beta[1] * dphi[1] + beta[2] * dphi[2]) +
-                         divb / 6.0;
-            rhs[V_K] = -trDDal + alpha * (AA + K * K / 3.0) + 4.0 * PI * alpha * (rho_m + Str) +
+            rhs[V_PHI] = -alpha * K / R(6.0) + (beta[0] * dphi[0] + beta[1] * dphi[1] + beta[2] * dphi[2]) +
+                         divb / R(6.0);
+            rhs[V_K] = -trDDal + alpha * (AA + K * K / R(3.0)) + R(4.0) * PI * alpha * (rho_m + Str) +
                        (beta[0] * dK[0] + beta[1] * dK[1] + beta[2] * dK[2]);
             // Gammatilde
-            double ddb[3][3][3];  // [q pair via j,k][i]
+            R ddb[3][3][3];  // [q pair via j,k][i]
             for (int j = 0; j < 3; j++)
                 for (int k = j; k < 3; k++)
                     for (int i = 0; i < 3; i++)
                         ddb[j][k][i] = ddb[k][j][i] = D2(7 + 1 + i, c_pair[j][k]);
-            double ddbk[3];  // d_j d_k beta^k
+            R ddbk[3];  // d_j d_k beta^k
             for (int j = 0; j < 3; j++) ddbk[j] = ddb[j][0][0] + ddb[j][1][1] + ddb[j][2][2];
             for (int i = 0; i < 3; i++) {
-                double s = 0.0;
+                R s = R(0.0);
                 for (int j = 0; j < 3; j++)
                     for (int k = 0; k < 3; k++) s += gti[j][k] * ddb[j][k][i];
-                double s2 = gti[i][0] * ddbk[0] + gti[i][1] * ddbk[1] + gti[i][2] * ddbk[2];
-                double adv = beta[0] * dGam[0][i] + beta[1] * dGam[1][i] + beta[2] * dGam[2][i];
-                double gdb = Gam[0] * dbe[0][i] + Gam[1] * dbe[1][i] + Gam[2] * dbe[2][i];
-                double Ada = Auu[i][0] * dal[0] + Auu[i][1] * dal[1] + Auu[i][2] * dal[2];
-                double CA = 0.0;
+                R s2 = gti[i][0] * ddbk[0] + gti[i][1] * ddbk[1] + gti[i][2] * ddbk[2];
+                R adv = beta[0] * dGam[0][i] + beta[1] * dGam[1][i] + beta[2] * dGam[2][i];
+                R gdb = Gam[0] * dbe[0][i] + Gam[1] * dbe[1][i] + Gam[2] * dbe[2][i];
+                R Ada = Auu[i][0] * dal[0] + Auu[i][1] * dal[1] + Auu[i][2] * dal[2];
+                R CA = R(0.0);
                 for (int j = 0; j < 3; j++)
                     for (int k = 0; k < 3; k++) CA += Cu[i][j][k] * Auu[j][k];
-                double Adp = Auu[i][0] * dphi[0] + Auu[i][1] * dphi[1] + Auu[i][2] * dphi[2];
-                double gdK = gti[i][0] * dK[0] + gti[i][1] * dK[1] + gti[i][2] * dK[2];
-                double gS = gti[i][0] * S_i[0] + gti[i][1] * S_i[1] + gti[i][2] * S_i[2];
-                rhs[V_GAM + i] = s + s2 / 3.0 + adv - gdb + (2.0 / 3.0) * Gam[i] * divb - 2.0 * Ada +
-                                 2.0 * alpha * (CA + 6.0 * Adp - (2.0 / 3.0) * gdK) -
-                                 16.0 * PI * alpha * gS;
+                R Adp = Auu[i][0] * dphi[0] + Auu[i][1] * dphi[1] + Auu[i][2] * dphi[2];
+                R gdK = gti[i][0] * dK[0] + gti[i][1] * dK[1] + gti[i][2] * dK[2];
+                R gS = gti[i][0] * S_i[0] + gti[i][1] * S_i[1] + gti[i][2] * S_i[2];
+                rhs[V_GAM + i] = s + s2 / R(3.0) + adv - gdb + (R(2.0) / R(3.0)) * Gam[i] * divb - R(2.0) * Ada +
+                                 R(2.0) * alpha * (CA + R(6.0) * Adp - (R(2.0) / R(3.0)) * gdK) -
+                                 R(16.0) * PI * alpha * gS;
             }
 #undef D2
             if (pp.gauge == 0) {
-                rhs[V_ALPHA] = -2.0 * alpha * K + beta[0] * dal[0] + beta[1] * dal[1] + beta[2] * dal[2];
+                rhs[V_ALPHA] = -R(2.0) * alpha * K + beta[0] * dal[0] + beta[1] * dal[1] + beta[2] * dal[2];
                 for (int i = 0; i < 3; i++) {
-                    rhs[V_BETA + i] = 0.75 * Bg[i];
-                    rhs[V_BG + i] = rhs[V_GAM + i] - pp.eta * Bg[i];
+                    rhs[V_BETA + i] = R(0.75) * Bg[i];
+                    rhs[V_BG + i] = rhs[V_GAM + i] - (R)pp.eta * Bg[i];
                 }
             } else {
-                rhs[V_ALPHA] = 0.0;
-                for (int i = 0; i < 3; i++) rhs[V_BETA + i] = rhs[V_BG + i] = 0.0;
+                rhs[V_ALPHA] = R(0.0);
+                for (int i = 0; i < 3; i++) rhs[V_BETA + i] = rhs[V_BG + i] = R(0.0);
             }
         } else {
-            for (int v = 0; v < N_BSSN; v++) rhs[v] = 0.0;
+            for (int v = 0; v < N_BSSN; v++) rhs[v] = R(0.0);
         }
     }
 
@@ -615,18 +627,18 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
         const long long ir = (p / d.NtNp) % d.Nr;
         const int e = (int)(p / d.elem);
         if (e == d.E - 1 && ir == d.Nr - 1)
-            for (int v = 0; v < NV; v++) rhs[v] = 0.0;
+            for (int v = 0; v < NV; v++) rhs[v] = R(0);
     }
 
     // ------------------------------------------------------------ output
     const double dt = dt_dev ? *dt_dev : 0.0;
     if (co.acc_mode < 0) {
-        for (int v = 0; v < NV; v++) out[v * P + p] = rhs[v];
+        for (int v = 0; v < NV; v++) out[v * P + p] = (double)rhs[v];
         return;
     }
     for (int v = 0; v < NV; v++) {
         long long ix = v * P + p;
-        double L = rhs[v];
+        double L = (double)rhs[v];
         double o;
         if (co.acc_mode == 0) {
             // SSP-RK3 (Shu-Osher): a U0 + b (Us + dt L)
@@ -661,11 +673,11 @@ cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, co
     int bs = 128;
     long long nb = (d.P + bs - 1) / bs;
     if (deriv_fp32)
-        k_rhs<float><<<(unsigned)nb, bs, 0, s>>>(d, pp, U0, Us, prim, flux, tmn, lam, (const float*)d1,
+        k_rhs<float, float><<<(unsigned)nb, bs, 0, s>>>(d, pp, U0, Us, prim, flux, tmn, lam, (const float*)d1,
                                                  (const float*)d2, (const float*)divF, r_scale_dev, dt_dev,
                                                  co, out, acc);
     else
-        k_rhs<double><<<(unsigned)nb, bs, 0, s>>>(d, pp, U0, Us, prim, flux, tmn, lam, (const double*)d1,
+        k_rhs<double, double><<<(unsigned)nb, bs, 0, s>>>(d, pp, U0, Us, prim, flux, tmn, lam, (const double*)d1,
                                                   (const double*)d2, (const double*)divF, r_scale_dev,
                                                   dt_dev, co, out, acc);
     return cudaGetLastError();

@@ -17,6 +17,7 @@ def main(argv=None):
     ap.add_argument("--rhs", type=int, default=1, help="RHS evaluations")
     ap.add_argument("--steps", type=int, default=0, help="RK steps (one graph)")
     ap.add_argument("--time", action="store_true", help="print per-kernel CUDA-event times")
+    ap.add_argument("--precision", type=int, default=0, help="0 FP64, 1 split BF16 x3, 2 TF32")
     a = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -27,7 +28,7 @@ def main(argv=None):
     from workloads import config, primitive_profiles
 
     cfg = config(a.config)
-    grid, phys, opts = pkg.make_structs(cfg)
+    grid, phys, opts = pkg.make_structs(cfg, precision=a.precision)
     stream = torch.cuda.Stream()
     ctx = pkg.Context(grid, phys, opts, stream.cuda_stream)
     r, t, ph = ctx.coords()
@@ -38,12 +39,23 @@ def main(argv=None):
     for _ in range(a.rhs):
         ctx.rhs(out, True)
     if a.steps:
-        ctx.step(ctx.cfl_dt(), a.steps)
+        dt = ctx.cfl_dt()
+        ctx.step(dt, a.steps)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(dt, a.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        print(f"{a.steps} steps: {ms:.3f} ms -> {3 * a.steps * ctx.n_points / ms * 1e3:.4e} "
+              f"point-updates/s")
     torch.cuda.synchronize()
     if a.time:
-        for k, (ms, fl) in ctx.kernel_times(reps=5).items():
+        for k, (ms, fl, by) in ctx.kernel_times(reps=5).items():
             tf = fl / (ms * 1e-3) / 1e12 if fl else 0.0
-            print(f"{k:14s} {ms:8.4f} ms  {tf:7.3f} TFLOP/s")
+            gb = by / (ms * 1e-3) / 1e9 if by else 0.0
+            print(f"{k:14s} {ms:8.4f} ms  {tf:8.3f} TFLOP/s  {gb:8.1f} GB/s")
     ctx.close()
     print("ok")
 
