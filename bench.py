@@ -1,9 +1,12 @@
 """Benchmark: coupled BSSN-Valencia RHS point-updates/s on the GB300.
 
-Workload (one bench step): the 8-element Kerr-Schild torus instance, spin a = 0.9,
-r in [1.5, 100], N_r = 24, N_theta = 32, N_phi = 64 (393,216 nodes, 32 evolved
+Default workload (one bench step): the 8-element Kerr-Schild torus instance, spin
+a = 0.9, r in [1.5, 100], N_r = 24, N_theta = 32, N_phi = 64 (393,216 nodes, 32 evolved
 variables), 100 SSP-RK3 time steps at CFL 0.3 recorded in one CUDA graph, FP64.
 value = nodes x RHS evaluations / second (3 RHS per step), summed over ranks.
+--precision 1 / 2 runs the mixed modes (tensor-core split-BF16 x3 / TF32 derivative
+contractions, FP32 algebra, FP64 state); --workload c5 the 16-element 32 x 64 x 128
+instance (4,194,304 nodes, 200 steps per bench step).
 
 --impl reference times the FP64 numpy oracle (the project's CPU reference) on the host
 cores on a bounded sample of the same workload.
@@ -21,10 +24,22 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "coupled RHS point-updates/s (FP64)"
 UNIT = "point-updates/s"
-NSTEPS_PER_BENCH_STEP = 100
 RHS_PER_STEP = 3
+PREC_NAME = {0: "FP64", 1: "mixed: split-BF16x3 tensor-core derivatives, FP32 algebra, FP64 "
+                           "state/c2p/metric/RK", 2: "mixed: TF32 tensor-core derivatives, FP32 "
+                                                      "algebra, FP64 state/c2p/metric/RK"}
+DTYPE = {0: "f64", 1: "f64 state + bf16x3/f32 derivatives", 2: "f64 state + tf32/f32 derivatives"}
+WORKLOADS = {
+    "c2": ("c2: a=0.9, 8 radial elements r in [1.5,100], N_r=24 N_theta=32 N_phi=64, "
+           "100 SSP-RK3 steps (CFL 0.3) per bench step in one CUDA graph", 100),
+    "c5": ("c5: a=0.94, 16 radial elements r in [1.3,500], N_r=32 N_theta=64 N_phi=128, "
+           "200 SSP-RK3 steps (CFL 0.3) per bench step in one CUDA graph", 200),
+}
+
+
+def metric_name(precision):
+    return f"coupled RHS point-updates/s ({PREC_NAME[precision]})"
 
 
 def _dist():
@@ -133,7 +148,7 @@ def run_reference(args):
         so.rhs(U, g, p)
     el = time.perf_counter() - t0
     val = npts * args.steps / el
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+    line = {"impl": "reference", "metric": metric_name(0), "value": val, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -161,8 +176,9 @@ def run_gpu(args):
     import paper_2508_18221_gb300 as pkg
     from workloads import config, primitive_profiles
 
-    cfg = config("c2")
-    grid, phys, opts = pkg.make_structs(cfg)
+    cfg = config(args.workload)
+    desc, nsteps = WORKLOADS[args.workload]
+    grid, phys, opts = pkg.make_structs(cfg, precision=args.precision)
     stream = torch.cuda.Stream()
     ctx = pkg.Context(grid, phys, opts, stream.cuda_stream)
     P = ctx.n_points
@@ -181,7 +197,7 @@ def run_gpu(args):
             flush.fill_(1.0)                      # evict L2 between timed steps
             if timed_events:
                 timed_events[0].record(stream)
-            ctx.step(dt, NSTEPS_PER_BENCH_STEP)
+            ctx.step(dt, nsteps)
             if timed_events:
                 timed_events[1].record(stream)
 
@@ -205,7 +221,7 @@ def run_gpu(args):
     if dist_on:
         tdist.all_reduce(ms_t, op=tdist.ReduceOp.MAX)
     ms_max = float(ms_t.item())
-    units = P * RHS_PER_STEP * NSTEPS_PER_BENCH_STEP * args.steps * world
+    units = P * RHS_PER_STEP * nsteps * args.steps * world
     value = units / (ms_max * 1e-3)
 
     # end to end through the C ABI with host buffers (pinned)
@@ -217,31 +233,47 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ctx.set_state(host_in, False)
-        ctx.step(dt, NSTEPS_PER_BENCH_STEP)
+        ctx.step(dt, nsteps)
         ctx.get_state(host_out, False)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_val = P * RHS_PER_STEP * NSTEPS_PER_BENCH_STEP * e2e_steps * world / e2e_s
+    e2e_val = P * RHS_PER_STEP * nsteps * e2e_steps * world / e2e_s
 
     # live per-kernel timing (CUDA events on the library's stream).  The dominant kernel
     # is the contraction kernel (k_deriv / k_deriv_eo): it runs 6 times per RHS stage and 3
     # times per filter, and takes most of a step; its roofline is the algorithmic FP64
     # work of all its launches in one step over their summed time.
     ctx.set_state(U0, True)
-    kt = {k: v[:2] for k, v in ctx.kernel_times(reps=5).items()}
+    kt_full = ctx.kernel_times(reps=5)
+    kt = {k: v[:2] for k, v in kt_full.items()}
     per_step = {k: (1 if k.startswith("filter") else RHS_PER_STEP) for k in kt}
     contr = [k for k in kt if kt[k][1] > 0]
     t_contr = sum(kt[k][0] * per_step[k] for k in contr)
     f_contr = sum(kt[k][1] * per_step[k] for k in contr)
     t_all = sum(kt[k][0] * per_step[k] for k in kt)
-    fp64_peak = 1.25  # TFLOP/s: GB300 nominal FP64 (ALU roofline)
-    achieved = f_contr / (t_contr * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": "k_deriv_eo (all contraction launches of one step)",
-            "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak, "traffic": None,
-            "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (ALU bound; of nominal)",
-            "share_of_step": t_contr / t_all,
-            "kernel_ms": {k: round(v[0], 5) for k, v in kt.items()}}
+    if args.precision == 0:
+        fp64_peak = 1.25  # TFLOP/s: GB300 nominal FP64 (ALU roofline)
+        achieved = f_contr / (t_contr * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_deriv_eo (all contraction launches of one step)",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (ALU bound; of nominal)",
+                "share_of_step": t_contr / t_all,
+                "kernel_ms": {k: round(v[0], 5) for k, v in kt.items()}}
+    else:
+        # tensor-core contractions (first/second derivative classes, 3 per step): HBM
+        hbm = _peaks().get("hbm_gbs", 6800.0)
+        tc = [k for k in ("d1_r", "d1_theta", "d1_phi", "d2_r", "d2_theta", "d2_phi")]
+        t_tc = sum(kt_full[k][0] * RHS_PER_STEP for k in tc)
+        b_tc = sum(kt_full[k][2] * RHS_PER_STEP for k in tc)
+        achieved = b_tc / (t_tc * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_contract_tc (all tensor-core contraction launches of "
+                                          "one step)",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "tensor_tflops": sum(kt_full[k][1] * RHS_PER_STEP for k in tc) / (t_tc * 1e-3) / 1e12,
+                "share_of_step": t_tc / t_all,
+                "kernel_ms": {k: round(v[0], 5) for k, v in kt.items()}}
     stats = ctx.diag()
     if rank == 0:
         cb = None
@@ -250,15 +282,14 @@ def run_gpu(args):
                 cb = cpu_baseline()
             except Exception as exc:  # noqa: BLE001
                 cb = {"error": str(exc)}
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        line = {"metric": metric_name(args.precision), "value": value, "unit": UNIT,
+                "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
                 "data": "synthetic (seeded Kerr-Schild torus, splitmix64 noise)",
-                "config": {"workload": "c2: a=0.9, 8 radial elements r in [1.5,100], "
-                                       "N_r=24 N_theta=32 N_phi=64, 100 SSP-RK3 steps "
-                                       "(CFL 0.3) per bench step in one CUDA graph",
-                           "nodes": P, "rk_steps_per_bench_step": NSTEPS_PER_BENCH_STEP,
+                "config": {"workload": desc, "precision": args.precision,
+                           "nodes": P, "rk_steps_per_bench_step": nsteps,
                            "l2": "flushed (256 MB write) before every timed step",
                            "dt": dt, "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cb,
@@ -281,6 +312,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -296,23 +296,30 @@ extern "C" int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, c
         }
     c->job_first_n = N_D1 + 8;
     const int vars2[N_D2] = {0, 1, 2, 3, 4, 5, 6, 17, 18, 19, 20};
-    // second derivatives: r: rr; theta: r-theta, theta-theta; phi: r-phi, theta-phi, phi-phi
+    // second derivatives, each mixed pair with the cheaper outer operator (same map: the
+    // operators commute, and D_theta commutes with the interface mean):
+    //   r:     rr = D_r(mean d_r u), r-theta = D_r(d_theta u), r-phi = D_r(d_phi u)
+    //   theta: theta-theta = D_theta(d_theta u), theta-phi = D_theta(d_phi u)
+    //   phi:   phi-phi = D_phi(d_phi u)
+    // the three radial results are interface-averaged afterwards (pairs rr, rth, rph are
+    // the d2 slots 0, 1, 2 of each field)
     c->job_second[0] = (int)jobs.size();
-    for (int s = 0; s < N_D2; s++) add(c->d1 + ((long long)vars2[s] * 3 + 0) * P, c->d2 + ((long long)s * 6 + 0) * P, 0);
-    c->job_second_n[0] = N_D2;
+    for (int s = 0; s < N_D2; s++) {
+        add(c->d1 + ((long long)vars2[s] * 3 + 0) * P, c->d2 + ((long long)s * 6 + 0) * P, 0);
+        add(c->d1 + ((long long)vars2[s] * 3 + 1) * P, c->d2 + ((long long)s * 6 + 1) * P, 0);
+        add(c->d1 + ((long long)vars2[s] * 3 + 2) * P, c->d2 + ((long long)s * 6 + 2) * P, 0);
+    }
+    c->job_second_n[0] = 3 * N_D2;
     c->job_second[1] = (int)jobs.size();
     for (int s = 0; s < N_D2; s++) {
-        add(c->d1 + ((long long)vars2[s] * 3 + 0) * P, c->d2 + ((long long)s * 6 + 1) * P, 0);
         add(c->d1 + ((long long)vars2[s] * 3 + 1) * P, c->d2 + ((long long)s * 6 + 3) * P, 0);
+        add(c->d1 + ((long long)vars2[s] * 3 + 2) * P, c->d2 + ((long long)s * 6 + 4) * P, 0);
     }
     c->job_second_n[1] = 2 * N_D2;
     c->job_second[2] = (int)jobs.size();
-    for (int s = 0; s < N_D2; s++) {
-        add(c->d1 + ((long long)vars2[s] * 3 + 0) * P, c->d2 + ((long long)s * 6 + 2) * P, 0);
-        add(c->d1 + ((long long)vars2[s] * 3 + 1) * P, c->d2 + ((long long)s * 6 + 4) * P, 0);
+    for (int s = 0; s < N_D2; s++)
         add(c->d1 + ((long long)vars2[s] * 3 + 2) * P, c->d2 + ((long long)s * 6 + 5) * P, 0);
-    }
-    c->job_second_n[2] = 3 * N_D2;
+    c->job_second_n[2] = N_D2;
     // filter chains: r: U[b] -> scratch; theta: scratch -> U[b]; phi: U[b] -> U[0]
     for (int b = 0; b < 3; b++)
         for (int dir = 0; dir < 3; dir++)
@@ -383,18 +390,17 @@ extern "C" int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, c
             }
         const int vars2[N_D2] = {0, 1, 2, 3, 4, 5, 6, 17, 18, 19, 20};
         c->tc_second[0] = (int)tj.size();
-        for (int q = 0; q < N_D2; q++) addt(d1f + ((long long)vars2[q] * 3 + 0) * P, d2f + ((long long)q * 6 + 0) * P, 0);
+        for (int q = 0; q < N_D2; q++)
+            for (int x = 0; x < 3; x++)
+                addt(d1f + ((long long)vars2[q] * 3 + x) * P, d2f + ((long long)q * 6 + x) * P, 0);
         c->tc_second[1] = (int)tj.size();
         for (int q = 0; q < N_D2; q++) {
-            addt(d1f + ((long long)vars2[q] * 3 + 0) * P, d2f + ((long long)q * 6 + 1) * P, 0);
             addt(d1f + ((long long)vars2[q] * 3 + 1) * P, d2f + ((long long)q * 6 + 3) * P, 0);
+            addt(d1f + ((long long)vars2[q] * 3 + 2) * P, d2f + ((long long)q * 6 + 4) * P, 0);
         }
         c->tc_second[2] = (int)tj.size();
-        for (int q = 0; q < N_D2; q++) {
-            addt(d1f + ((long long)vars2[q] * 3 + 0) * P, d2f + ((long long)q * 6 + 2) * P, 0);
-            addt(d1f + ((long long)vars2[q] * 3 + 1) * P, d2f + ((long long)q * 6 + 4) * P, 0);
+        for (int q = 0; q < N_D2; q++)
             addt(d1f + ((long long)vars2[q] * 3 + 2) * P, d2f + ((long long)q * 6 + 5) * P, 0);
-        }
         if (cudaMalloc(&c->tcjobs, tj.size() * sizeof(TcJob)) != cudaSuccess ||
             cudaMalloc(&c->tc_err, sizeof(int)) != cudaSuccess ||
             cudaMemcpyAsync(c->tcjobs, tj.data(), tj.size() * sizeof(TcJob), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -468,22 +474,24 @@ static int enqueue_first_derivs(grmhd_ctx* c, int b) {
 static int enqueue_second_derivs(grmhd_ctx* c) {
     if (c->opts.precision > 0) {
         const int tf32 = c->opts.precision == 2;
-        const int n[3] = {N_D2, 2 * N_D2, 3 * N_D2};
+        const int n[3] = {3 * N_D2, 2 * N_D2, N_D2};
         for (int dir = 0; dir < 3; dir++) {
             CK(launch_contract_tc(dir, 1, c->d, c->tcjobs + c->tc_second[dir], n[dir], c->tc_img[dir], tf32,
                                   c->r_scale, c->tc_err, c->stream));
             c->launches_tmp++;
         }
-        CK(launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d2), 6 * c->d.P, N_D2, c->stream));
-        c->launches_tmp++;
+        for (int x = 0; x < 3; x++)
+            CK(launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d2) + x * c->d.P, 6 * c->d.P, N_D2, c->stream));
+        if (c->d.E > 1) c->launches_tmp += 3;
         return GRMHD_OK;
     }
     for (int dir = 0; dir < 3; dir++) {
         CK(contract(c, dir, 0, c->jobs + c->job_second[dir], c->job_second_n[dir]));
         c->launches_tmp++;
     }
-    CK(launch_iface_avg(c->d, c->d2, 6 * c->d.P, N_D2, c->stream));
-    c->launches_tmp++;
+    for (int x = 0; x < 3; x++)
+        CK(launch_iface_avg(c->d, c->d2 + x * c->d.P, 6 * c->d.P, N_D2, c->stream));
+    if (c->d.E > 1) c->launches_tmp += 3;
     return GRMHD_OK;
 }
 
@@ -806,7 +814,7 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
                           : launch_iface_avg(c->d, c->d1, 3 * P, N_D1, c->stream);
             } else if (k >= 5 && k <= 7) {
                 int dir = k - 5;
-                const int nj[3] = {N_D2, 2 * N_D2, 3 * N_D2};
+                const int nj[3] = {3 * N_D2, 2 * N_D2, N_D2};
                 if (mixed) {
                     e = launch_contract_tc(dir, 1, c->d, c->tcjobs + c->tc_second[dir], nj[dir], c->tc_img[dir], tf32,
                                            c->r_scale, c->tc_err, c->stream);
@@ -818,8 +826,9 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
                     by[k] = (double)P * c->job_second_n[dir] * 16.0;
                 }
             } else if (k == 8) {
-                e = mixed ? launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d2), 6 * P, N_D2, c->stream)
-                          : launch_iface_avg(c->d, c->d2, 6 * P, N_D2, c->stream);
+                for (int x = 0; x < 3 && e == cudaSuccess; x++)
+                    e = mixed ? launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d2) + x * P, 6 * P, N_D2, c->stream)
+                              : launch_iface_avg(c->d, c->d2 + x * P, 6 * P, N_D2, c->stream);
             }
             else if (k == 9) e = launch_rhs(c->d, c->pp, c->U[0], c->U[1], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
                                             c->divF, c->opts.precision > 0, c->r_scale, c->dt, co, c->scratch,

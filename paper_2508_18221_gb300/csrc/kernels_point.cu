@@ -143,10 +143,10 @@ __device__ int con2prim_point(double D, const double S_d[3], double tau, const d
 
     double lo = 0.0, hi = 1.0;
     int ok = 1;
-    double fhi = master<double>(1.0, c, nullptr, nullptr, nullptr);
-    if (!(fhi >= 0.0)) ok = 0;
     double mu = (guess_mu > 0.0 && guess_mu < 1.0) ? guess_mu : 0.5;
     int conv = 0;
+    // f(0+) < 0 and f(1) >= 0 for every admissible state (h >= 1); a state without a root
+    // never converges and is flagged below
     for (int it = 0; it < maxit; it++) {
         Dual f = master<Dual>(mk(mu, 1.0), c, nullptr, nullptr, nullptr);
         if (f.v == 0.0) { conv = 1; break; }

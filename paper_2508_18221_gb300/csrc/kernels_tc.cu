@@ -117,34 +117,49 @@ __global__ void __launch_bounds__(128) k_contract_tc(Dims d, const TcJob* __rest
                      "l"(op_img), "r"(bytes), "r"(smem_u32(&bars[0]))
                      : "memory");
     }
-    // line tile: convert and split into the K-major layout (zero padding in K and lines)
+    // line tile: convert and split into the K-major layout (zero padding in K and lines).
+    // Each thread first issues LD independent global loads, then converts them, so that
+    // LD loads per thread are in flight at once (128 * Kp is a multiple of 128 * LD).
     const int K = N;
-    for (int idx = tid; idx < 128 * Kp; idx += 128) {
-        int m, k;
-        if (DIR == 2) { m = idx / Kp; k = idx % Kp; }   // consecutive threads walk along a line
-        else { k = idx / 128; m = idx % 128; }          // consecutive threads walk across lines
-        float v = 0.f;
-        long long t = t0 + m;
-        if (k < K && t < nlines) {
-            long long base;
-            if (DIR == 0) { long long e = t / d.NtNp; base = e * d.elem + (t - e * d.NtNp); }
-            else if (DIR == 1) { long long eil = t / d.Np; base = eil * d.NtNp + (t - eil * d.Np); }
-            else base = t * N;
-            v = (float)static_cast<const TIn*>(job.src)[base + (long long)k * stride];
+    constexpr int LD = 8;
+    for (int base_idx = 0; base_idx < 128 * Kp; base_idx += 128 * LD) {
+        float v[LD];
+#pragma unroll
+        for (int u = 0; u < LD; u++) {
+            const int idx = base_idx + u * 128 + tid;
+            int m, k;
+            if (DIR == 2) { m = idx / Kp; k = idx % Kp; }   // consecutive threads along a line
+            else { k = idx / 128; m = idx % 128; }          // consecutive threads across lines
+            const long long t = t0 + m;
+            v[u] = 0.f;
+            if (k < K && t < nlines) {
+                long long base;
+                if (DIR == 0) { long long e = t / d.NtNp; base = e * d.elem + (t - e * d.NtNp); }
+                else if (DIR == 1) { long long eil = t / d.Np; base = eil * d.NtNp + (t - eil * d.Np); }
+                else base = t * N;
+                v[u] = (float)static_cast<const TIn*>(job.src)[base + (long long)k * stride];
+            }
         }
-        uint32_t off = core_off(m, k, kcores, es);
-        if (tf32) {
-            uint32_t u;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
-            *reinterpret_cast<uint32_t*>(sA + off) = u;
-        } else {
-            __nv_bfloat16 x1 = __float2bfloat16_rn(v);
-            float r1 = v - __bfloat162float(x1);
-            __nv_bfloat16 x2 = __float2bfloat16_rn(r1);
-            __nv_bfloat16 x3 = __float2bfloat16_rn(r1 - __bfloat162float(x2));
-            *reinterpret_cast<__nv_bfloat16*>(sA + off) = x1;
-            *reinterpret_cast<__nv_bfloat16*>(sA + a_bytes + off) = x2;
-            *reinterpret_cast<__nv_bfloat16*>(sA + 2 * a_bytes + off) = x3;
+#pragma unroll
+        for (int u = 0; u < LD; u++) {
+            const int idx = base_idx + u * 128 + tid;
+            int m, k;
+            if (DIR == 2) { m = idx / Kp; k = idx % Kp; }
+            else { k = idx / 128; m = idx % 128; }
+            const uint32_t off = core_off(m, k, kcores, es);
+            if (tf32) {
+                uint32_t w;
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w) : "f"(v[u]));
+                *reinterpret_cast<uint32_t*>(sA + off) = w;
+            } else {
+                __nv_bfloat16 x1 = __float2bfloat16_rn(v[u]);
+                float r1 = v[u] - __bfloat162float(x1);
+                __nv_bfloat16 x2 = __float2bfloat16_rn(r1);
+                __nv_bfloat16 x3 = __float2bfloat16_rn(r1 - __bfloat162float(x2));
+                *reinterpret_cast<__nv_bfloat16*>(sA + off) = x1;
+                *reinterpret_cast<__nv_bfloat16*>(sA + a_bytes + off) = x2;
+                *reinterpret_cast<__nv_bfloat16*>(sA + 2 * a_bytes + off) = x3;
+            }
         }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -207,14 +222,30 @@ __global__ void __launch_bounds__(128) k_contract_tc(Dims d, const TcJob* __rest
                      : "r"(ta));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (ok && t < nlines) {
+            if (DIR == 2 && cb + 8 <= N && (N & 3) == 0) {
+                // a line's 8 outputs are contiguous: two 16-byte stores
+                float o[8];
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
-                int i = cb + j;
-                if (i < N) {
-                    float o = (float)(scale * (double)__uint_as_float(r[j]));
-                    float* p = job.dst + base + (long long)i * stride;
-                    if (job.accumulate) *p += o;
-                    else *p = o;
+                for (int j = 0; j < 8; j++) o[j] = (float)(scale * (double)__uint_as_float(r[j]));
+                float4* p4 = reinterpret_cast<float4*>(job.dst + base + cb);
+                float4 lo = make_float4(o[0], o[1], o[2], o[3]), hi = make_float4(o[4], o[5], o[6], o[7]);
+                if (job.accumulate) {
+                    float4 a0 = p4[0], a1 = p4[1];
+                    lo.x += a0.x; lo.y += a0.y; lo.z += a0.z; lo.w += a0.w;
+                    hi.x += a1.x; hi.y += a1.y; hi.z += a1.z; hi.w += a1.w;
+                }
+                p4[0] = lo;
+                p4[1] = hi;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    int i = cb + j;
+                    if (i < N) {
+                        float o = (float)(scale * (double)__uint_as_float(r[j]));
+                        float* p = job.dst + base + (long long)i * stride;
+                        if (job.accumulate) *p += o;
+                        else *p = o;
+                    }
                 }
             }
         }

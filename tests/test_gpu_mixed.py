@@ -141,3 +141,27 @@ def test_precision_variant_report(pkg, capsys):
     for i, t in enumerate(TENSORS):
         if r["trunc_tensor"][i] > 0:
             assert r["l2_tensor"][i] <= r["trunc_tensor"][i], (list(t), r["l2_tensor"][i], r["trunc_tensor"][i])
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_con2prim_reaches_fp64_root(pkg, precision):
+    """In the mixed modes the primitive recovery stays FP64: the result is the FP64 root
+    (same bar as the FP64 parity test)."""
+    import torch
+    cfg = config("c1")
+    g, p, U = _oracle(cfg)
+    prim = so.primitives(U, p)
+    grid, phys, opts = pkg.make_structs(cfg, precision=precision)
+    ctx = pkg.Context(grid, phys, opts, torch.cuda.current_stream().cuda_stream)
+    ctx.set_state(torch.from_numpy(U.reshape(-1).copy()).cuda(), True)
+    out = torch.empty(7 * U[0].size, dtype=torch.float64, device="cuda")
+    nf = ctx.con2prim(out, True)
+    P = out.cpu().numpy().reshape((7,) + U.shape[1:])
+    assert nf == int(np.sum(~prim["ok"]))
+    ref = [prim["rho"], prim["v"][..., 0], prim["v"][..., 1], prim["v"][..., 2], prim["eps"],
+           prim["p"], prim["W"]]
+    vmax = max(np.abs(ref[i]).max() for i in (1, 2, 3))
+    for i in range(7):
+        sc = vmax if i in (1, 2, 3) else np.abs(ref[i]).max()
+        assert np.abs(P[i] - ref[i]).max() <= 1e-12 * sc, i
+    ctx.close()
