@@ -177,14 +177,34 @@ enum { GRMHD_NKT = 13 };
 int grmhd_kernel_times(grmhd_ctx* ctx, int reps, double* ms_out, double* flops_out,
                        double* bytes_out, int n);
 
-/* Independent instances advanced together (one context per instance, all sharing one
- * stream; the step of every instance is captured into one CUDA graph).  Instances may
- * differ in every grid, physics and option field. */
+/* Independent instances advanced together (the batched workload of many black-hole
+ * set-ups).  Instances that share n_r, n_theta, n_phi, the theta range, gamma_eos, the
+ * floors and every option field form one group; a group is one grid whose radial
+ * elements are the instances' elements in order (the right-hand side does not depend
+ * on M and a, which enter only through the initial data), with interface coupling and
+ * the outer-boundary freeze applied per instance and a per-instance time step.  Each
+ * group therefore advances with the launches of a single instance, and all groups of a
+ * step are recorded in one CUDA graph.  Instances may differ in spin, mass, element
+ * count and radial range inside a group, and in anything across groups.  grids, phys
+ * and opts are arrays of n entries.  All instances share the stream given here. */
 int grmhd_batch_create(int n, const grmhd_grid* grids, const grmhd_physics* phys,
                        const grmhd_opts* opts, void* cuda_stream, grmhd_batch** out);
-grmhd_ctx* grmhd_batch_instance(grmhd_batch* b, int i);
+int grmhd_batch_num_groups(const grmhd_batch* b);
+/* nodes of instance i (its canonical arrays have GRMHD_NV * that many doubles) */
+long long grmhd_batch_num_points(const grmhd_batch* b, int i);
+/* node coordinates of instance i (host arrays of num_points doubles, any may be NULL) */
+int grmhd_batch_coords(const grmhd_batch* b, int i, double* r, double* theta, double* phi);
+/* initial data of instance i from primitives on its nodes (as grmhd_init_prims) */
+int grmhd_batch_init_prims(grmhd_batch* b, int i, const double* rho, const double* p,
+                           const double* vr, const double* vth, const double* vph,
+                           const double* A_phi);
+/* canonical state of instance i in / out (layout and on_device as grmhd_set_state) */
+int grmhd_batch_set_state(grmhd_batch* b, int i, const double* state, int on_device);
+int grmhd_batch_get_state(grmhd_batch* b, int i, double* state, int on_device);
+/* nsteps steps of every instance, instance i with time step dt[i] > 0 (host array) */
 int grmhd_batch_step(grmhd_batch* b, const double* dt, int nsteps);
 int grmhd_batch_destroy(grmhd_batch* b);
+const char* grmhd_batch_last_error(const grmhd_batch* b);
 
 /* Test hook: apply the first derivative along direction dir (0 r, 1 theta, 2 phi) to
  * `nfields` canonical fields (nfields * num_points doubles) with the library's

@@ -58,9 +58,15 @@ SIGNATURES = {
     "grmhd_kernel_times": (C.c_int, [_P, C.c_int, _D, _D, _D, C.c_int]),
     "grmhd_batch_create": (C.c_int, [C.c_int, C.POINTER(Grid), C.POINTER(Physics),
                                      C.POINTER(Opts), _P, C.POINTER(_P)]),
-    "grmhd_batch_instance": (_P, [_P, C.c_int]),
+    "grmhd_batch_num_groups": (C.c_int, [_P]),
+    "grmhd_batch_num_points": (C.c_longlong, [_P, C.c_int]),
+    "grmhd_batch_coords": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "grmhd_batch_init_prims": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P]),
+    "grmhd_batch_set_state": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+    "grmhd_batch_get_state": (C.c_int, [_P, C.c_int, _P, C.c_int]),
     "grmhd_batch_step": (C.c_int, [_P, _D, C.c_int]),
     "grmhd_batch_destroy": (C.c_int, [_P]),
+    "grmhd_batch_last_error": (C.c_char_p, [_P]),
     "grmhd_debug_deriv": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
     "grmhd_cfl_dt_noalloc": (C.c_int, [_P, C.c_longlong, C.c_double, C.c_double, _P, _P]),
     "grmhd_strerror": (C.c_char_p, [C.c_int]),
@@ -202,6 +208,66 @@ class Context:
 
     def debug_deriv(self, src, dst, nfields: int, direction: int):
         self._chk(self.lib.grmhd_debug_deriv(self.h, _ptr(src), _ptr(dst), nfields, direction))
+
+
+class Batch:
+    """Many independent instances advanced together (grmhd_batch_*)."""
+
+    def __init__(self, structs, stream: int = 0):
+        self.lib = load()
+        n = len(structs)
+        grids = (Grid * n)(*[s[0] for s in structs])
+        physs = (Physics * n)(*[s[1] for s in structs])
+        opts = (Opts * n)(*[s[2] for s in structs])
+        h = C.c_void_p()
+        check(self.lib.grmhd_batch_create(n, grids, physs, opts, C.c_void_p(stream or None),
+                                          C.byref(h)))
+        self.h, self.n = h, n
+
+    def _chk(self, st):
+        if st != GRMHD_OK:
+            raise GrmhdError(f"grmhd status {st}: {self.lib.grmhd_strerror(st).decode()}: "
+                             f"{self.lib.grmhd_batch_last_error(self.h).decode()}")
+
+    def num_groups(self):
+        return int(self.lib.grmhd_batch_num_groups(self.h))
+
+    def num_points(self, i):
+        return int(self.lib.grmhd_batch_num_points(self.h, i))
+
+    def coords(self, i):
+        import numpy as np
+        n = self.num_points(i)
+        r, t, p = (np.empty(n) for _ in range(3))
+        self._chk(self.lib.grmhd_batch_coords(self.h, i, _ptr(r), _ptr(t), _ptr(p)))
+        return r, t, p
+
+    def init_prims(self, i, rho, p, vr, vth, vph, A_phi):
+        import numpy as np
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel()
+                for a in (rho, p, vr, vth, vph, A_phi)]
+        self._chk(self.lib.grmhd_batch_init_prims(self.h, i, *[_ptr(a) for a in arrs]))
+
+    def set_state(self, i, state, on_device: bool):
+        self._chk(self.lib.grmhd_batch_set_state(self.h, i, _ptr(state), int(on_device)))
+
+    def get_state(self, i, out, on_device: bool):
+        self._chk(self.lib.grmhd_batch_get_state(self.h, i, _ptr(out), int(on_device)))
+
+    def step(self, dts, nsteps: int):
+        arr = (C.c_double * self.n)(*[float(x) for x in dts])
+        self._chk(self.lib.grmhd_batch_step(self.h, arr, int(nsteps)))
+
+    def close(self):
+        if self.h:
+            self.lib.grmhd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def make_structs(cfg, **opt_overrides):

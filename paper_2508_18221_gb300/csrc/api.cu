@@ -50,11 +50,13 @@ struct grmhd_ctx {
     double* Fs[3];           // reflection-split filter operators
     double* r_scale;         // E
     double* wq;              // P quadrature weights
-    double* hmin;            // 1
-    double* dt;              // 1
+    double* hmin;            // n_inst CFL spacings
+    double* dt;              // n_inst time steps
     double* diag;            // 8
     unsigned long long* nfail;
-    unsigned long long* lam_bits;
+    unsigned long long* lam_bits;   // n_inst
+    unsigned char* iface_dev;       // E: element e coupled to e + 1
+    int* elem_inst_dev;             // E: owning instance
     int* nan_flag;
     DerivJob* jobs;          // all job lists
     // mixed-precision (tensor-core) contractions
@@ -71,6 +73,11 @@ struct grmhd_ctx {
     int job_dbg;
     // host copies
     std::vector<double> r_nodes, th_nodes, ph_nodes, rscale_h;
+    // instances of the group (concatenated along r)
+    int n_inst;
+    std::vector<int> inst_E, inst_off;      // elements per instance, first element
+    std::vector<double> inst_M, inst_a;     // Kerr-Schild background per instance
+    std::vector<int> elem_inst;
     // graph
     cudaGraphExec_t gexec;
     int g_nsteps;
@@ -81,12 +88,15 @@ struct grmhd_ctx {
 };
 
 struct grmhd_batch {
-    int n;
-    grmhd_ctx** inst;
+    int n;                       // instances
+    int ngroups;
+    grmhd_ctx** groups;          // one context per group of compatible instances
+    std::vector<int> grp, idx;   // instance -> (group, index inside the group)
     cudaStream_t stream;
     bool own_stream;
     cudaGraphExec_t gexec;
     int g_nsteps;
+    char err[256];
 };
 
 static int set_err(grmhd_ctx* c, int code, const char* fmt, ...) {
@@ -159,6 +169,8 @@ static void free_ctx(grmhd_ctx* c) {
         if (c->Ds[k]) cudaFree(c->Ds[k]);
         if (c->Fs[k]) cudaFree(c->Fs[k]);
     }
+    if (c->iface_dev) cudaFree(c->iface_dev);
+    if (c->elem_inst_dev) cudaFree(c->elem_inst_dev);
     if (c->nfail) cudaFree(c->nfail);
     if (c->lam_bits) cudaFree(c->lam_bits);
     if (c->nan_flag) cudaFree(c->nan_flag);
@@ -180,20 +192,46 @@ static cudaError_t upload(double* dst, const std::vector<double>& v, cudaStream_
     return cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, s);
 }
 
-extern "C" int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, const grmhd_opts* opts,
-                            void* cuda_stream, grmhd_ctx** out) {
-    if (!out) return GRMHD_EINVAL;
+// Instances that share the node counts, the theta range, the equation of state, the
+// floors and the options form one group: they are concatenated along r as radial
+// elements of one grid (the right-hand side never uses M or a: the background enters
+// only through the initial data), with per-element flags for interface coupling and
+// the outer-boundary freeze and per-instance dt.
+static bool same_group(const grmhd_grid& g0, const grmhd_physics& p0, const grmhd_grid& g,
+                       const grmhd_physics& p) {
+    return g.n_r == g0.n_r && g.n_theta == g0.n_theta && g.n_phi == g0.n_phi &&
+           g.theta_min == g0.theta_min && g.theta_max == g0.theta_max &&
+           p.gamma_eos == p0.gamma_eos && p.rho_atm == p0.rho_atm && p.eps_atm == p0.eps_atm;
+}
+
+static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* physs,
+                      const grmhd_opts* opts, void* cuda_stream, grmhd_ctx** out) {
+    if (!out || ninst < 1 || !grids || !physs || !opts) return GRMHD_EINVAL;
     *out = nullptr;
     char msg[256] = {0};
-    int st = validate(grid, phys, opts, msg);
-    if (st != GRMHD_OK) return st;
+    for (int i = 0; i < ninst; i++) {
+        int st = validate(&grids[i], &physs[i], opts, msg);
+        if (st != GRMHD_OK) return st;
+        if (!same_group(grids[0], physs[0], grids[i], physs[i])) return GRMHD_EINVAL;
+    }
+    const grmhd_grid* grid = &grids[0];
+    const grmhd_physics* phys = &physs[0];
     // value-initialisation zeroes every plain member and constructs the vectors
     grmhd_ctx* c = new (std::nothrow) grmhd_ctx();
     if (!c) return GRMHD_ENOMEM;
     c->grid = *grid;
     c->phys = *phys;
     c->opts = *opts;
-    const int E = grid->n_elem, Nr = grid->n_r, Nt = grid->n_theta, Np = grid->n_phi;
+    c->n_inst = ninst;
+    int E = 0;
+    for (int i = 0; i < ninst; i++) {
+        c->inst_off.push_back(E);
+        c->inst_E.push_back(grids[i].n_elem);
+        c->inst_M.push_back(physs[i].M);
+        c->inst_a.push_back(physs[i].a);
+        E += grids[i].n_elem;
+    }
+    const int Nr = grid->n_r, Nt = grid->n_theta, Np = grid->n_phi;
     c->d.E = E; c->d.Nr = Nr; c->d.Nt = Nt; c->d.Np = Np;
     c->d.NtNp = (long long)Nt * Np;
     c->d.elem = c->d.NtNp * Nr;
@@ -216,20 +254,27 @@ extern "C" int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, c
     std::vector<double> wcgl = quad_weights(Nr, true);
     c->pp.w_end = wcgl[0];
 
-    // grid
-    std::vector<double> bounds(E + 1);
-    for (int e = 0; e <= E; e++)
-        bounds[e] = grid->elem_map == 1 ? grid->r_min * std::pow(grid->r_max / grid->r_min, (double)e / E)
-                                        : grid->r_min + (grid->r_max - grid->r_min) * e / E;
-    bounds[0] = grid->r_min;
-    bounds[E] = grid->r_max;
+    // grid: element bounds of every instance, concatenated
     std::vector<double> xr = cgl_nodes(Nr), xt = gauss_nodes(Nt);
     c->r_nodes.resize((size_t)E * Nr);
     c->rscale_h.resize(E);
-    for (int e = 0; e < E; e++) {
-        double a = bounds[e], b = bounds[e + 1];
-        c->rscale_h[e] = 2.0 / (b - a);
-        for (int i = 0; i < Nr; i++) c->r_nodes[(size_t)e * Nr + i] = 0.5 * (a + b) + 0.5 * (b - a) * xr[i];
+    c->elem_inst.resize(E);
+    std::vector<unsigned char> iface(E, 0);
+    for (int in = 0; in < ninst; in++) {
+        const grmhd_grid& gi = grids[in];
+        const int Ei = gi.n_elem, off = c->inst_off[in];
+        for (int e = 0; e < Ei; e++) {
+            double a = gi.elem_map == 1 ? gi.r_min * std::pow(gi.r_max / gi.r_min, (double)e / Ei)
+                                        : gi.r_min + (gi.r_max - gi.r_min) * e / Ei;
+            double b = gi.elem_map == 1 ? gi.r_min * std::pow(gi.r_max / gi.r_min, (double)(e + 1) / Ei)
+                                        : gi.r_min + (gi.r_max - gi.r_min) * (e + 1) / Ei;
+            if (e == 0) a = gi.r_min;
+            if (e == Ei - 1) b = gi.r_max;
+            c->rscale_h[off + e] = 2.0 / (b - a);
+            for (int i = 0; i < Nr; i++) c->r_nodes[(size_t)(off + e) * Nr + i] = 0.5 * (a + b) + 0.5 * (b - a) * xr[i];
+            c->elem_inst[off + e] = in;
+            iface[off + e] = e < Ei - 1;
+        }
     }
     double tscale = 2.0 / (grid->theta_max - grid->theta_min);
     c->th_nodes.resize(Nt);
@@ -246,7 +291,7 @@ extern "C" int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, c
     // quadrature weights and the CFL spacing
     std::vector<double> wt = quad_weights(Nt, false);
     std::vector<double> wq((size_t)P);
-    double hmin = 1e300;
+    std::vector<double> hmin(ninst, 1e300);
     for (int e = 0; e < E; e++)
         for (int i = 0; i < Nr; i++) {
             const double* rn = &c->r_nodes[(size_t)e * Nr];
@@ -256,7 +301,7 @@ extern "C" int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, c
                 double dth = k == 0 ? tn[1] - tn[0] : (k == Nt - 1 ? tn[k] - tn[k - 1] : std::fmin(tn[k] - tn[k - 1], tn[k + 1] - tn[k]));
                 double r = rn[i];
                 double h = std::fmin(std::fmin(dr, r * dth), r * std::sin(tn[k]) * (2.0 * M_PI / Np));
-                hmin = std::fmin(hmin, h);
+                hmin[c->elem_inst[e]] = std::fmin(hmin[c->elem_inst[e]], h);
                 for (int l = 0; l < Np; l++)
                     wq[(((size_t)e * Nr + i) * Nt + k) * Np + l] =
                         wcgl[i] / c->rscale_h[e] * wt[k] / tscale * (2.0 * M_PI / Np);
@@ -278,13 +323,16 @@ extern "C" int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, c
     AL(c->scratch, NV * P);
     AL(c->Dr, Nr * Nr); AL(c->Dt, Nt * Nt); AL(c->Dp, Np);
     AL(c->Fr, Nr * Nr); AL(c->Ft, Nt * Nt); AL(c->Fp, Np);
-    AL(c->r_scale, E); AL(c->wq, P); AL(c->hmin, 1); AL(c->dt, 1); AL(c->diag, 8);
-    AL(c->nfail, 1); AL(c->lam_bits, 1); AL(c->nan_flag, 1);
+    AL(c->r_scale, E); AL(c->wq, P); AL(c->hmin, ninst); AL(c->dt, ninst); AL(c->diag, 8);
+    AL(c->nfail, 1); AL(c->lam_bits, ninst); AL(c->nan_flag, 1);
+    AL(c->iface_dev, E); AL(c->elem_inst_dev, E);
 #undef AL
     if (ce != cudaSuccess) {
         free_ctx(c);
         return ce == cudaErrorMemoryAllocation ? GRMHD_ENOMEM : GRMHD_ECUDA;
     }
+    c->d.iface_next = c->iface_dev;
+    c->d.elem_inst = c->elem_inst_dev;
     // job lists
     std::vector<DerivJob> jobs;
     auto add = [&](const double* s, double* dd, int acc) { DerivJob j; j.src = s; j.dst = dd; j.accumulate = acc; j.pad = 0; jobs.push_back(j); };
@@ -339,7 +387,10 @@ extern "C" int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, c
         upload(c->Dp, Dp, s) != cudaSuccess || upload(c->Fr, Fr, s) != cudaSuccess ||
         upload(c->Ft, Ft, s) != cudaSuccess || upload(c->Fp, Fp, s) != cudaSuccess ||
         upload(c->r_scale, c->rscale_h, s) != cudaSuccess || upload(c->wq, wq, s) != cudaSuccess ||
-        cudaMemcpyAsync(c->hmin, &hmin, sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        upload(c->hmin, hmin, s) != cudaSuccess ||
+        cudaMemsetAsync(c->dt, 0, sizeof(double) * ninst, s) != cudaSuccess ||
+        cudaMemcpyAsync(c->iface_dev, iface.data(), E, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(c->elem_inst_dev, c->elem_inst.data(), sizeof(int) * E, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(c->prim, 0, sizeof(double) * N_PRIM * P, s) != cudaSuccess ||
         cudaMemsetAsync(c->U[0], 0, sizeof(double) * NV * P, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -411,6 +462,14 @@ extern "C" int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, c
     }
     *out = c;
     return GRMHD_OK;
+}
+
+extern "C" int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, const grmhd_opts* opts,
+                            void* cuda_stream, grmhd_ctx** out) {
+    if (!out) return GRMHD_EINVAL;
+    *out = nullptr;
+    if (!grid || !phys || !opts) return GRMHD_EINVAL;
+    return ctx_create(1, grid, phys, opts, cuda_stream, out);
 }
 
 extern "C" int grmhd_destroy(grmhd_ctx* c) {
@@ -580,27 +639,30 @@ extern "C" int grmhd_get_state(grmhd_ctx* c, double* state, int on_device) {
     return copy_out(c, state, c->U[0], (size_t)NV * c->d.P, on_device);
 }
 
-extern "C" int grmhd_init_prims(grmhd_ctx* c, const double* rho, const double* p, const double* vr,
-                                const double* vth, const double* vph, const double* A_phi) {
-    if (!c || !rho || !p || !vr || !vth || !vph || !A_phi) return GRMHD_EINVAL;
+// Canonical state (GRMHD_NV x P_i, instance-local layout) of instance `in` of the group:
+// Kerr-Schild BSSN data of that instance's background, densitized field from A_phi with
+// the grid operators, conserved variables from the primitives (instance-local arrays).
+static void build_instance_state(const grmhd_ctx* c, int in, const double* rho, const double* p,
+                                 const double* vr, const double* vth, const double* vph,
+                                 const double* A_phi, std::vector<double>& U) {
     const Dims& d = c->d;
-    const long long P = d.P;
-    std::vector<double> U((size_t)NV * P, 0.0);
+    const int Ei = c->inst_E[in], off = c->inst_off[in];
+    const long long Pi = (long long)Ei * d.elem;
+    U.assign((size_t)NV * Pi, 0.0);
     double bssn[24];
     // Kerr-Schild BSSN data depends on (r, theta) only
-    for (int e = 0; e < d.E; e++)
+    for (int e = 0; e < Ei; e++)
         for (int i = 0; i < d.Nr; i++)
             for (int k = 0; k < d.Nt; k++) {
-                ks_bssn_point(c->phys.M, c->phys.a, c->r_nodes[(size_t)e * d.Nr + i], c->th_nodes[k], bssn);
+                ks_bssn_point(c->inst_M[in], c->inst_a[in], c->r_nodes[(size_t)(off + e) * d.Nr + i], c->th_nodes[k], bssn);
                 for (int l = 0; l < d.Np; l++) {
                     size_t pt = (((size_t)e * d.Nr + i) * d.Nt + k) * d.Np + l;
-                    for (int v = 0; v < 24; v++) U[(size_t)v * P + pt] = bssn[v];
+                    for (int v = 0; v < 24; v++) U[(size_t)v * Pi + pt] = bssn[v];
                 }
             }
-    // densitized field from A_phi with the grid operators
     std::vector<double> Dr = cheb_lobatto_D(d.Nr), Dt = cheb_gauss_D(d.Nt);
     double tscale = 2.0 / (c->grid.theta_max - c->grid.theta_min);
-    for (int e = 0; e < d.E; e++)
+    for (int e = 0; e < Ei; e++)
         for (int i = 0; i < d.Nr; i++)
             for (int k = 0; k < d.Nt; k++)
                 for (int l = 0; l < d.Np; l++) {
@@ -610,24 +672,59 @@ extern "C" int grmhd_init_prims(grmhd_ctx* c, const double* rho, const double* p
                         dth += Dt[(size_t)k * d.Nt + j] * A_phi[(((size_t)e * d.Nr + i) * d.Nt + j) * d.Np + l];
                     for (int j = 0; j < d.Nr; j++)
                         drr += Dr[(size_t)i * d.Nr + j] * A_phi[(((size_t)e * d.Nr + j) * d.Nt + k) * d.Np + l];
-                    U[(size_t)V_B * P + pt] = dth * tscale;
-                    U[(size_t)(V_B + 1) * P + pt] = -drr * c->rscale_h[e];
-                    U[(size_t)(V_B + 2) * P + pt] = 0.0;
+                    U[(size_t)V_B * Pi + pt] = dth * tscale;
+                    U[(size_t)(V_B + 1) * Pi + pt] = -drr * c->rscale_h[off + e];
+                    U[(size_t)(V_B + 2) * Pi + pt] = 0.0;
                 }
-    for (long long pt = 0; pt < P; pt++) {
+    for (long long pt = 0; pt < Pi; pt++) {
         double b[24];
-        for (int v = 0; v < 24; v++) b[v] = U[(size_t)v * P + pt];
+        for (int v = 0; v < 24; v++) b[v] = U[(size_t)v * Pi + pt];
         double g[3][3], sqg;
         metric_from_bssn_point(b, g, &sqg);
-        double B_u[3] = {U[(size_t)V_B * P + pt] / sqg, U[(size_t)(V_B + 1) * P + pt] / sqg, U[(size_t)(V_B + 2) * P + pt] / sqg};
+        double B_u[3] = {U[(size_t)V_B * Pi + pt] / sqg, U[(size_t)(V_B + 1) * Pi + pt] / sqg, U[(size_t)(V_B + 2) * Pi + pt] / sqg};
         double v_u[3] = {vr[pt], vth[pt], vph[pt]};
         double D, S[3], tau;
         prim_to_cons_point(rho[pt], p[pt], v_u, B_u, g, c->phys.gamma_eos, &D, S, &tau);
-        U[(size_t)V_D * P + pt] = sqg * D;
-        for (int j = 0; j < 3; j++) U[(size_t)(V_S + j) * P + pt] = sqg * S[j];
-        U[(size_t)V_TAU * P + pt] = sqg * tau;
+        U[(size_t)V_D * Pi + pt] = sqg * D;
+        for (int j = 0; j < 3; j++) U[(size_t)(V_S + j) * Pi + pt] = sqg * S[j];
+        U[(size_t)V_TAU * Pi + pt] = sqg * tau;
     }
-    return grmhd_set_state(c, U.data(), 0);
+}
+
+// copy an instance-local canonical array into / out of the group's state (row v of the
+// instance is a contiguous block at element offset inst_off in row v of the group)
+static int inst_copy(grmhd_ctx* c, int in, double* dev_rows, long long rows, const double* src, double* dst,
+                     int on_device, int to_device) {
+    const long long Pi = (long long)c->inst_E[in] * c->d.elem;
+    const size_t w = (size_t)Pi * sizeof(double), gp = (size_t)c->d.P * sizeof(double);
+    double* base = dev_rows + (long long)c->inst_off[in] * c->d.elem;
+    cudaMemcpyKind k = to_device ? (on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice)
+                                 : (on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+    if (to_device) CK(cudaMemcpy2DAsync(base, gp, src, w, w, (size_t)rows, k, c->stream));
+    else CK(cudaMemcpy2DAsync(dst, w, base, gp, w, (size_t)rows, k, c->stream));
+    if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    return GRMHD_OK;
+}
+
+static int inst_set_state(grmhd_ctx* c, int in, const double* state, int on_device) {
+    const long long Pi = (long long)c->inst_E[in] * c->d.elem;
+    // reset this instance's primitive guess (the next recovery starts from a bracket)
+    CK(cudaMemset2DAsync(c->prim + (long long)c->inst_off[in] * c->d.elem, (size_t)c->d.P * sizeof(double), 0,
+                         (size_t)Pi * sizeof(double), N_PRIM, c->stream));
+    return inst_copy(c, in, c->U[0], NV, state, nullptr, on_device, 1);
+}
+
+extern "C" int grmhd_init_prims(grmhd_ctx* c, const double* rho, const double* p, const double* vr,
+                                const double* vth, const double* vph, const double* A_phi) {
+    if (!c || !rho || !p || !vr || !vth || !vph || !A_phi) return GRMHD_EINVAL;
+    std::vector<double> U;
+    for (int in = 0; in < c->n_inst; in++) {
+        const long long o = (long long)c->inst_off[in] * c->d.elem;
+        build_instance_state(c, in, rho + o, p + o, vr + o, vth + o, vph + o, A_phi + o, U);
+        int st = inst_set_state(c, in, U.data(), 0);
+        if (st) return st;
+    }
+    return GRMHD_OK;
 }
 
 extern "C" int grmhd_rhs(grmhd_ctx* c, double* out, int on_device) {
@@ -662,7 +759,7 @@ extern "C" int grmhd_con2prim(grmhd_ctx* c, double* prim_out, int on_device, lon
 
 extern "C" int grmhd_cfl_dt(grmhd_ctx* c, double* dt) {
     if (!c || !dt) return GRMHD_EINVAL;
-    CK(launch_cfl(c->d, c->U[0], c->hmin, c->opts.cfl, c->dt, (unsigned int*)c->lam_bits, c->stream));
+    CK(launch_cfl(c->d, c->n_inst, c->U[0], c->hmin, c->opts.cfl, c->dt, c->lam_bits, c->stream));
     CK(cudaMemcpyAsync(dt, c->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return GRMHD_OK;
@@ -675,7 +772,7 @@ static int build_graph(grmhd_ctx* c, int nsteps, int auto_dt) {
     int st = GRMHD_OK;
     c->launches_tmp = 0;
     if (auto_dt) {
-        cudaError_t e = launch_cfl(c->d, c->U[0], c->hmin, c->opts.cfl, c->dt, (unsigned int*)c->lam_bits, c->stream);
+        cudaError_t e = launch_cfl(c->d, c->n_inst, c->U[0], c->hmin, c->opts.cfl, c->dt, c->lam_bits, c->stream);
         if (e != cudaSuccess) st = set_err(c, GRMHD_ECUDA, "cfl: %s", cudaGetErrorString(e));
         c->launches_tmp += 2;
     }
@@ -699,7 +796,8 @@ extern "C" int grmhd_step(grmhd_ctx* c, double dt, int nsteps, double* dt_used) 
         int st = build_graph(c, nsteps, auto_dt);
         if (st) return st;
     }
-    if (!auto_dt) CK(cudaMemcpyAsync(c->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    std::vector<double> dts(c->n_inst, dt);
+    if (!auto_dt) CK(cudaMemcpyAsync(c->dt, dts.data(), sizeof(double) * c->n_inst, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(c->nfail, 0, sizeof(unsigned long long), c->stream));
     CK(cudaGraphLaunch(c->gexec, c->stream));
     CK(cudaMemsetAsync(c->nan_flag, 0, sizeof(int), c->stream));
@@ -889,6 +987,15 @@ extern "C" const char* grmhd_strerror(int s) {
 extern "C" const char* grmhd_last_error(const grmhd_ctx* c) { return c ? c->err : "no context"; }
 
 // ------------------------------------------------------------------ batch
+#define BCK(call)                                                                      \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            snprintf(b->err, sizeof(b->err), "%s: %s", #call, cudaGetErrorString(e_)); \
+            return GRMHD_ECUDA;                                                        \
+        }                                                                              \
+    } while (0)
+
 extern "C" int grmhd_batch_create(int n, const grmhd_grid* grids, const grmhd_physics* phys,
                                   const grmhd_opts* opts, void* cuda_stream, grmhd_batch** out) {
     if (!out || n < 1 || !grids || !phys || !opts) return GRMHD_EINVAL;
@@ -901,56 +1008,126 @@ extern "C" int grmhd_batch_create(int n, const grmhd_grid* grids, const grmhd_ph
         b->own_stream = true;
     }
     b->n = n;
-    b->inst = new (std::nothrow) grmhd_ctx*[n]();
-    if (!b->inst) { grmhd_batch_destroy(b); return GRMHD_ENOMEM; }
+    b->grp.assign(n, -1);
+    b->idx.assign(n, -1);
+    // group compatible instances (same node counts, theta range, EOS, floors, options)
+    std::vector<std::vector<int>> members;
     for (int i = 0; i < n; i++) {
-        int st = grmhd_create(&grids[i], &phys[i], &opts[i], b->stream, &b->inst[i]);
+        int g = -1;
+        for (size_t k = 0; k < members.size(); k++) {
+            int f = members[k][0];
+            if (same_group(grids[f], phys[f], grids[i], phys[i]) && std::memcmp(&opts[f], &opts[i], sizeof(grmhd_opts)) == 0) {
+                g = (int)k;
+                break;
+            }
+        }
+        if (g < 0) { members.emplace_back(); g = (int)members.size() - 1; }
+        b->grp[i] = g;
+        b->idx[i] = (int)members[g].size();
+        members[g].push_back(i);
+    }
+    b->ngroups = (int)members.size();
+    b->groups = new (std::nothrow) grmhd_ctx*[b->ngroups]();
+    if (!b->groups) { grmhd_batch_destroy(b); return GRMHD_ENOMEM; }
+    for (int g = 0; g < b->ngroups; g++) {
+        std::vector<grmhd_grid> gg;
+        std::vector<grmhd_physics> pp;
+        for (int i : members[g]) { gg.push_back(grids[i]); pp.push_back(phys[i]); }
+        int st = ctx_create((int)gg.size(), gg.data(), pp.data(), &opts[members[g][0]], b->stream, &b->groups[g]);
         if (st) { grmhd_batch_destroy(b); return st; }
     }
     *out = b;
     return GRMHD_OK;
 }
 
-extern "C" grmhd_ctx* grmhd_batch_instance(grmhd_batch* b, int i) {
-    return (b && i >= 0 && i < b->n) ? b->inst[i] : nullptr;
+extern "C" int grmhd_batch_num_groups(const grmhd_batch* b) { return b ? b->ngroups : -1; }
+
+extern "C" long long grmhd_batch_num_points(const grmhd_batch* b, int i) {
+    if (!b || i < 0 || i >= b->n) return -1;
+    const grmhd_ctx* c = b->groups[b->grp[i]];
+    return (long long)c->inst_E[b->idx[i]] * c->d.elem;
+}
+
+extern "C" int grmhd_batch_coords(const grmhd_batch* b, int i, double* r, double* th, double* ph) {
+    if (!b || i < 0 || i >= b->n) return GRMHD_EINVAL;
+    const grmhd_ctx* c = b->groups[b->grp[i]];
+    const int in = b->idx[i], off = c->inst_off[in];
+    const Dims& d = c->d;
+    for (int e = 0; e < c->inst_E[in]; e++)
+        for (int ii = 0; ii < d.Nr; ii++)
+            for (int k = 0; k < d.Nt; k++)
+                for (int l = 0; l < d.Np; l++) {
+                    size_t p = (((size_t)e * d.Nr + ii) * d.Nt + k) * d.Np + l;
+                    if (r) r[p] = c->r_nodes[(size_t)(off + e) * d.Nr + ii];
+                    if (th) th[p] = c->th_nodes[k];
+                    if (ph) ph[p] = c->ph_nodes[l];
+                }
+    return GRMHD_OK;
+}
+
+extern "C" int grmhd_batch_init_prims(grmhd_batch* b, int i, const double* rho, const double* p,
+                                      const double* vr, const double* vth, const double* vph,
+                                      const double* A_phi) {
+    if (!b || i < 0 || i >= b->n || !rho || !p || !vr || !vth || !vph || !A_phi) return GRMHD_EINVAL;
+    grmhd_ctx* c = b->groups[b->grp[i]];
+    std::vector<double> U;
+    build_instance_state(c, b->idx[i], rho, p, vr, vth, vph, A_phi, U);
+    return inst_set_state(c, b->idx[i], U.data(), 0);
+}
+
+extern "C" int grmhd_batch_set_state(grmhd_batch* b, int i, const double* state, int on_device) {
+    if (!b || i < 0 || i >= b->n || !state) return GRMHD_EINVAL;
+    return inst_set_state(b->groups[b->grp[i]], b->idx[i], state, on_device);
+}
+
+extern "C" int grmhd_batch_get_state(grmhd_batch* b, int i, double* state, int on_device) {
+    if (!b || i < 0 || i >= b->n || !state) return GRMHD_EINVAL;
+    grmhd_ctx* c = b->groups[b->grp[i]];
+    return inst_copy(c, b->idx[i], c->U[0], NV, nullptr, state, on_device, 0);
 }
 
 extern "C" int grmhd_batch_step(grmhd_batch* b, const double* dt, int nsteps) {
     if (!b || !dt || nsteps < 1) return GRMHD_EINVAL;
     for (int i = 0; i < b->n; i++)
         if (!(dt[i] > 0.0)) return GRMHD_EINVAL;
-    grmhd_ctx* c = b->inst[0];
     if (!b->gexec || b->g_nsteps != nsteps) {
         if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
         cudaGraph_t g = nullptr;
-        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         int st = GRMHD_OK;
         for (int s = 0; s < nsteps && st == GRMHD_OK; s++)
-            for (int i = 0; i < b->n && st == GRMHD_OK; i++) st = enqueue_step(b->inst[i]);
+            for (int k = 0; k < b->ngroups && st == GRMHD_OK; k++) st = enqueue_step(b->groups[k]);
         cudaError_t e = cudaStreamEndCapture(b->stream, &g);
         if (st) { if (g) cudaGraphDestroy(g); return st; }
-        if (e != cudaSuccess) return set_err(c, GRMHD_ECUDA, "batch capture: %s", cudaGetErrorString(e));
+        BCK(e);
         e = cudaGraphInstantiate(&b->gexec, g, 0);
         cudaGraphDestroy(g);
-        if (e != cudaSuccess) return set_err(c, GRMHD_ECUDA, "batch instantiate: %s", cudaGetErrorString(e));
+        BCK(e);
         b->g_nsteps = nsteps;
     }
-    for (int i = 0; i < b->n; i++)
-        CK(cudaMemcpyAsync(b->inst[i]->dt, &dt[i], sizeof(double), cudaMemcpyHostToDevice, b->stream));
-    CK(cudaGraphLaunch(b->gexec, b->stream));
-    CK(cudaStreamSynchronize(b->stream));
+    for (int k = 0; k < b->ngroups; k++) {
+        grmhd_ctx* c = b->groups[k];
+        std::vector<double> dts(c->n_inst);
+        for (int i = 0; i < b->n; i++)
+            if (b->grp[i] == k) dts[b->idx[i]] = dt[i];
+        BCK(cudaMemcpyAsync(c->dt, dts.data(), sizeof(double) * c->n_inst, cudaMemcpyHostToDevice, b->stream));
+    }
+    BCK(cudaGraphLaunch(b->gexec, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
     return GRMHD_OK;
 }
 
 extern "C" int grmhd_batch_destroy(grmhd_batch* b) {
     if (!b) return GRMHD_EINVAL;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    if (b->inst) {
-        for (int i = 0; i < b->n; i++)
-            if (b->inst[i]) grmhd_destroy(b->inst[i]);
-        delete[] b->inst;
+    if (b->groups) {
+        for (int g = 0; g < b->ngroups; g++)
+            if (b->groups[g]) grmhd_destroy(b->groups[g]);
+        delete[] b->groups;
     }
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return GRMHD_OK;
 }
+
+extern "C" const char* grmhd_batch_last_error(const grmhd_batch* b) { return b ? b->err : "no batch"; }

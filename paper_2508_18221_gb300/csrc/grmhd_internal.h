@@ -33,6 +33,9 @@ struct Dims {
     long long P;          // points
     long long NtNp;       // points per radial shell
     long long elem;       // points per element
+    // element topology of a group of instances concatenated along r (device pointers)
+    const unsigned char* iface_next;  // [E] 1: element e is coupled to e + 1
+    const int* elem_inst;             // [E] instance owning element e
 };
 
 struct PhysParams {
@@ -88,8 +91,9 @@ cudaError_t launch_iface_avg(const Dims& d, double* base, long long field_stride
                              cudaStream_t s);
 cudaError_t launch_iface_avg_f(const Dims& d, float* base, long long field_stride, int nfields,
                                cudaStream_t s);
-cudaError_t launch_cfl(const Dims& d, const double* U, const double* hmin_dev, double cfl,
-                       double* dt_dev, unsigned int* lam_bits, cudaStream_t s);
+// per instance: dt[i] = cfl * hmin[i] / max over its nodes of lambda
+cudaError_t launch_cfl(const Dims& d, int n_inst, const double* U, const double* hmin_dev, double cfl,
+                       double* dt_dev, unsigned long long* lam_bits, cudaStream_t s);
 cudaError_t launch_diag(const Dims& d, const PhysParams& pp, const double* U,
                         const double* prim, const double* wq, const double* divB,
                         double* out_dev, cudaStream_t s);

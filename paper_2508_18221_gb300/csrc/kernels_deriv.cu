@@ -90,6 +90,7 @@ __global__ void k_iface_avg(Dims d, T* base, long long fstride, int nfields) {
     long long r = t % nif;
     int e = (int)(r / d.NtNp);
     long long kl = r % d.NtNp;
+    if (!d.iface_next[e]) return;  // instance boundary inside a batch group
     T* u = base + f * fstride;
     long long pl = (long long)e * d.elem + (long long)(d.Nr - 1) * d.NtNp + kl;
     long long pr = pl + d.NtNp;
@@ -123,7 +124,9 @@ __global__ void k_cfl_lam(Dims d, const double* __restrict__ U, unsigned long lo
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long P = d.P;
     double lam = 0.0;
+    int inst = -1;
     if (p < P) {
+        inst = d.elem_inst[p / d.elem];
         double e4 = exp(4.0 * U[V_PHI * P + p]);
         double b[3] = {U[V_BETA * P + p], U[(V_BETA + 1) * P + p], U[(V_BETA + 2) * P + p]};
         const int sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
@@ -134,24 +137,31 @@ __global__ void k_cfl_lam(Dims d, const double* __restrict__ U, unsigned long lo
         lam = sqrt(e4 * bb) + fmax(al, sqrt(2.0 * al));
         if (!(lam >= 0.0)) lam = INFINITY;
     }
-    for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(bits, (unsigned long long)__double_as_longlong(lam));
+    // warp maximum when the whole warp belongs to one instance, else one atomic per node
+    const int i0 = __shfl_sync(0xffffffffu, inst, 0);
+    if (__all_sync(0xffffffffu, inst == i0)) {
+        for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+        if ((threadIdx.x & 31) == 0 && i0 >= 0) atomicMax(&bits[i0], (unsigned long long)__double_as_longlong(lam));
+    } else if (inst >= 0) {
+        atomicMax(&bits[inst], (unsigned long long)__double_as_longlong(lam));
+    }
 }
 
-__global__ void k_cfl_dt(const unsigned long long* bits, const double* hmin, double cfl,
+__global__ void k_cfl_dt(int n_inst, const unsigned long long* bits, const double* hmin, double cfl,
                          double* dt) {
-    double lam = __longlong_as_double((long long)*bits);
-    *dt = cfl * (*hmin) / lam;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inst) return;
+    double lam = __longlong_as_double((long long)bits[i]);
+    dt[i] = cfl * hmin[i] / lam;
 }
 
-cudaError_t launch_cfl(const Dims& d, const double* U, const double* hmin_dev, double cfl,
-                       double* dt_dev, unsigned int* lam_bits, cudaStream_t s) {
-    unsigned long long* bits = reinterpret_cast<unsigned long long*>(lam_bits);
-    cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned long long), s);
+cudaError_t launch_cfl(const Dims& d, int n_inst, const double* U, const double* hmin_dev, double cfl,
+                       double* dt_dev, unsigned long long* bits, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n_inst, s);
     if (e != cudaSuccess) return e;
     int bs = 256;
     k_cfl_lam<<<(unsigned)((d.P + bs - 1) / bs), bs, 0, s>>>(d, U, bits);
-    k_cfl_dt<<<1, 1, 0, s>>>(bits, hmin_dev, cfl, dt_dev);
+    k_cfl_dt<<<(n_inst + 127) / 128, 128, 0, s>>>(n_inst, bits, hmin_dev, cfl, dt_dev);
     return cudaGetLastError();
 }
 

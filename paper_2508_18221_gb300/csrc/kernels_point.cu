@@ -419,8 +419,8 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
         const long long ir = (p / shell) % d.Nr;
         const int e = (int)(p / d.elem);
         int side = 0;
-        if (ir == d.Nr - 1 && e < d.E - 1) side = +1;
-        if (ir == 0 && e > 0) side = -1;
+        if (ir == d.Nr - 1 && d.iface_next[e]) side = +1;
+        if (ir == 0 && e > 0 && d.iface_next[e - 1]) side = -1;
         if (side != 0) {
             long long pl = side > 0 ? p : p - shell;
             long long pr_ = side > 0 ? p + shell : p;
@@ -622,16 +622,16 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
         }
     }
 
-    // frozen outer boundary node
+    // frozen outer boundary node of each instance
+    const int elem_id = (int)(p / d.elem);
     {
         const long long ir = (p / d.NtNp) % d.Nr;
-        const int e = (int)(p / d.elem);
-        if (e == d.E - 1 && ir == d.Nr - 1)
+        if (ir == d.Nr - 1 && !d.iface_next[elem_id])
             for (int v = 0; v < NV; v++) rhs[v] = R(0);
     }
 
     // ------------------------------------------------------------ output
-    const double dt = dt_dev ? *dt_dev : 0.0;
+    const double dt = dt_dev ? dt_dev[d.elem_inst[elem_id]] : 0.0;
     if (co.acc_mode < 0) {
         for (int v = 0; v < NV; v++) out[v * P + p] = (double)rhs[v];
         return;
