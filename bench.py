@@ -35,7 +35,71 @@ WORKLOADS = {
            "100 SSP-RK3 steps (CFL 0.3) per bench step in one CUDA graph", 100),
     "c5": ("c5: a=0.94, 16 radial elements r in [1.3,500], N_r=32 N_theta=64 N_phi=128, "
            "200 SSP-RK3 steps (CFL 0.3) per bench step in one CUDA graph", 200),
+    "c4": ("c4: 256 independent instances, a ~ U[0,0.99], 2-8 radial elements, "
+           "N_r = N_theta in {8,12,16,24,32}, N_phi in {16,32,64}, Bondi-like profiles; "
+           "10 SSP-RK3 steps per bench step, all instances in one CUDA graph", 10),
 }
+
+
+def run_batch(args):
+    """Batched workload: instances grouped by shape, each group one element-concatenated
+    grid; value = aggregate point-updates/s, also instance-steps/s."""
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    import paper_2508_18221_gb300 as pkg
+    from workloads import batch_configs, primitive_profiles
+    cfgs = batch_configs(256)
+    desc, nsteps = WORKLOADS["c4"]
+    stream = torch.cuda.Stream()
+    batch = pkg.Batch([pkg.make_structs(c, precision=args.precision) for c in cfgs], stream.cuda_stream)
+    npts = 0
+    states = []
+    for i, c in enumerate(cfgs):
+        r, t, ph = batch.coords(i)
+        pr = primitive_profiles(c, r.reshape(c.shape), t.reshape(c.shape), ph.reshape(c.shape))
+        batch.init_prims(i, pr["rho"], pr["p"], pr["vr"], pr["vth"], pr["vph"], pr["A_phi"])
+        st = torch.empty(pkg.NV * batch.num_points(i), dtype=torch.float64, device="cuda")
+        batch.get_state(i, st, True)
+        states.append(st)
+        npts += batch.num_points(i)
+    dts = batch.cfl_dt()
+
+    def one(ev=None):
+        for i in range(len(cfgs)):
+            batch.set_state(i, states[i], True)
+        torch.cuda.synchronize()
+        if ev:
+            ev[0].record(stream)
+        batch.step(dts, nsteps)
+        if ev:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            one(evs[k])
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    value = npts * RHS_PER_STEP * nsteps * args.steps / (ms * 1e-3)
+    line = {"metric": "batched " + metric_name(args.precision), "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE[args.precision],
+            "data": "synthetic (seeded Bondi-like profiles, splitmix64 noise)",
+            "config": {"workload": desc, "precision": args.precision, "instances": len(cfgs),
+                       "nodes": npts, "groups": batch.num_groups(),
+                       "instance_steps_per_s": len(cfgs) * nsteps * args.steps / (ms * 1e-3)},
+            "gpu_launches": batch.launch_count() * nsteps * args.steps,
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
 
 
 def metric_name(precision):
@@ -317,6 +381,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c4":
+        run_batch(args)
     else:
         run_gpu(args)
 

@@ -201,6 +201,10 @@ int grmhd_batch_init_prims(grmhd_batch* b, int i, const double* rho, const doubl
 /* canonical state of instance i in / out (layout and on_device as grmhd_set_state) */
 int grmhd_batch_set_state(grmhd_batch* b, int i, const double* state, int on_device);
 int grmhd_batch_get_state(grmhd_batch* b, int i, double* state, int on_device);
+/* CFL time step of every instance's current state (dt_out: host array of n) */
+int grmhd_batch_cfl_dt(grmhd_batch* b, double* dt_out);
+/* kernel launches per step issued by the last grmhd_batch_step (all groups) */
+long long grmhd_batch_launch_count(const grmhd_batch* b);
 /* nsteps steps of every instance, instance i with time step dt[i] > 0 (host array) */
 int grmhd_batch_step(grmhd_batch* b, const double* dt, int nsteps);
 int grmhd_batch_destroy(grmhd_batch* b);

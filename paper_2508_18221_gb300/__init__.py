@@ -65,6 +65,8 @@ SIGNATURES = {
     "grmhd_batch_set_state": (C.c_int, [_P, C.c_int, _P, C.c_int]),
     "grmhd_batch_get_state": (C.c_int, [_P, C.c_int, _P, C.c_int]),
     "grmhd_batch_step": (C.c_int, [_P, _D, C.c_int]),
+    "grmhd_batch_cfl_dt": (C.c_int, [_P, _D]),
+    "grmhd_batch_launch_count": (C.c_longlong, [_P]),
     "grmhd_batch_destroy": (C.c_int, [_P]),
     "grmhd_batch_last_error": (C.c_char_p, [_P]),
     "grmhd_debug_deriv": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
@@ -257,6 +259,14 @@ class Batch:
     def step(self, dts, nsteps: int):
         arr = (C.c_double * self.n)(*[float(x) for x in dts])
         self._chk(self.lib.grmhd_batch_step(self.h, arr, int(nsteps)))
+
+    def cfl_dt(self):
+        arr = (C.c_double * self.n)()
+        self._chk(self.lib.grmhd_batch_cfl_dt(self.h, arr))
+        return list(arr)
+
+    def launch_count(self):
+        return int(self.lib.grmhd_batch_launch_count(self.h))
 
     def close(self):
         if self.h:

@@ -96,6 +96,7 @@ struct grmhd_batch {
     bool own_stream;
     cudaGraphExec_t gexec;
     int g_nsteps;
+    long long launches_per_step;
     char err[256];
 };
 
@@ -1086,6 +1087,22 @@ extern "C" int grmhd_batch_get_state(grmhd_batch* b, int i, double* state, int o
     return inst_copy(c, b->idx[i], c->U[0], NV, nullptr, state, on_device, 0);
 }
 
+extern "C" int grmhd_batch_cfl_dt(grmhd_batch* b, double* dt_out) {
+    if (!b || !dt_out) return GRMHD_EINVAL;
+    for (int k = 0; k < b->ngroups; k++) {
+        grmhd_ctx* c = b->groups[k];
+        BCK(launch_cfl(c->d, c->n_inst, c->U[0], c->hmin, c->opts.cfl, c->dt, c->lam_bits, b->stream));
+        std::vector<double> dts(c->n_inst);
+        BCK(cudaMemcpyAsync(dts.data(), c->dt, sizeof(double) * c->n_inst, cudaMemcpyDeviceToHost, b->stream));
+        BCK(cudaStreamSynchronize(b->stream));
+        for (int i = 0; i < b->n; i++)
+            if (b->grp[i] == k) dt_out[i] = dts[b->idx[i]];
+    }
+    return GRMHD_OK;
+}
+
+extern "C" long long grmhd_batch_launch_count(const grmhd_batch* b) { return b ? b->launches_per_step : -1; }
+
 extern "C" int grmhd_batch_step(grmhd_batch* b, const double* dt, int nsteps) {
     if (!b || !dt || nsteps < 1) return GRMHD_EINVAL;
     for (int i = 0; i < b->n; i++)
@@ -1095,8 +1112,14 @@ extern "C" int grmhd_batch_step(grmhd_batch* b, const double* dt, int nsteps) {
         cudaGraph_t g = nullptr;
         BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         int st = GRMHD_OK;
+        long long launches = 0;
         for (int s = 0; s < nsteps && st == GRMHD_OK; s++)
-            for (int k = 0; k < b->ngroups && st == GRMHD_OK; k++) st = enqueue_step(b->groups[k]);
+            for (int k = 0; k < b->ngroups && st == GRMHD_OK; k++) {
+                b->groups[k]->launches_tmp = 0;
+                st = enqueue_step(b->groups[k]);
+                launches += b->groups[k]->launches_tmp;
+            }
+        b->launches_per_step = launches / nsteps;
         cudaError_t e = cudaStreamEndCapture(b->stream, &g);
         if (st) { if (g) cudaGraphDestroy(g); return st; }
         BCK(e);
