@@ -71,14 +71,23 @@ typedef struct {
     double rho_atm, eps_atm;
 } grmhd_physics;
 
-/* Options.  precision: 0 = FP64 everywhere.  integrator: 0 SSP-RK3, 1 RK4.
+/* Options.  precision: 0 = FP64 values everywhere; 1 = mixed: derivative contractions
+ * as split-BF16 x3 tensor-core products with FP32 results and the BSSN / Valencia
+ * algebra in FP32, while the metric determinant and inverse, the conformal factor, the
+ * interface penalty, the Runge-Kutta sums, the primitive recovery and the filter stay
+ * FP64; 2 = as 1 with TF32 products (at most 128 nodes per direction for 1 and 2).
+ * integrator: 0 SSP-RK3, 1 RK4.
  * evolve_metric: 1 evolve BSSN + gauge, 0 keep the metric fixed (RHS of variables
  * 0-23 is zero).  gauge: 0 1+log + Gamma-driver with damping eta, 1 frozen lapse/shift.
  * filter: bits 0/1/2 filter the Valencia variables in r/theta/phi, bits 3/4/5 the BSSN
  * variables in r/theta/phi (default 47: all but theta for BSSN); filt_alpha, filt_p are
  * the exponential-filter constants (paper: 36, 8); dealias23_phi applies the 2/3 rule
  * in phi.  cfl: Courant factor for dt <= 0.  c2p_maxit, c2p_tol: Newton iteration
- * limit and relative tolerance of the primitive recovery. */
+ * limit and relative tolerance of the primitive recovery.  contraction: how the FP64
+ * spectral contractions (all derivatives at precision 0, the filter at every precision)
+ * run: 0 (default) on the BF16 tensor cores with exact base-256 digit slices of the
+ * FP64 values (Ozaki splitting; error about 2^-53 of sum_j |D_ij| max_j |u_j|, directions
+ * with more than 64 nodes fall back to 1), 1 on the FP64 units. */
 typedef struct {
     int precision;
     int integrator;
@@ -90,6 +99,7 @@ typedef struct {
     int dealias23_phi;
     int c2p_maxit;
     double c2p_tol;
+    int contraction;
 } grmhd_opts;
 
 typedef struct grmhd_ctx grmhd_ctx;

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrmhd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["kernels_point.cu", "kernels_deriv.cu", "kernels_eo.cu", "kernels_tc.cu", "api.cu",
+CU = ["kernels_point.cu", "kernels_deriv.cu", "kernels_eo.cu", "kernels_tc.cu", "kernels_fx.cu", "api.cu",
       "noalloc.cu"]
 CPP = ["host_ops.cpp"]
 

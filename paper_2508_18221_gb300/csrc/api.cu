@@ -61,6 +61,11 @@ struct grmhd_ctx {
     DerivJob* jobs;          // all job lists
     // mixed-precision (tensor-core) contractions
     uint8_t* tc_img[3];      // operator images r / theta / phi
+    // FP64-accurate tensor-core contractions (opts.contraction = 0): digit-slice images of
+    // the derivative (radial: one per element, r-scale folded in) and filter operators
+    uint8_t* fx_d[3];
+    uint8_t* fx_f[3];
+    long long fx_estride;    // bytes between the per-element radial derivative images
     TcJob* tcjobs;
     int tc_first[3][3];      // [buffer][dir]
     int tc_second[3];
@@ -128,6 +133,7 @@ extern "C" int grmhd_defaults(grmhd_grid* g, grmhd_physics* ph, grmhd_opts* o) {
         o->precision = 0; o->integrator = 0; o->evolve_metric = 1; o->gauge = 0;
         o->eta = 2.0; o->cfl = 0.3; o->filter = 47; o->filt_alpha = 36.0; o->filt_p = 8.0;
         o->dealias23_phi = 1; o->c2p_maxit = 60; o->c2p_tol = 1e-15;
+        o->contraction = 0;
     }
     return GRMHD_OK;
 }
@@ -155,6 +161,7 @@ static int validate(const grmhd_grid* g, const grmhd_physics* ph, const grmhd_op
     if (o->gauge != 0 && o->gauge != 1) { strcpy(msg, "gauge must be 0 or 1"); return GRMHD_EINVAL; }
     if (!(o->cfl > 0.0) || o->c2p_maxit < 1 || !(o->c2p_tol > 0.0)) { strcpy(msg, "bad cfl / c2p options"); return GRMHD_EINVAL; }
     if (o->filter < 0 || o->filter > 63) { strcpy(msg, "filter mask must be in [0, 63]"); return GRMHD_EINVAL; }
+    if (o->contraction != 0 && o->contraction != 1) { strcpy(msg, "contraction must be 0 or 1"); return GRMHD_EINVAL; }
     return GRMHD_OK;
 }
 
@@ -176,8 +183,11 @@ static void free_ctx(grmhd_ctx* c) {
     if (c->lam_bits) cudaFree(c->lam_bits);
     if (c->nan_flag) cudaFree(c->nan_flag);
     if (c->jobs) cudaFree(c->jobs);
-    for (int k = 0; k < 3; k++)
+    for (int k = 0; k < 3; k++) {
         if (c->tc_img[k]) cudaFree(c->tc_img[k]);
+        if (c->fx_d[k]) cudaFree(c->fx_d[k]);
+        if (c->fx_f[k]) cudaFree(c->fx_f[k]);
+    }
     if (c->tcjobs) cudaFree(c->tcjobs);
     if (c->tc_err) cudaFree(c->tc_err);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -325,7 +335,7 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
     AL(c->Dr, Nr * Nr); AL(c->Dt, Nt * Nt); AL(c->Dp, Np);
     AL(c->Fr, Nr * Nr); AL(c->Ft, Nt * Nt); AL(c->Fp, Np);
     AL(c->r_scale, E); AL(c->wq, P); AL(c->hmin, ninst); AL(c->dt, ninst); AL(c->diag, 8);
-    AL(c->nfail, 1); AL(c->lam_bits, ninst); AL(c->nan_flag, 1);
+    AL(c->nfail, 1); AL(c->lam_bits, ninst); AL(c->nan_flag, 1); AL(c->tc_err, 1);
     AL(c->iface_dev, E); AL(c->elem_inst_dev, E);
 #undef AL
     if (ce != cudaSuccess) {
@@ -416,6 +426,37 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         if (cudaStreamSynchronize(s) != cudaSuccess) { free_ctx(c); return GRMHD_ECUDA; }
     }
     if (kernels_init() != cudaSuccess) { free_ctx(c); return GRMHD_ECUDA; }
+    if (cudaMemsetAsync(c->tc_err, 0, sizeof(int), s) != cudaSuccess) { free_ctx(c); return GRMHD_ECUDA; }
+    // digit-slice images of the FP64 operators (every direction with at most 64 nodes)
+    if (opts->contraction == 0) {
+        const int Ns[3] = {Nr, Nt, Np};
+        std::vector<double> dense_d[3] = {Dr, Dt, circulant(Dp)};
+        std::vector<double> dense_f[3] = {Fr, Ft, circulant(Fp)};
+        for (int k = 0; k < 3; k++) {
+            if (!fx_supported(k, Ns[k])) continue;
+            int np_, kp_, kc_;
+            fx_geometry(Ns[k], &np_, &kp_, &kc_);
+            std::vector<uint8_t> img_f = fx_operator_image(dense_f[k], Ns[k], 1.0, np_, kp_, kc_);
+            std::vector<uint8_t> img_d;
+            if (k == 0) {
+                for (int e = 0; e < E; e++) {
+                    std::vector<uint8_t> one = fx_operator_image(dense_d[k], Ns[k], c->rscale_h[e], np_, kp_, kc_);
+                    c->fx_estride = (long long)one.size();
+                    img_d.insert(img_d.end(), one.begin(), one.end());
+                }
+            } else {
+                img_d = fx_operator_image(dense_d[k], Ns[k], 1.0, np_, kp_, kc_);
+            }
+            if (cudaMalloc(&c->fx_d[k], img_d.size()) != cudaSuccess ||
+                cudaMalloc(&c->fx_f[k], img_f.size()) != cudaSuccess ||
+                cudaMemcpyAsync(c->fx_d[k], img_d.data(), img_d.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(c->fx_f[k], img_f.data(), img_f.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) {
+                free_ctx(c);
+                return GRMHD_ENOMEM;
+            }
+        }
+    }
     // tensor-core operator images and job lists (mixed-precision modes)
     if (opts->precision > 0) {
         const int tf32 = opts->precision == 2;
@@ -454,7 +495,6 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         for (int q = 0; q < N_D2; q++)
             addt(d1f + ((long long)vars2[q] * 3 + 2) * P, d2f + ((long long)q * 6 + 5) * P, 0);
         if (cudaMalloc(&c->tcjobs, tj.size() * sizeof(TcJob)) != cudaSuccess ||
-            cudaMalloc(&c->tc_err, sizeof(int)) != cudaSuccess ||
             cudaMemcpyAsync(c->tcjobs, tj.data(), tj.size() * sizeof(TcJob), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(c->tc_err, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
             free_ctx(c);
@@ -498,10 +538,15 @@ extern "C" int grmhd_coords(const grmhd_ctx* c, double* r, double* th, double* p
 }
 
 // ------------------------------------------------------------------ pipeline
-// One directional contraction of `njobs` fields: the reflection-split kernel when the
-// size has a compiled instance, the dense kernel otherwise.  filter = 1 uses the modal
-// filter operator (unscaled), 0 the derivative (radial: scaled per element).
+// One directional contraction of `njobs` FP64 fields: the digit-sliced tensor-core
+// kernel when the context built its images (opts.contraction = 0, at most 64 nodes),
+// else the reflection-split kernel when the size has a compiled instance, else the dense
+// kernel.  filter = 1 uses the modal filter operator (unscaled), 0 the derivative
+// (radial: scaled per element).
 static cudaError_t contract(grmhd_ctx* c, int dir, int filter, const DerivJob* jobs, int njobs) {
+    const uint8_t* fx = filter ? c->fx_f[dir] : c->fx_d[dir];
+    if (fx) return launch_contract_fx(dir, c->d, jobs, njobs, fx, (dir == 0 && !filter) ? c->fx_estride : 0,
+                                      c->tc_err, c->stream);
     const double* split = filter ? c->Fs[dir] : c->Ds[dir];
     const double* rs = filter ? nullptr : c->r_scale;
     if (split) return launch_deriv_eo(dir, c->d, jobs, njobs, split, filter ? 1 : -1, rs, c->stream);

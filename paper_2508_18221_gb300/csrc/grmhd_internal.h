@@ -65,6 +65,8 @@ struct TcJob {
 // ---- kernel launchers (defined in kernels_*.cu); all return cudaGetLastError()
 // one-time function-attribute setup (shared-memory opt-in); call outside stream capture
 cudaError_t kernels_init();
+cudaError_t eo_init();
+cudaError_t tc_init();
 cudaError_t launch_prep(const Dims& d, const PhysParams& pp, const double* U, double* prim,
                         double* flux, double* tmn, double* lam, unsigned long long* nfail,
                         cudaStream_t s);
@@ -79,6 +81,14 @@ cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, co
 cudaError_t launch_contract_tc(int dir, int in_fp32, const Dims& d, const TcJob* jobs, int njobs,
                                const uint8_t* op_img, int tf32, const double* r_scale, int* err,
                                cudaStream_t s);
+// FP64-accurate contraction on the BF16 tensor cores (kernels_fx.cu): exact digit
+// slices of the FP64 values; op_img from fx_operator_image, img_estride = bytes between
+// per-element images (radial direction) or 0; Np, Kp, KC from fx_geometry
+void fx_geometry(int N, int* Np, int* Kp, int* KC);
+bool fx_supported(int dir, int N);   // 2..64 nodes (even in phi)
+cudaError_t fx_init();
+cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int njobs, const uint8_t* op_img,
+                               long long img_estride, int* err, cudaStream_t s);
 cudaError_t launch_deriv(int dir, const Dims& d, const DerivJob* jobs_dev, int njobs,
                          const double* mat_dev, const double* r_scale_dev, cudaStream_t s);
 // reflection-split contraction (kernels_eo.cu): cudaErrorNotSupported when N has no

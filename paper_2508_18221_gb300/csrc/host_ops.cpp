@@ -9,6 +9,7 @@
 // transforms of the Lobatto and Gauss node sets, and a circulant row for phi.
 #include "host_ops.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -206,6 +207,51 @@ std::vector<uint8_t> tc_operator_image(const std::vector<double>& D, int N, int 
                 std::memcpy(&img[2 * slice + off], &b3, 2);
             }
         }
+    return img;
+}
+
+// Digit slices of the operator rows for the FP64-accurate tensor-core contraction.  Row
+// n of scale * D gets the exponent F_n (largest biased exponent of the row, 0 for a zero
+// row); Y = round(x 2^(1076 - F_n)) is a signed integer with |Y| <= 2^54, and the bytes of
+// Y + 0x80808080808080 minus 128 are its balanced base-256 digits c_1..c_7 (most
+// significant first).  Slice l holds c_l 2^(-8 (l - 1)), exact in BF16.
+std::vector<uint8_t> fx_operator_image(const std::vector<double>& D, int N, double scale, int Np, int Kp,
+                                       int KC) {
+    const int nch = Kp / KC, kcores = KC / 8;
+    const size_t slice = (size_t)Np * KC * 2, chunk = 7 * slice;
+    const size_t bytes = ((size_t)nch * chunk + (size_t)Np * 4 + 15) / 16 * 16;
+    std::vector<uint8_t> img(bytes, 0);
+    std::vector<int32_t> fexp(Np, 0);
+    for (int n = 0; n < N; n++) {
+        int F = 0;
+        for (int k = 0; k < N; k++) {
+            const double x = D[(size_t)n * N + k] * scale;
+            if (x != 0.0) {
+                int ex;
+                std::frexp(x, &ex);
+                F = std::max(F, ex + 1022);
+            }
+        }
+        fexp[n] = F;
+        if (F <= 0) continue;
+        for (int k = 0; k < N; k++) {
+            const double x = D[(size_t)n * N + k] * scale;
+            const long long Y = std::llround(std::ldexp(x, 1076 - F));
+            const unsigned long long Z = (unsigned long long)(Y + 0x80808080808080LL);
+            const int kc = k / KC, kk = k % KC;
+            const size_t off = (size_t)kc * chunk + ((size_t)((n >> 3) * kcores + (kk >> 3))) * 128 + (n & 7) * 16 +
+                               (kk & 7) * 2;
+            for (int q = 1; q <= 7; q++) {
+                const int digit = (int)((Z >> (8 * (7 - q))) & 0xFF) - 128;
+                const float v = std::ldexp((float)digit, -8 * (q - 1));
+                uint32_t u;
+                std::memcpy(&u, &v, 4);
+                const uint16_t b = (uint16_t)(u >> 16);
+                std::memcpy(&img[off + (size_t)(q - 1) * slice], &b, 2);
+            }
+        }
+    }
+    std::memcpy(&img[(size_t)nch * chunk], fexp.data(), (size_t)Np * 4);
     return img;
 }
 

@@ -19,6 +19,12 @@ std::vector<double> circulant(const std::vector<double>& row);
 // operator D (N x N, row = output node) in the tensor-core kernel's shared-memory image:
 // K-major core-matrix layout padded to 16 in both dims; 3 BF16 slices or 1 TF32 copy
 std::vector<uint8_t> tc_operator_image(const std::vector<double>& D, int N, int tf32);
+// operator scale * D (N x N) for the FP64-accurate tensor-core contraction
+// (kernels_fx.cu): per K chunk of KC columns its seven balanced base-256 digit slices
+// (BF16, Np x KC, K-major core-matrix layout), then the Np row exponents (int32);
+// size a multiple of 16 bytes
+std::vector<uint8_t> fx_operator_image(const std::vector<double>& D, int N, double scale, int Np, int Kp,
+                                       int KC);
 // BSSN variables 0..23 of the Kerr-Schild slice at (r, theta)
 void ks_bssn_point(double M, double a, double r, double th, double out[24]);
 void prim_to_cons_point(double rho, double p, const double v_u[3], const double B_u[3],

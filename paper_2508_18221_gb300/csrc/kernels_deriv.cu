@@ -77,6 +77,7 @@ cudaError_t kernels_init() {
     if ((e = cudaFuncSetAttribute(k_deriv<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * 8)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8)) != cudaSuccess) return e;
     if ((e = eo_init()) != cudaSuccess) return e;
+    if ((e = fx_init()) != cudaSuccess) return e;
     return tc_init();
 }
 

@@ -1,0 +1,129 @@
+"""FP64 spectral contractions on the GPU, both kinds: digit-sliced tensor-core products
+(contraction = 0) and FP64 units (contraction = 1), against the oracle's derivative
+operators (coefficient route, numpy FP64).
+
+An FP64 dot product sum_j D_ij u_j is exact to a few units of 2^-53 of
+b_i = sum_j |D_ij| max_j |u_j|; both kinds must stay within 2e-14 b_i of the oracle (the
+oracle's own coefficient route and the library's barycentric matrices differ by about
+1e-15 b_i).  Lines of very different magnitude (1e-100 .. 1e100) check that every line
+is scaled by its own exponent; a NaN must spread over its line only; zero stays zero.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import solver as so
+from workloads import config
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2508_18221_gb300 as pkg
+    if not os.path.exists(pkg.LIB_PATH):
+        from paper_2508_18221_gb300 import _build
+        _build.build()
+    pkg.load()
+    return pkg
+
+
+def _setup(pkg, cfg, contraction):
+    import torch
+    g = so.Grid(so.Params.from_config(cfg))
+    grid, phys, opts = pkg.make_structs(cfg, contraction=contraction)
+    ctx = pkg.Context(grid, phys, opts, torch.cuda.current_stream().cuda_stream)
+    return g, ctx
+
+
+def _abs_ops(g):
+    """|D| per direction from the oracle operators applied to unit vectors."""
+    E, Nr, Nt, Np = g.shape
+    out = []
+    for d, (op, n, ax) in enumerate(((g.d_r, Nr, 1), (g.d_t, Nt, 2), (g.d_p, Np, 3))):
+        cols = []
+        for j in range(n):
+            u = np.zeros(g.shape)
+            idx = [slice(None)] * 4
+            idx[ax] = j
+            u[tuple(idx)] = 1.0
+            cols.append(op(u))
+        out.append(np.abs(np.stack(cols, axis=-1)))   # (..., j) along the last axis
+    return out
+
+
+def _bound(g, absD, u, d):
+    """b = sum_j |D_ij| max_j |u_j| on every node for direction d."""
+    ax = d + 1
+    m = np.max(np.abs(u), axis=ax, keepdims=True)
+    return np.sum(absD[d], axis=-1) * m
+
+
+def _run(pkg, ctx, u, d):
+    import torch
+    src = torch.from_numpy(u.reshape(-1).copy()).cuda()
+    dst = torch.zeros_like(src)
+    ctx.debug_deriv(src, dst, 1, d)
+    return dst.cpu().numpy().reshape(u.shape)
+
+
+@pytest.mark.parametrize("contraction", [0, 1])
+def test_contraction_accuracy(pkg, contraction):
+    cfg = config("c1", n_elem=3, n_r=10, n_theta=9, n_phi=8)
+    g, ctx = _setup(pkg, cfg, contraction)
+    absD = _abs_ops(g)
+    rng = np.random.default_rng(11)
+    ops = (g.d_r, g.d_t, g.d_p)
+    for d in range(3):
+        # values spanning 12 decades inside every line, line magnitudes 1e-100 .. 1e100
+        u = rng.normal(size=g.shape) * 10.0 ** rng.uniform(-6, 6, size=g.shape)
+        line_shape = list(g.shape)
+        line_shape[d + 1] = 1
+        u = u * 10.0 ** rng.integers(-100, 100, size=line_shape)
+        got = _run(pkg, ctx, u, d)
+        ref = ops[d](u)
+        b = _bound(g, absD, u, d)
+        err = np.abs(got - ref) / b
+        assert np.all(np.isfinite(got))
+        assert err.max() <= 2e-14, (d, float(err.max()))
+    ctx.close()
+
+
+@pytest.mark.parametrize("contraction", [0, 1])
+def test_contraction_nan_and_zero(pkg, contraction):
+    cfg = config("c1", n_elem=2, n_r=8, n_theta=8, n_phi=8)
+    g, ctx = _setup(pkg, cfg, contraction)
+    rng = np.random.default_rng(5)
+    for d in range(3):
+        u = rng.normal(size=g.shape)
+        u[1, 3, 4, 5] = np.nan
+        got = _run(pkg, ctx, u, d)
+        line = [1, 3, 4, 5]
+        line[d + 1] = slice(None)
+        bad = np.zeros(g.shape, dtype=bool)
+        bad[tuple(line)] = True
+        assert np.all(np.isnan(got[bad])), d
+        assert np.all(np.isfinite(got[~bad])), d
+        z = _run(pkg, ctx, np.zeros(g.shape), d)
+        assert np.all(z == 0.0), d
+    ctx.close()
+
+
+def test_contraction_sizes(pkg):
+    """Every size class of the tensor-core kernel (K chunks of 16 and 32, Np 16..64) on
+    smooth data."""
+    for nr, nt, nph in ((4, 5, 4), (16, 17, 16), (24, 33, 34), (40, 48, 64), (64, 20, 48)):
+        cfg = config("c1", n_elem=2, n_r=nr, n_theta=nt, n_phi=nph)
+        g, ctx = _setup(pkg, cfg, 0)
+        absD = _abs_ops(g)
+        ops = (g.d_r, g.d_t, g.d_p)
+        u = np.sin(g.R) * np.cos(2 * g.T) * (1.5 + np.sin(3 * g.P)) + 0.1 * g.R
+        for d in range(3):
+            got = _run(pkg, ctx, u, d)
+            err = np.abs(got - ops[d](u)) / _bound(g, absD, u, d)
+            assert err.max() <= 2e-14, ((nr, nt, nph), d, float(err.max()))
+        ctx.close()

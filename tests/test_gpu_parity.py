@@ -37,7 +37,7 @@ def pkg():
 
 def _ctx(pkg, cfg, **kw):
     import torch
-    opt_keys = ("evolve_metric", "gauge", "integrator", "filter")
+    opt_keys = ("evolve_metric", "gauge", "integrator", "filter", "contraction")
     grid, phys, opts = pkg.make_structs(cfg, **{k: v for k, v in kw.items() if k in opt_keys})
     return pkg.Context(grid, phys, opts, torch.cuda.current_stream().cuda_stream)
 
@@ -109,6 +109,7 @@ def _gpu_rhs(pkg, ctx, U):
 
 CASES = [
     ("c1", {}),                                             # 2 elements, 12 x 12 x 16
+    ("c1", {"contraction": 1}),                             # contractions on the FP64 units
     ("c1", {"evolve_metric": 0}),                           # fixed Kerr-Schild metric
     ("c1", {"gauge": 1}),                                   # frozen gauge
     ("c1:ragged", {}),                                      # odd sizes, 3 elements
@@ -140,11 +141,12 @@ def test_rhs_parity(pkg, name, kw):
     ctx.close()
 
 
-def test_derivative_operators(pkg):
+@pytest.mark.parametrize("contraction", [0, 1])
+def test_derivative_operators(pkg, contraction):
     import torch
     cfg = config("c1", n_elem=3, n_r=10, n_theta=9, n_phi=8)
     g, p, U = _oracle(cfg)
-    ctx = _ctx(pkg, cfg)
+    ctx = _ctx(pkg, cfg, contraction=contraction)
     src = torch.from_numpy(U.reshape(-1).copy()).cuda()
     dst = torch.empty_like(src)
     for d, op in enumerate((g.d_r, g.d_t, g.d_p)):
@@ -178,19 +180,19 @@ def test_con2prim_parity(pkg):
     ctx.close()
 
 
-@pytest.mark.parametrize("integrator", [0, 1])
-def test_step_parity(pkg, integrator):
+@pytest.mark.parametrize("integrator,contraction", [(0, 0), (1, 0), (0, 1)])
+def test_step_parity(pkg, integrator, contraction):
     import torch
     cfg = config("c1", n_elem=3, n_r=9, n_theta=10, n_phi=8)
     g, p, U = _oracle(cfg, integrator=integrator)
-    ctx = _ctx(pkg, cfg, integrator=integrator)
+    ctx = _ctx(pkg, cfg, integrator=integrator, contraction=contraction)
     ctx.set_state(torch.from_numpy(U.reshape(-1).copy()).cuda(), True)
     dt = 2e-3
     ctx.step(dt, 2)
     got = np.empty(U.size)
     ctx.get_state(got, False)
     ref = so.rk_step(so.rk_step(U, dt, g, p), dt, g, p)
-    assert_parity(got.reshape(U.shape), ref, f"2 steps integrator {integrator}", U=U)
+    assert_parity(got.reshape(U.shape), ref, f"2 steps integrator {integrator} contraction {contraction}", U=U)
     ctx.close()
 
 
