@@ -15,8 +15,12 @@
 
 namespace gk {
 
-#define SI(i, j) c_sidx[i][j]
-__device__ __constant__ int c_sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+// packed index of the symmetric pair (i, j): 00 01 02 11 12 22 -> 0..5 (a compile-time
+// constant inside unrolled loops, so arrays indexed by it stay in registers)
+__host__ __device__ constexpr int sym_idx(int i, int j) {
+    return i <= j ? i * 3 - i * (i + 1) / 2 + j : j * 3 - j * (j + 1) / 2 + i;
+}
+#define SI(i, j) sym_idx(i, j)
 
 // --------------------------------------------------------------------------- helpers
 __device__ __forceinline__ double det3(const double g[3][3]) {
@@ -60,57 +64,50 @@ __device__ __forceinline__ Dual operator-(double a, Dual b) { return mk(a - b.v,
 __device__ __forceinline__ Dual operator*(Dual a, double b) { return mk(a.v * b, a.d * b); }
 __device__ __forceinline__ Dual operator*(double a, Dual b) { return mk(a * b.v, a * b.d); }
 __device__ __forceinline__ Dual operator/(double a, Dual b) {
-    double q = a / b.v;
-    return mk(q, -q * b.d / b.v);
+    double iv = 1.0 / b.v;
+    double q = a * iv;
+    return mk(q, -q * b.d * iv);
 }
-__device__ __forceinline__ Dual dsqrt(Dual a) {
-    double s = sqrt(a.v);
-    return mk(s, a.d * 0.5 / s);
+// 1/sqrt(a) and its derivative -a'/(2 a^{3/2}) = -a' r^3 / 2 (no division)
+__device__ __forceinline__ Dual drsqrt(Dual a) {
+    double r = rsqrt(a.v);
+    return mk(r, -0.5 * a.d * r * r * r);
 }
+__device__ __forceinline__ double drsqrt(double a) { return rsqrt(a); }
 __device__ __forceinline__ Dual dmin(Dual a, Dual b) { return a.v <= b.v ? a : b; }
 __device__ __forceinline__ Dual dmax(Dual a, Dual b) { return a.v >= b.v ? a : b; }
-__device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ double dmin(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ double dmax(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ double val(double a) { return a; }
 __device__ __forceinline__ double val(Dual a) { return a.v; }
+template <class T> __device__ __forceinline__ T cst(double v);
+template <> __device__ __forceinline__ double cst<double>(double v) { return v; }
+template <> __device__ __forceinline__ Dual cst<Dual>(double v) { return mk(v); }
 
 // Scalar invariants of the conserved state entering the one-variable master function
 // in mu = 1/(h W) (Kastaun, Kalinani & Ciolfi 2021): q = tau/D, r^2 = S^2/D^2,
 // bb = B^2/D, rb2 = (S.B)^2/D^3.
 struct C2PScal {
     double D, q, r2, bb, rb2, gam, eps_min;
+    double v2max;   // r^2 / (1 + r^2), the largest admissible v^2
 };
 
+// One evaluation of the master function (value, or value and d/dmu for T = Dual):
+// 1/W = sqrt(1 - v^2) = (1 - v^2) W, so W comes from one reciprocal square root and h/W
+// needs no division.
 template <class T>
 __device__ __forceinline__ T master(T mu, const C2PScal& c, T* W_o, T* eps_o, T* x_o) {
     T x = 1.0 / (1.0 + mu * c.bb);
     T rbar2 = c.r2 * x * x + mu * x * (1.0 + x) * c.rb2;
     T qbar = c.q - 0.5 * c.bb - 0.5 * mu * mu * x * x * (c.bb * c.r2 - c.rb2);
-    T v2 = dmin(mu * mu * rbar2, T(c.r2 / (1.0 + c.r2)) + 0.0 * mu);
-    T W = 1.0 / dsqrt(1.0 - v2);
+    T v2 = dmin(mu * mu * rbar2, cst<T>(c.v2max));
+    T om = 1.0 - v2;
+    T W = drsqrt(om);
     T eps = W * (qbar - mu * rbar2) + v2 * W * W / (1.0 + W);
-    T eps_c = dmax(eps, T(c.eps_min) + 0.0 * mu);
+    T eps_c = dmax(eps, cst<T>(c.eps_min));
     T ahat = (c.gam - 1.0) * eps_c / (1.0 + eps_c);
     T h = (1.0 + eps_c) * (1.0 + ahat);
-    T nu = dmax(h / W, (1.0 + ahat) * (1.0 + qbar - mu * rbar2));
-    if (W_o) *W_o = W;
-    if (eps_o) *eps_o = eps;
-    if (x_o) *x_o = x;
-    return mu - 1.0 / (nu + mu * rbar2);
-}
-template <> __device__ __forceinline__ Dual master<Dual>(Dual mu, const C2PScal& c, Dual* W_o,
-                                                         Dual* eps_o, Dual* x_o) {
-    Dual x = 1.0 / (1.0 + mu * c.bb);
-    Dual rbar2 = c.r2 * x * x + mu * x * (1.0 + x) * c.rb2;
-    Dual qbar = c.q - 0.5 * c.bb - 0.5 * mu * mu * x * x * (c.bb * c.r2 - c.rb2);
-    Dual v2 = dmin(mu * mu * rbar2, mk(c.r2 / (1.0 + c.r2)));
-    Dual W = 1.0 / dsqrt(1.0 - v2);
-    Dual eps = W * (qbar - mu * rbar2) + v2 * W * W / (1.0 + W);
-    Dual eps_c = dmax(eps, mk(c.eps_min));
-    Dual ahat = (c.gam - 1.0) * eps_c / (1.0 + eps_c);
-    Dual h = (1.0 + eps_c) * (1.0 + ahat);
-    Dual nu = dmax(h / W, (1.0 + ahat) * (1.0 + qbar - mu * rbar2));
+    T nu = dmax(h * (om * W), (1.0 + ahat) * (1.0 + qbar - mu * rbar2));
     if (W_o) *W_o = W;
     if (eps_o) *eps_o = eps;
     if (x_o) *x_o = x;
@@ -140,6 +137,7 @@ __device__ int con2prim_point(double D, const double S_d[3], double tau, const d
     c.rb2 = SB * SB * iD * iD * iD;
     c.gam = gam;
     c.eps_min = eps_min;
+    c.v2max = c.r2 / (1.0 + c.r2);
 
     double lo = 0.0, hi = 1.0;
     int ok = 1;
@@ -286,8 +284,8 @@ __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const doubl
 }
 
 // --------------------------------------------------------------------------- k_rhs
-// indices of the 6 second-derivative pairs
-__device__ __constant__ int c_pair[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+// the 6 second-derivative pairs rr, rth, rph, thth, thph, phph use the same packing
+#define c_pair_idx(i, j) sym_idx(i, j)
 
 template <typename DT, typename R>
 __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double* __restrict__ U0,
@@ -306,6 +304,7 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
     const long long P = d.P;
     if (p >= P) return;
     const R PI = R(3.141592653589793);
+    const R third = R(1.0 / 3.0), sixth = R(1.0 / 6.0), two3 = R(2.0 / 3.0);
     R rhs[NV];
 
     // ------------------------------------------------------------ state and metric
@@ -328,15 +327,20 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
     }
     // conformal factor, physical metric, its determinant and inverse, conformal inverse:
     // FP64 in every mode; the algebra below runs in R
+    // gamma = e^{4phi} gammatilde: gamma^{-1} = e^{-4phi} gammatilde^{-1} and
+    // det gamma = e^{12 phi} det gammatilde (one cofactor inverse)
     const double e4 = exp(4.0 * phi);
     const double e4m = 1.0 / e4;
     const R e4r = (R)e4, e4mr = (R)e4m;
     double g64[3][3], gi64[3][3], gti64[3][3];
+    const double detgt = inv3sym(gt64, gti64);
     for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++) g64[i][j] = e4 * gt64[i][j];
-    double detg = inv3sym(g64, gi64);
+        for (int j = 0; j < 3; j++) {
+            g64[i][j] = e4 * gt64[i][j];
+            gi64[i][j] = e4m * gti64[i][j];
+        }
+    const double detg = e4 * e4 * e4 * detgt;
     const R sqg = (R)sqrt(detg);
-    inv3sym(gt64, gti64);
     R g[3][3], gi[3][3], gti[3][3];
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) {
@@ -378,34 +382,51 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
         R T0_d[3];
         for (int i = 0; i < 3; i++)
             T0_d[i] = beta_d[i] * T00 + g[i][0] * T0i[0] + g[i][1] * T0i[1] + g[i][2] * T0i[2];
+        const R K3 = K * third;
         R Kij[3][3];
         for (int i = 0; i < 3; i++)
-            for (int j = 0; j < 3; j++) Kij[i][j] = e4r * (At[i][j] + gt[i][j] * K / R(3.0));
+            for (int j = i; j < 3; j++) Kij[i][j] = Kij[j][i] = e4r * (At[i][j] + gt[i][j] * K3);
         R asg = alpha * sqg;
+        // symmetric weights w_kl (1 on the diagonal, 2 off it) folded into the contracted
+        // tensors: bbw = w beta^k beta^l, tbw = w (T^{0k} beta^l)_(kl), Tw = w T^{kl}
+        R bbw[6], tbw[6], Tw[6], gtw[3] = {R(0.0), R(0.0), R(0.0)};
+        for (int k = 0; k < 3; k++)
+            for (int l = k; l < 3; l++) {
+                const int q = SI(k, l);
+                const R w = k == l ? R(1.0) : R(2.0);
+                bbw[q] = w * beta[k] * beta[l];
+                tbw[q] = R(0.5) * w * (T0i[k] * beta[l] + T0i[l] * beta[k]);
+                Tw[q] = w * Tij[k][l];
+                gtw[0] += bbw[q] * gt[k][l];
+                gtw[1] += tbw[q] * gt[k][l];
+                gtw[2] += Tw[q] * gt[k][l];
+            }
         for (int jd = 0; jd < 3; jd++) {
             // d_j gamma_kl = e^{4phi} (d_j gammatilde_kl + 4 gammatilde_kl d_j phi)
-            R dg[3][3];
+            R sb = R(0.0), st = R(0.0), sT = R(0.0);
             for (int k = 0; k < 3; k++)
-                for (int l = 0; l < 3; l++) dg[k][l] = e4r * (dgt[jd][k][l] + R(4.0) * gt[k][l] * dphi[jd]);
-            R bbdg = R(0.0), t0dg = R(0.0), tdg = R(0.0);
-            for (int k = 0; k < 3; k++)
-                for (int l = 0; l < 3; l++) {
-                    bbdg += beta[k] * beta[l] * dg[k][l];
-                    t0dg += T0i[k] * beta[l] * dg[k][l];
-                    tdg += Tij[k][l] * dg[k][l];
+                for (int l = k; l < 3; l++) {
+                    const int q = SI(k, l);
+                    sb += bbw[q] * dgt[jd][k][l];
+                    st += tbw[q] * dgt[jd][k][l];
+                    sT += Tw[q] * dgt[jd][k][l];
                 }
+            const R f4 = R(4.0) * dphi[jd];
+            const R bbdg = e4r * (sb + f4 * gtw[0]);
+            const R t0dg = e4r * (st + f4 * gtw[1]);
+            const R tdg = e4r * (sT + f4 * gtw[2]);
             R t0db = T0_d[0] * dbe[jd][0] + T0_d[1] * dbe[jd][1] + T0_d[2] * dbe[jd][2];
             R SS = T00 * (R(0.5) * bbdg - alpha * dal[jd]) + t0dg + t0db + R(0.5) * tdg;
             rhs[V_S + jd] = -(R)divF[(1 + jd) * P + p] + asg * SS;
         }
         R bbK = R(0.0), TK = R(0.0), t0 = R(0.0);
-        for (int i = 0; i < 3; i++) {
-            R bK = R(0.0);
-            for (int j = 0; j < 3; j++) {
-                bbK += beta[i] * beta[j] * Kij[i][j];
-                TK += Tij[i][j] * Kij[i][j];
-                bK += beta[j] * Kij[i][j];
+        for (int k = 0; k < 3; k++)
+            for (int l = k; l < 3; l++) {
+                bbK += bbw[SI(k, l)] * Kij[k][l];
+                TK += Tw[SI(k, l)] * Kij[k][l];
             }
+        for (int i = 0; i < 3; i++) {
+            const R bK = beta[0] * Kij[i][0] + beta[1] * Kij[i][1] + beta[2] * Kij[i][2];
             t0 += T0i[i] * (R(2.0) * bK - dal[i]);
         }
         R bda = beta[0] * dal[0] + beta[1] * dal[1] + beta[2] * dal[2];
@@ -452,13 +473,12 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
             R gT0[3];
             for (int i = 0; i < 3; i++) gT0[i] = g[i][0] * T0i[0] + g[i][1] * T0i[1] + g[i][2] * T0i[2];
             for (int i = 0; i < 3; i++)
-                for (int j = 0; j < 3; j++) {
+                for (int j = i; j < 3; j++) {
                     R s = beta_d[i] * beta_d[j] * T00 + beta_d[i] * gT0[j] + beta_d[j] * gT0[i] +
                                gT[i][0] * g[0][j] + gT[i][1] * g[1][j] + gT[i][2] * g[2][j];
-                    Sij[i][j] = s;
+                    Sij[i][j] = Sij[j][i] = s;
+                    Str += (i == j ? R(1.0) : R(2.0)) * gi[i][j] * s;
                 }
-            for (int i = 0; i < 3; i++)
-                for (int j = 0; j < 3; j++) Str += gi[i][j] * Sij[i][j];
 
             // -------------------------------------------------------- BSSN
 #define D2(f, q) ((R)d2[((long long)(f) * 6 + (q)) * P + p])
@@ -474,26 +494,39 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
                     for (int j = i; j < 3; j++)
                         Cu[k][i][j] = Cu[k][j][i] =
                             gti[k][0] * Cl[0][i][j] + gti[k][1] * Cl[1][i][j] + gti[k][2] * Cl[2][i][j];
+            // gammatilde^{jk} with the symmetric weights (contractions with symmetric tensors)
+            R gw[6];
+            for (int j = 0; j < 3; j++)
+                for (int k = j; k < 3; k++) gw[SI(j, k)] = (j == k ? R(1.0) : R(2.0)) * gti[j][k];
             R Gd[3];
             for (int i = 0; i < 3; i++) {
                 R s = R(0.0);
                 for (int j = 0; j < 3; j++)
-                    for (int k = 0; k < 3; k++) s += gti[j][k] * Cu[i][j][k];
+                    for (int k = j; k < 3; k++) s += gw[SI(j, k)] * Cu[i][j][k];
                 Gd[i] = s;
             }
             R divb = dbe[0][0] + dbe[1][1] + dbe[2][2];
-            // A[k][i][m] = gti^{lm} Cu[k][l][i];  Bt[k][j][m] = gti^{lm} Cl[k][l][j]
-            R Ar[3][3][3], Bt[3][3][3];
+            // Bt[k][j][m] = gti^{lm} Gamma_{k l j}.  The quadratic Christoffel part of the
+            // Ricci tensor, gti^{lm} (Gamma^k_{li} Gamma_{jkm} + Gamma^k_{lj} Gamma_{ikm} +
+            // Gamma^k_{im} Gamma_{klj}), is Pq_ij + Pq_ji + Qq_ij with
+            // Pq_ij = Gamma^k_{li} Bt[j][k][l] and the symmetric Qq_ij = Gamma^k_{im} Bt[k][j][m].
+            R Bt[3][3][3];
             for (int k = 0; k < 3; k++)
                 for (int i = 0; i < 3; i++)
-                    for (int m = 0; m < 3; m++) {
-                        Ar[k][i][m] = gti[0][m] * Cu[k][0][i] + gti[1][m] * Cu[k][1][i] + gti[2][m] * Cu[k][2][i];
+                    for (int m = 0; m < 3; m++)
                         Bt[k][i][m] = gti[0][m] * Cl[k][0][i] + gti[1][m] * Cl[k][1][i] + gti[2][m] * Cl[k][2][i];
-                    }
+            R Pq[3][3];
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) {
+                    R t = R(0.0);
+                    for (int k = 0; k < 3; k++)
+                        for (int l = 0; l < 3; l++) t += Cu[k][l][i] * Bt[j][k][l];
+                    Pq[i][j] = t;
+                }
             R ddphi[3][3], ddal[3][3];
             for (int i = 0; i < 3; i++)
                 for (int j = i; j < 3; j++) {
-                    int q = c_pair[i][j];
+                    int q = c_pair_idx(i, j);
                     ddphi[i][j] = ddphi[j][i] = D2(6, q);
                     ddal[i][j] = ddal[j][i] = D2(7, q);
                 }
@@ -515,9 +548,9 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
                 }
             R lapphi = R(0.0), trDDal = R(0.0);
             for (int i = 0; i < 3; i++)
-                for (int j = 0; j < 3; j++) {
-                    lapphi += gti[i][j] * DDphi[i][j];
-                    trDDal += gti[i][j] * DDal[i][j];
+                for (int j = i; j < 3; j++) {
+                    lapphi += gw[SI(i, j)] * DDphi[i][j];
+                    trDDal += gw[SI(i, j)] * DDal[i][j];
                 }
             trDDal *= e4mr;
             // Atilde with raised indices
@@ -525,12 +558,12 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
             for (int k = 0; k < 3; k++)
                 for (int j = 0; j < 3; j++)
                     Aud[k][j] = gti[k][0] * At[0][j] + gti[k][1] * At[1][j] + gti[k][2] * At[2][j];
-            for (int i = 0; i < 3; i++)
-                for (int j = 0; j < 3; j++)
-                    Auu[i][j] = Aud[i][0] * gti[0][j] + Aud[i][1] * gti[1][j] + Aud[i][2] * gti[2][j];
             R AA = R(0.0);
             for (int i = 0; i < 3; i++)
-                for (int j = 0; j < 3; j++) AA += At[i][j] * Auu[i][j];
+                for (int j = i; j < 3; j++) {
+                    Auu[i][j] = Auu[j][i] = Aud[i][0] * gti[0][j] + Aud[i][1] * gti[1][j] + Aud[i][2] * gti[2][j];
+                    AA += (i == j ? R(1.0) : R(2.0)) * At[i][j] * Auu[i][j];
+                }
 
             // X_ij = -D_i D_j alpha + alpha (R_ij - 8 pi S_ij)
             R X[3][3];
@@ -539,19 +572,14 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
                     int sij = SI(i, j);
                     R lapg = R(0.0);
                     for (int l = 0; l < 3; l++)
-                        for (int m = l; m < 3; m++) {
-                            R w = (l == m) ? gti[l][m] : R(2.0) * gti[l][m];
-                            lapg += w * D2(sij, c_pair[l][m]);
-                        }
+                        for (int m = l; m < 3; m++) lapg += gw[SI(l, m)] * D2(sij, c_pair_idx(l, m));
                     R Ric = -R(0.5) * lapg;
                     for (int k = 0; k < 3; k++)
                         Ric += R(0.5) * (gt[k][i] * dGam[j][k] + gt[k][j] * dGam[i][k]) +
                                R(0.5) * Gd[k] * (Cl[i][j][k] + Cl[j][i][k]);
-                    R t = R(0.0);
+                    R t = Pq[i][j] + Pq[j][i];
                     for (int k = 0; k < 3; k++)
-                        for (int m = 0; m < 3; m++)
-                            t += Ar[k][i][m] * Cl[j][k][m] + Ar[k][j][m] * Cl[i][k][m] +
-                                 Cu[k][i][m] * Bt[k][j][m];
+                        for (int m = 0; m < 3; m++) t += Cu[k][i][m] * Bt[k][j][m];
                     Ric += t;
                     Ric += -R(2.0) * DDphi[i][j] - R(2.0) * gt[i][j] * lapphi + R(4.0) * dphi[i] * dphi[j] -
                            R(4.0) * gt[i][j] * gdphi2;
@@ -559,7 +587,8 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
                 }
             R trX = R(0.0);
             for (int i = 0; i < 3; i++)
-                for (int j = 0; j < 3; j++) trX += gti[i][j] * X[i][j];
+                for (int j = i; j < 3; j++) trX += gw[SI(i, j)] * X[i][j];
+            const R trX3 = trX * third;
             for (int i = 0; i < 3; i++)
                 for (int j = i; j < 3; j++) {
                     int sij = SI(i, j);
@@ -571,39 +600,39 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
                         la += At[i][k] * dbe[j][k] + At[j][k] * dbe[i][k];
                         AAd += At[i][k] * Aud[k][j];
                     }
-                    rhs[V_GT + sij] = -R(2.0) * alpha * At[i][j] + adv_g + lg - (R(2.0) / R(3.0)) * gt[i][j] * divb;
-                    R XTF = X[i][j] - gt[i][j] * trX / R(3.0);
+                    rhs[V_GT + sij] = -R(2.0) * alpha * At[i][j] + adv_g + lg - two3 * gt[i][j] * divb;
+                    R XTF = X[i][j] - gt[i][j] * trX3;
                     rhs[V_AT + sij] = e4mr * XTF + alpha * (K * At[i][j] - R(2.0) * AAd) + adv_a + la -
-                                      (R(2.0) / R(3.0)) * At[i][j] * divb;
+                                      two3 * At[i][j] * divb;
                 }
-            rhs[V_PHI] = -alpha * K / R(6.0) + (beta[0] * dphi[0] + beta[1] * dphi[1] + beta[2] * dphi[2]) +
-                         divb / R(6.0);
-            rhs[V_K] = -trDDal + alpha * (AA + K * K / R(3.0)) + R(4.0) * PI * alpha * (rho_m + Str) +
+            rhs[V_PHI] = -alpha * K * sixth + (beta[0] * dphi[0] + beta[1] * dphi[1] + beta[2] * dphi[2]) +
+                         divb * sixth;
+            rhs[V_K] = -trDDal + alpha * (AA + K * K3) + R(4.0) * PI * alpha * (rho_m + Str) +
                        (beta[0] * dK[0] + beta[1] * dK[1] + beta[2] * dK[2]);
             // Gammatilde
             R ddb[3][3][3];  // [q pair via j,k][i]
             for (int j = 0; j < 3; j++)
                 for (int k = j; k < 3; k++)
                     for (int i = 0; i < 3; i++)
-                        ddb[j][k][i] = ddb[k][j][i] = D2(7 + 1 + i, c_pair[j][k]);
+                        ddb[j][k][i] = ddb[k][j][i] = D2(7 + 1 + i, c_pair_idx(j, k));
             R ddbk[3];  // d_j d_k beta^k
             for (int j = 0; j < 3; j++) ddbk[j] = ddb[j][0][0] + ddb[j][1][1] + ddb[j][2][2];
             for (int i = 0; i < 3; i++) {
                 R s = R(0.0);
                 for (int j = 0; j < 3; j++)
-                    for (int k = 0; k < 3; k++) s += gti[j][k] * ddb[j][k][i];
+                    for (int k = j; k < 3; k++) s += gw[SI(j, k)] * ddb[j][k][i];
                 R s2 = gti[i][0] * ddbk[0] + gti[i][1] * ddbk[1] + gti[i][2] * ddbk[2];
                 R adv = beta[0] * dGam[0][i] + beta[1] * dGam[1][i] + beta[2] * dGam[2][i];
                 R gdb = Gam[0] * dbe[0][i] + Gam[1] * dbe[1][i] + Gam[2] * dbe[2][i];
                 R Ada = Auu[i][0] * dal[0] + Auu[i][1] * dal[1] + Auu[i][2] * dal[2];
                 R CA = R(0.0);
                 for (int j = 0; j < 3; j++)
-                    for (int k = 0; k < 3; k++) CA += Cu[i][j][k] * Auu[j][k];
+                    for (int k = j; k < 3; k++) CA += (j == k ? R(1.0) : R(2.0)) * Cu[i][j][k] * Auu[j][k];
                 R Adp = Auu[i][0] * dphi[0] + Auu[i][1] * dphi[1] + Auu[i][2] * dphi[2];
                 R gdK = gti[i][0] * dK[0] + gti[i][1] * dK[1] + gti[i][2] * dK[2];
                 R gS = gti[i][0] * S_i[0] + gti[i][1] * S_i[1] + gti[i][2] * S_i[2];
-                rhs[V_GAM + i] = s + s2 / R(3.0) + adv - gdb + (R(2.0) / R(3.0)) * Gam[i] * divb - R(2.0) * Ada +
-                                 R(2.0) * alpha * (CA + R(6.0) * Adp - (R(2.0) / R(3.0)) * gdK) -
+                rhs[V_GAM + i] = s + s2 * third + adv - gdb + two3 * Gam[i] * divb - R(2.0) * Ada +
+                                 R(2.0) * alpha * (CA + R(6.0) * Adp - two3 * gdK) -
                                  R(16.0) * PI * alpha * gS;
             }
 #undef D2
