@@ -8,6 +8,7 @@ oracle's own coefficient route and the library's barycentric matrices differ by 
 1e-15 b_i).  Lines of very different magnitude (1e-100 .. 1e100) check that every line
 is scaled by its own exponent; a NaN must spread over its line only; zero stays zero.
 """
+import json
 import os
 
 import numpy as np
@@ -71,6 +72,18 @@ def _run(pkg, ctx, u, d):
     return dst.cpu().numpy().reshape(u.shape)
 
 
+def _report(name, value):
+    """measured errors go to gpurun_out/fx_accuracy.json when that folder exists"""
+    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if not os.path.isdir(out):
+        return
+    fn = os.path.join(out, "fx_accuracy.json")
+    data = json.load(open(fn)) if os.path.exists(fn) else {}
+    data[name] = value
+    with open(fn, "w") as fh:
+        json.dump(data, fh, indent=1)
+
+
 @pytest.mark.parametrize("contraction", [0, 1])
 def test_contraction_accuracy(pkg, contraction):
     cfg = config("c1", n_elem=3, n_r=10, n_theta=9, n_phi=8)
@@ -78,6 +91,7 @@ def test_contraction_accuracy(pkg, contraction):
     absD = _abs_ops(g)
     rng = np.random.default_rng(11)
     ops = (g.d_r, g.d_t, g.d_p)
+    worst = []
     for d in range(3):
         # values spanning 12 decades inside every line, line magnitudes 1e-100 .. 1e100
         u = rng.normal(size=g.shape) * 10.0 ** rng.uniform(-6, 6, size=g.shape)
@@ -89,7 +103,9 @@ def test_contraction_accuracy(pkg, contraction):
         b = _bound(g, absD, u, d)
         err = np.abs(got - ref) / b
         assert np.all(np.isfinite(got))
+        worst.append(float(err.max()))
         assert err.max() <= 2e-14, (d, float(err.max()))
+    _report(f"accuracy_contraction{contraction}", worst)
     ctx.close()
 
 
@@ -116,6 +132,7 @@ def test_contraction_nan_and_zero(pkg, contraction):
 def test_contraction_sizes(pkg):
     """Every size class of the tensor-core kernel (K chunks of 16 and 32, Np 16..64) on
     smooth data."""
+    worst = {}
     for nr, nt, nph in ((4, 5, 4), (16, 17, 16), (24, 33, 34), (40, 48, 64), (64, 20, 48)):
         cfg = config("c1", n_elem=2, n_r=nr, n_theta=nt, n_phi=nph)
         g, ctx = _setup(pkg, cfg, 0)
@@ -125,5 +142,7 @@ def test_contraction_sizes(pkg):
         for d in range(3):
             got = _run(pkg, ctx, u, d)
             err = np.abs(got - ops[d](u)) / _bound(g, absD, u, d)
+            worst[f"{(nr, nt, nph)[d]} nodes dir {d}"] = float(err.max())
             assert err.max() <= 2e-14, ((nr, nt, nph), d, float(err.max()))
         ctx.close()
+    _report("sizes_contraction0", worst)
