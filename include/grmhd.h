@@ -87,7 +87,11 @@ typedef struct {
  * spectral contractions (all derivatives at precision 0, the filter at every precision)
  * run: 0 (default) on the BF16 tensor cores with exact base-256 digit slices of the
  * FP64 values (Ozaki splitting; error about 2^-53 of sum_j |D_ij| max_j |u_j|, directions
- * with more than 64 nodes fall back to 1), 1 on the FP64 units. */
+ * with more than 64 nodes fall back to 1), 1 on the FP64 units.  coupling: 0 (default) one
+ * unsplit right-hand side over all 32 variables per Runge-Kutta stage; 1 the paper's
+ * coupled loop ("Coupled Main Loop"): per step the fluid is advanced by the selected
+ * Runge-Kutta scheme on the frozen metric, then BSSN + gauge take one forward-Euler step
+ * with the fluid frozen (matter sources from the updated fluid), then the filter. */
 typedef struct {
     int precision;
     int integrator;
@@ -100,6 +104,7 @@ typedef struct {
     int c2p_maxit;
     double c2p_tol;
     int contraction;
+    int coupling;
 } grmhd_opts;
 
 typedef struct grmhd_ctx grmhd_ctx;

@@ -22,6 +22,13 @@ Chebyshev-Fourier grids" without stating the coupling):
   1/(w_end J) with the Clenshaw-Curtis end weight;
 * outer radial node: RHS = 0 (frozen); inner node (inside the horizon): no condition;
 * time integrator: SSP-RK3 (Shu-Osher) by default, the paper's RK4 as an option;
+* coupling: the unsplit method of lines by default; as an option the paper's coupled
+  loop ("Coupled Main Loop", "Main Coupled Evolution Loop"): per step the fluid is
+  advanced by the Runge-Kutta scheme on the frozen metric, then BSSN and gauge take one
+  forward-Euler step with the fluid frozen, the matter sources computed from the
+  updated fluid (first-order Lie splitting; the paper's "half-step" is read as the
+  fluid half of the split step, both halves advancing by dt, since a fluid advanced by
+  dt/2 per step would fall behind the metric);
 * post-step filter: exponential (alpha = 36, p = 8) on the Chebyshev modes in r
   (per element) and theta and on the Fourier modes in phi, plus the 2/3 rule in
   phi; then the BSSN variables of duplicated interface nodes are averaged.
@@ -76,6 +83,8 @@ class Params:
     dealias23_phi: int = 1
     cfl: float = 0.3
     eps_atm: float = 1e-10       # floor of the specific internal energy
+    coupling: int = 0            # 0 unsplit method of lines, 1 the paper's split loop
+    evolve_fluid: int = 1        # 0: Valencia right-hand side zero (BSSN half of a split step)
 
     @classmethod
     def from_config(cls, cfg, **kw):
@@ -305,6 +314,8 @@ def rhs_from_prims(U, prim, g: Grid, p: Params, freeze_outer=True):
             rhs[I_BG + i] = r["B"][..., i]
         rhs[I_ALPHA] = r["alpha"]
 
+    if not p.evolve_fluid:
+        rhs[I_D:I_D + 8] = 0.0
     # frozen outer boundary
     if freeze_outer:
         rhs[:, E - 1, -1] = 0.0
@@ -344,7 +355,17 @@ def apply_filter(U, g: Grid, p: Params):
 
 # ---------------------------------------------------------------------- time step
 def rk_step(U, dt, g: Grid, p: Params):
-    """One time step: SSP-RK3 in Shu-Osher form (or classical RK4), then the filter."""
+    """One time step: SSP-RK3 in Shu-Osher form (or classical RK4), then the filter.
+    With coupling = 1 the paper's split loop: the fluid step on the frozen metric, then
+    one forward-Euler step of BSSN + gauge with the fluid frozen, then the filter."""
+    if p.coupling == 1:
+        pf = dataclasses.replace(p, coupling=0, evolve_metric=0, filter_mask=0)
+        Uf = rk_step(U, dt, g, pf)
+        U3 = Uf
+        if p.evolve_metric:
+            pb = dataclasses.replace(p, coupling=0, evolve_fluid=0)
+            U3 = Uf + dt * rhs(Uf, g, pb)
+        return apply_filter(U3, g, p) if p.filter_mask else U3
     if p.integrator == 0:
         U1 = U + dt * rhs(U, g, p)
         U2 = 0.75 * U + 0.25 * (U1 + dt * rhs(U1, g, p))

@@ -34,7 +34,7 @@ class Opts(C.Structure):
                 ("gauge", C.c_int), ("eta", C.c_double), ("cfl", C.c_double),
                 ("filter", C.c_int), ("filt_alpha", C.c_double), ("filt_p", C.c_double),
                 ("dealias23_phi", C.c_int), ("c2p_maxit", C.c_int), ("c2p_tol", C.c_double),
-                ("contraction", C.c_int)]
+                ("contraction", C.c_int), ("coupling", C.c_int)]
 
 
 _P = C.c_void_p

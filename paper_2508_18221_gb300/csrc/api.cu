@@ -134,6 +134,7 @@ extern "C" int grmhd_defaults(grmhd_grid* g, grmhd_physics* ph, grmhd_opts* o) {
         o->eta = 2.0; o->cfl = 0.3; o->filter = 47; o->filt_alpha = 36.0; o->filt_p = 8.0;
         o->dealias23_phi = 1; o->c2p_maxit = 60; o->c2p_tol = 1e-15;
         o->contraction = 0;
+        o->coupling = 0;
     }
     return GRMHD_OK;
 }
@@ -162,6 +163,7 @@ static int validate(const grmhd_grid* g, const grmhd_physics* ph, const grmhd_op
     if (!(o->cfl > 0.0) || o->c2p_maxit < 1 || !(o->c2p_tol > 0.0)) { strcpy(msg, "bad cfl / c2p options"); return GRMHD_EINVAL; }
     if (o->filter < 0 || o->filter > 63) { strcpy(msg, "filter mask must be in [0, 63]"); return GRMHD_EINVAL; }
     if (o->contraction != 0 && o->contraction != 1) { strcpy(msg, "contraction must be 0 or 1"); return GRMHD_EINVAL; }
+    if (o->coupling != 0 && o->coupling != 1) { strcpy(msg, "coupling must be 0 or 1"); return GRMHD_EINVAL; }
     return GRMHD_OK;
 }
 
@@ -261,6 +263,7 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
     c->pp.M = phys->M; c->pp.a = phys->a; c->pp.gam = phys->gamma_eos;
     c->pp.rho_atm = phys->rho_atm; c->pp.eps_atm = phys->eps_atm;
     c->pp.eta = opts->eta; c->pp.gauge = opts->gauge; c->pp.evolve_metric = opts->evolve_metric;
+    c->pp.evolve_fluid = 1;
     c->pp.c2p_maxit = opts->c2p_maxit; c->pp.c2p_tol = opts->c2p_tol;
     std::vector<double> wcgl = quad_weights(Nr, true);
     c->pp.w_end = wcgl[0];
@@ -600,17 +603,18 @@ static int enqueue_second_derivs(grmhd_ctx* c) {
     return GRMHD_OK;
 }
 
-// one RHS evaluation on state buffer b (Us); output per RKCoef
-static int enqueue_stage(grmhd_ctx* c, int b, RKCoef co, double* out) {
-    CK(launch_prep(c->d, c->pp, c->U[b], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream));
+// one RHS evaluation on state buffer b (Us); output per RKCoef; pp selects the halves of
+// a split step (evolve_metric / evolve_fluid)
+static int enqueue_stage(grmhd_ctx* c, int b, RKCoef co, double* out, const PhysParams& pp) {
+    CK(launch_prep(c->d, pp, c->U[b], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream));
     c->launches_tmp++;
     int st = enqueue_first_derivs(c, b);
     if (st) return st;
-    if (c->opts.evolve_metric) {
+    if (pp.evolve_metric) {
         st = enqueue_second_derivs(c);
         if (st) return st;
     }
-    CK(launch_rhs(c->d, c->pp, c->U[0], c->U[b], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
+    CK(launch_rhs(c->d, pp, c->U[0], c->U[b], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
                   c->divF, c->opts.precision > 0, c->r_scale, c->dt, co, out, c->acc, c->stream));
     c->launches_tmp++;
     return GRMHD_OK;
@@ -642,20 +646,32 @@ static int enqueue_filter(grmhd_ctx* c, int b) {
 static int enqueue_step(grmhd_ctx* c) {
     int st;
     int last;
+    // split coupling: the Runge-Kutta stages advance the fluid on the frozen metric
+    PhysParams pp = c->pp;
+    if (c->opts.coupling == 1) pp.evolve_metric = 0;
     if (c->opts.integrator == 0) {
         RKCoef s1 = {0.0, 1.0, 0.0, 0.0, 0}, s2 = {0.75, 0.25, 0.0, 0.0, 0}, s3 = {1.0 / 3.0, 2.0 / 3.0, 0.0, 0.0, 0};
-        if ((st = enqueue_stage(c, 0, s1, c->U[1]))) return st;
-        if ((st = enqueue_stage(c, 1, s2, c->U[2]))) return st;
-        if ((st = enqueue_stage(c, 2, s3, c->U[1]))) return st;
+        if ((st = enqueue_stage(c, 0, s1, c->U[1], pp))) return st;
+        if ((st = enqueue_stage(c, 1, s2, c->U[2], pp))) return st;
+        if ((st = enqueue_stage(c, 2, s3, c->U[1], pp))) return st;
         last = 1;
     } else {
         RKCoef k1 = {0, 0, 0.5, 1.0 / 6.0, 1}, k2 = {0, 0, 0.5, 1.0 / 3.0, 2}, k3 = {0, 0, 1.0, 1.0 / 3.0, 2},
                k4 = {0, 0, 0.0, 1.0 / 6.0, 3};
-        if ((st = enqueue_stage(c, 0, k1, c->U[1]))) return st;
-        if ((st = enqueue_stage(c, 1, k2, c->U[2]))) return st;
-        if ((st = enqueue_stage(c, 2, k3, c->U[1]))) return st;
-        if ((st = enqueue_stage(c, 1, k4, c->U[2]))) return st;
+        if ((st = enqueue_stage(c, 0, k1, c->U[1], pp))) return st;
+        if ((st = enqueue_stage(c, 1, k2, c->U[2], pp))) return st;
+        if ((st = enqueue_stage(c, 2, k3, c->U[1], pp))) return st;
+        if ((st = enqueue_stage(c, 1, k4, c->U[2], pp))) return st;
         last = 2;
+    }
+    if (c->opts.coupling == 1 && c->pp.evolve_metric) {
+        // then one forward-Euler step of BSSN + gauge with the fluid frozen
+        PhysParams pb = c->pp;
+        pb.evolve_fluid = 0;
+        const RKCoef eu = {0.0, 1.0, 0.0, 0.0, 0};
+        const int nb = last == 1 ? 2 : 1;
+        if ((st = enqueue_stage(c, last, eu, c->U[nb], pb))) return st;
+        last = nb;
     }
     if (c->opts.filter) return enqueue_filter(c, last);
     CK(cudaMemcpyAsync(c->U[0], c->U[last], sizeof(double) * NV * c->d.P, cudaMemcpyDeviceToDevice, c->stream));
@@ -779,7 +795,7 @@ extern "C" int grmhd_rhs(grmhd_ctx* c, double* out, int on_device) {
     CK(cudaMemsetAsync(c->nfail, 0, sizeof(unsigned long long), c->stream));
     RKCoef co = {0, 0, 0, 0, -1};
     double* dst = on_device ? out : c->scratch;
-    int st = enqueue_stage(c, 0, co, dst);
+    int st = enqueue_stage(c, 0, co, dst, c->pp);
     if (st) return st;
     c->launches_per_call = c->launches_tmp;
     if (!on_device) return copy_out(c, out, c->scratch, (size_t)NV * c->d.P, 0);
@@ -936,7 +952,7 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
     int st = GRMHD_OK;
     for (int k = 0; k < GRMHD_NKT && st == GRMHD_OK; k++) {
         // bring the buffers the kernel reads up to date (untimed)
-        if (k >= 1) { c->launches_tmp = 0; st = enqueue_stage(c, 1, co, c->scratch); if (st) break; }
+        if (k >= 1) { c->launches_tmp = 0; st = enqueue_stage(c, 1, co, c->scratch, c->pp); if (st) break; }
         CK(cudaEventRecord(e0, c->stream));
         for (int r = 0; r < reps; r++) {
             cudaError_t e = cudaSuccess;

@@ -42,6 +42,7 @@ struct PhysParams {
     double M, a, gam, rho_atm, eps_atm;
     double eta;
     int gauge, evolve_metric;
+    int evolve_fluid;     // 0: Valencia right-hand side zero (BSSN half of a split step)
     int c2p_maxit;
     double c2p_tol;
     double w_end;         // Clenshaw-Curtis end weight on [-1, 1] for n_r CGL nodes

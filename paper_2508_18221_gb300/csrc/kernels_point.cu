@@ -651,6 +651,8 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
         }
     }
 
+    if (!pp.evolve_fluid)
+        for (int v = V_D; v < NV; v++) rhs[v] = R(0);
     // frozen outer boundary node of each instance
     const int elem_id = (int)(p / d.elem);
     {

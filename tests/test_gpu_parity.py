@@ -37,13 +37,13 @@ def pkg():
 
 def _ctx(pkg, cfg, **kw):
     import torch
-    opt_keys = ("evolve_metric", "gauge", "integrator", "filter", "contraction")
+    opt_keys = ("evolve_metric", "gauge", "integrator", "filter", "contraction", "coupling")
     grid, phys, opts = pkg.make_structs(cfg, **{k: v for k, v in kw.items() if k in opt_keys})
     return pkg.Context(grid, phys, opts, torch.cuda.current_stream().cuda_stream)
 
 
 def _oracle(cfg, **kw):
-    pk = {k: v for k, v in kw.items() if k in ("evolve_metric", "gauge", "integrator")}
+    pk = {k: v for k, v in kw.items() if k in ("evolve_metric", "gauge", "integrator", "coupling")}
     if "filter" in kw:
         pk["filter_mask"] = kw["filter"]
     return so.workload_state(cfg, **pk)
@@ -180,19 +180,22 @@ def test_con2prim_parity(pkg):
     ctx.close()
 
 
-@pytest.mark.parametrize("integrator,contraction", [(0, 0), (1, 0), (0, 1)])
-def test_step_parity(pkg, integrator, contraction):
+@pytest.mark.parametrize("integrator,contraction,coupling", [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 0, 1), (0, 0, 1)])
+def test_step_parity(pkg, integrator, contraction, coupling):
+    """2 steps; coupling = 1 is the paper's split loop (fluid RK on the frozen metric,
+    then a forward-Euler BSSN + gauge step)."""
     import torch
     cfg = config("c1", n_elem=3, n_r=9, n_theta=10, n_phi=8)
-    g, p, U = _oracle(cfg, integrator=integrator)
-    ctx = _ctx(pkg, cfg, integrator=integrator, contraction=contraction)
+    g, p, U = _oracle(cfg, integrator=integrator, coupling=coupling)
+    ctx = _ctx(pkg, cfg, integrator=integrator, contraction=contraction, coupling=coupling)
     ctx.set_state(torch.from_numpy(U.reshape(-1).copy()).cuda(), True)
     dt = 2e-3
     ctx.step(dt, 2)
     got = np.empty(U.size)
     ctx.get_state(got, False)
     ref = so.rk_step(so.rk_step(U, dt, g, p), dt, g, p)
-    assert_parity(got.reshape(U.shape), ref, f"2 steps integrator {integrator} contraction {contraction}", U=U)
+    assert_parity(got.reshape(U.shape), ref,
+                  f"2 steps integrator {integrator} contraction {contraction} coupling {coupling}", U=U)
     ctx.close()
 
 
