@@ -131,14 +131,15 @@ __device__ __forceinline__ double ldexp_int(long long R, int X) {
 }
 
 // T = g2 + g3 + g4 + g5 + gf as the integer R = round(T 2^40): g2 is an integer, g3 a
-// multiple of 2^-8, g4 of 2^-16, g5 of 2^-24 (all exact, |g_s 2^(8 (s-2))| <= 2^22 for
-// K <= 64), gf carries the rounded low-order terms (|gf| < 2^-8).
-__device__ __forceinline__ long long combine(float g2, float g3, float g4, float g5, float gf) {
+// multiple of 2^-8, g4 of 2^-16, g5 of 2^-24 (all exact: |g_s 2^(8 (s-2))| <= 2^22 for
+// K <= 64, < 2^24 for K <= 128), gf carries the rounded low-order terms (|gf| < 2^-8).
+__device__ __forceinline__ long long combine(float g2, float g3, float g4, float g5, float gf, bool wide) {
     const float MAG = 12582912.f;  // 1.5 * 2^23: float -> nearest integer for |x| <= 2^22
     const int n2 = __float_as_int(g2 + MAG) - 0x4B400000;
     const int n3 = __float_as_int(fmaf(g3, 256.f, MAG)) - 0x4B400000;
-    const int n4 = __float_as_int(fmaf(g4, 65536.f, MAG)) - 0x4B400000;
-    const int n5 = __float_as_int(fmaf(g5, 16777216.f, MAG)) - 0x4B400000;
+    // K > 64: g4, g5 scaled reach 2^23 (exact integers below 2^24): plain conversions
+    const int n4 = wide ? __float2int_rn(g4 * 65536.f) : __float_as_int(fmaf(g4, 65536.f, MAG)) - 0x4B400000;
+    const int n5 = wide ? __float2int_rn(g5 * 16777216.f) : __float_as_int(fmaf(g5, 16777216.f, MAG)) - 0x4B400000;
     const float fh = fmaf(gf, 16777216.f, MAG);
     const int nfh = __float_as_int(fh) - 0x4B400000;
     const float flo = fmaf(gf, 16777216.f, -(fh - MAG));  // exact remainder in [-1/2, 1/2]
@@ -211,6 +212,7 @@ struct FxParams {
     const uint8_t* img;
     long long img_estride;
     int N, Np, Kp, tmem_cols, nstg, njobs;
+    int Npp;                 // output columns per pass (Np, or 64 when Np = 128)
     long long ntiles;
     uint32_t stg_bytes;
     int* err;
@@ -350,8 +352,10 @@ __global__ void __launch_bounds__(256) k_contract_fx(Dims d, FxParams fp) {
         const int EL = max(sEL[m], sEL[128 + m]);
         const bool line_bad = EL == 0x7FF;
 
+        const int Npp = fp.Npp, npass = Np / Npp;
+        for (int ch = 0; ch < npass; ch++) {
         for (int kc = 0; kc < nchunks; kc++) {
-            // the previous MMAs (previous chunk or item) have finished reading A and B
+            // the previous MMAs (previous chunk, pass or item) have finished reading A and B
             if (n_commit > 0 && !mbar_wait(&bars[3], (n_commit - 1) & 1)) ok = false;
             if (tid == 0) {
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bars[2])),
@@ -399,7 +403,7 @@ __global__ void __launch_bounds__(256) k_contract_fx(Dims d, FxParams fp) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             // with one staging buffer the next item's tile is fetched once the last chunk of
             // this one is converted
-            if (fp.nstg == 1 && kc == nchunks - 1 && warp == 0 && nxt < nitems) {
+            if (fp.nstg == 1 && ch == npass - 1 && kc == nchunks - 1 && warp == 0 && nxt < nitems) {
                 FxTile t;
                 fx_tile<DIR>(d, nxt % fp.ntiles, N, &t);
                 fx_stage<DIR>(d, t, N, fp.jobs[nxt / fp.ntiles].src, reinterpret_cast<double*>(sm), &bars[0],
@@ -407,8 +411,10 @@ __global__ void __launch_bounds__(256) k_contract_fx(Dims d, FxParams fp) {
             }
             if (tid == 0) {
                 if (mbar_wait(&bars[2], n_bload & 1)) {
-                    const uint32_t id = instr_desc_bf16(128, Np);
+                    const uint32_t id = instr_desc_bf16(128, Npp);
                     const uint32_t lbo = 128u, sbo = (uint32_t)kcores * 128u;
+                    // this pass's operator rows ch Npp .. : whole 8-row core-matrix groups
+                    const uint32_t brow = (uint32_t)(ch * Npp / 8) * sbo;
                     // digit pairs (q, l), 0-based, s = q + l <= 6 into accumulator min(s, 4);
                     // within the folded accumulator the smallest terms first
                     for (int sd = NDIG - 1; sd >= 0; sd--) {
@@ -417,8 +423,8 @@ __global__ void __launch_bounds__(256) k_contract_fx(Dims d, FxParams fp) {
                             const int l = sd - q;
                             const bool first = kc == 0 && q == 0 && (sd < NACC - 1 || sd == NDIG - 1);
                             const uint64_t da = smem_desc(smem_u32(sA + q * a_bytes), lbo, sbo);
-                            const uint64_t db = smem_desc(smem_u32(sB + l * b_bytes), lbo, sbo);
-                            mma_bf16(tmem + (uint32_t)(g * Np), da, db, id, first ? 0u : 1u);
+                            const uint64_t db = smem_desc(smem_u32(sB + l * b_bytes) + brow, lbo, sbo);
+                            mma_bf16(tmem + (uint32_t)(g * Npp), da, db, id, first ? 0u : 1u);
                         }
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -437,13 +443,14 @@ __global__ void __launch_bounds__(256) k_contract_fx(Dims d, FxParams fp) {
         if (!mbar_wait(&bars[3], (n_commit - 1) & 1)) ok = false;
         asm volatile("tcgen05.fence::after_thread_sync;");
 
-        // epilogue: TMEM lane m (this thread's line), this half's output columns, 8 at a time
-        const int c0 = half * (Np / 2), c1 = c0 + Np / 2;
+        // epilogue: TMEM lane m (this thread's line), this half's output columns of the
+        // pass, 8 at a time
+        const int c0 = ch * Npp + half * (Npp / 2), c1 = c0 + Npp / 2;
         for (int cb = c0; cb < c1; cb += 8) {
             uint32_t r[NACC][8];
 #pragma unroll
             for (int g = 0; g < NACC; g++) {
-                const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * Np + cb);
+                const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * Npp + cb - ch * Npp);
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                              : "=r"(r[g][0]), "=r"(r[g][1]), "=r"(r[g][2]), "=r"(r[g][3]), "=r"(r[g][4]),
                                "=r"(r[g][5]), "=r"(r[g][6]), "=r"(r[g][7])
@@ -456,7 +463,7 @@ __global__ void __launch_bounds__(256) k_contract_fx(Dims d, FxParams fp) {
                 for (int j = 0; j < 8; j++) {
                     const long long R = combine(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]),
                                                 __uint_as_float(r[2][j]), __uint_as_float(r[3][j]),
-                                                __uint_as_float(r[4][j]));
+                                                __uint_as_float(r[4][j]), fp.Kp > 64);
                     v[j] = scale_int(R, EL + sF[cb + j] - 2096);
                 }
                 if (line_bad)
@@ -474,10 +481,11 @@ __global__ void __launch_bounds__(256) k_contract_fx(Dims d, FxParams fp) {
                 }
             }
         }
-        // TMEM, sF and sEL are free for the next item
+        // TMEM (and, after the last pass, sF and sEL) free for the next pass or item
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
+        }
     }
     if (!ok && lane == 0) atomicExch(fp.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -485,13 +493,14 @@ __global__ void __launch_bounds__(256) k_contract_fx(Dims d, FxParams fp) {
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(fp.tmem_cols));
 }
 
+// K padded to 16; output rows padded to K (<= 64) or to 128 (two passes of 64 columns)
 void fx_geometry(int N, int* Np, int* Kp, int* KC) {
     *Kp = (N + 15) / 16 * 16;
-    *Np = *Kp;
+    *Np = *Kp <= 64 ? *Kp : 128;
     *KC = 16;
 }
 
-bool fx_supported(int dir, int N) { return N >= 2 && N <= 64 && (dir != 2 || (N % 2) == 0); }
+bool fx_supported(int dir, int N) { return N >= 2 && N <= 128 && (dir != 2 || (N % 2) == 0); }
 
 static uint32_t fx_stg_bytes(int dir, int N) {
     if (dir == 2) return 128u * (uint32_t)((N / 2) | 1) * 16u;
@@ -515,7 +524,8 @@ static FxCfg fx_cfg(int dir, int N) {
     int Np, Kp, KC;
     fx_geometry(N, &Np, &Kp, &KC);
     FxCfg c;
-    const int need = NACC * Np;
+    const int Npp = Np > 64 ? 64 : Np;
+    const int need = NACC * Npp;
     c.cols = need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : (need <= 256 ? 256 : 512)));
     c.ctas = c.cols <= 256 ? 2 : 1;
     const size_t share = 233472 / c.ctas - 1024;
@@ -531,7 +541,7 @@ size_t fx_smem_bytes(int dir, int N) { return fx_cfg(dir, N).smem; }
 
 static size_t fx_smem_max(int dir) {
     size_t mx = 0;
-    for (int n = 2; n <= 64; n++) mx = fx_smem_bytes(dir, n) > mx ? fx_smem_bytes(dir, n) : mx;
+    for (int n = 2; n <= 128; n++) mx = fx_smem_bytes(dir, n) > mx ? fx_smem_bytes(dir, n) : mx;
     return mx;
 }
 
@@ -562,6 +572,7 @@ cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int
     fp.N = N;
     fp.Np = Np;
     fp.Kp = Kp;
+    fp.Npp = Np > 64 ? 64 : Np;
     const FxCfg cfg = fx_cfg(dir, N);
     fp.tmem_cols = cfg.cols;
     fp.nstg = cfg.nstg;

@@ -18,6 +18,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=0, help="RK steps (one graph)")
     ap.add_argument("--time", action="store_true", help="print per-kernel CUDA-event times")
     ap.add_argument("--precision", type=int, default=0, help="0 FP64, 1 split BF16 x3, 2 TF32")
+    ap.add_argument("--coupling", type=int, default=0, help="0 unsplit, 1 split (fluid RK, BSSN Euler)")
+    ap.add_argument("--integrator", type=int, default=0, help="0 SSP-RK3, 1 RK4")
     a = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -28,7 +30,8 @@ def main(argv=None):
     from workloads import config, primitive_profiles
 
     cfg = config(a.config)
-    grid, phys, opts = pkg.make_structs(cfg, precision=a.precision)
+    grid, phys, opts = pkg.make_structs(cfg, precision=a.precision, coupling=a.coupling,
+                                        integrator=a.integrator)
     stream = torch.cuda.Stream()
     ctx = pkg.Context(grid, phys, opts, stream.cuda_stream)
     r, t, ph = ctx.coords()

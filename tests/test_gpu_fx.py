@@ -129,13 +129,17 @@ def test_contraction_nan_and_zero(pkg, contraction):
     ctx.close()
 
 
-def test_contraction_sizes(pkg):
-    """Every size class of the tensor-core kernel (K chunks of 16 and 32, Np 16..64) on
-    smooth data."""
+@pytest.mark.parametrize("contraction", [0, 1])
+def test_contraction_sizes(pkg, contraction):
+    """Every size class of the tensor-core kernel (output width 16..64 in one pass, 128 in
+    two passes of 64 columns) on smooth data, beside the FP64-unit kind.  The bar, 3e-14
+    of the bound, is about twice the worst-case bound K 2^-53 of an FP64 dot product of
+    length K = 128 (the oracle's own coefficient route is part of the difference)."""
     worst = {}
-    for nr, nt, nph in ((4, 5, 4), (16, 17, 16), (24, 33, 34), (40, 48, 64), (64, 20, 48)):
+    for nr, nt, nph in ((4, 5, 4), (16, 17, 16), (24, 33, 34), (40, 48, 64), (64, 20, 48),
+                        (8, 72, 8), (8, 100, 8), (8, 8, 96), (8, 8, 128)):
         cfg = config("c1", n_elem=2, n_r=nr, n_theta=nt, n_phi=nph)
-        g, ctx = _setup(pkg, cfg, 0)
+        g, ctx = _setup(pkg, cfg, contraction)
         absD = _abs_ops(g)
         ops = (g.d_r, g.d_t, g.d_p)
         u = np.sin(g.R) * np.cos(2 * g.T) * (1.5 + np.sin(3 * g.P)) + 0.1 * g.R
@@ -143,6 +147,6 @@ def test_contraction_sizes(pkg):
             got = _run(pkg, ctx, u, d)
             err = np.abs(got - ops[d](u)) / _bound(g, absD, u, d)
             worst[f"{(nr, nt, nph)[d]} nodes dir {d}"] = float(err.max())
-            assert err.max() <= 2e-14, ((nr, nt, nph), d, float(err.max()))
+            assert err.max() <= 3e-14, ((nr, nt, nph), d, float(err.max()))
         ctx.close()
-    _report("sizes_contraction0", worst)
+    _report(f"sizes_contraction{contraction}", worst)
