@@ -91,7 +91,13 @@ typedef struct {
  * unsplit right-hand side over all 32 variables per Runge-Kutta stage; 1 the paper's
  * coupled loop ("Coupled Main Loop"): per step the fluid is advanced by the selected
  * Runge-Kutta scheme on the frozen metric, then BSSN + gauge take one forward-Euler step
- * with the fluid frozen (matter sources from the updated fluid), then the filter. */
+ * with the fluid frozen (matter sources from the updated fluid), then the filter.  glm: 1
+ * adds GLM divergence cleaning ("GLM Constraint Damping Source") with the scalar psi as
+ * variable 32 (state arrays then hold 33 fields, see grmhd_num_vars): d_t psi =
+ * alpha (-glm_ch^2 D_i B^i - psi / glm_tau), D_i B^i = d_i(sqrt(gamma) B^i) / sqrt(gamma),
+ * and -alpha sqrt(gamma) gamma^ij d_j psi added to the right-hand side of sqrt(gamma) B^i
+ * (defaults glm_ch = 1, glm_tau = 1; psi starts at zero, is filtered with the Valencia
+ * variables and averaged at duplicated interface nodes). */
 typedef struct {
     int precision;
     int integrator;
@@ -105,6 +111,8 @@ typedef struct {
     double c2p_tol;
     int contraction;
     int coupling;
+    int glm;
+    double glm_ch, glm_tau;
 } grmhd_opts;
 
 typedef struct grmhd_ctx grmhd_ctx;
@@ -125,6 +133,11 @@ int grmhd_destroy(grmhd_ctx* ctx);
 /* Number of nodes E * n_r * n_theta * n_phi. */
 long long grmhd_num_points(const grmhd_ctx* ctx);
 
+/* Evolved variables per node: GRMHD_NV (32), or 33 with GLM cleaning (psi last).  Every
+ * state and right-hand-side array of the context holds this many fields of
+ * grmhd_num_points doubles; -1 for a NULL context. */
+int grmhd_num_vars(const grmhd_ctx* ctx);
+
 /* Node coordinates in canonical point order (3 arrays of num_points doubles: r, theta,
  * phi).  Any of the pointers may be NULL. Host memory. */
 int grmhd_coords(const grmhd_ctx* ctx, double* r, double* theta, double* phi);
@@ -140,13 +153,13 @@ int grmhd_coords(const grmhd_ctx* ctx, double* r, double* theta, double* phi);
 int grmhd_init_prims(grmhd_ctx* ctx, const double* rho, const double* p, const double* vr,
                      const double* vth, const double* vph, const double* A_phi);
 
-/* Copy a full canonical state (GRMHD_NV * num_points doubles) in / out. set_state
+/* Copy a full canonical state (grmhd_num_vars * num_points doubles) in / out. set_state
  * also resets the primitive guess (the next primitive recovery starts from a bracket). */
 int grmhd_set_state(grmhd_ctx* ctx, const double* state, int on_device);
 int grmhd_get_state(grmhd_ctx* ctx, double* state, int on_device);
 
 /* L(U) of the current state: one right-hand-side evaluation (one Runge-Kutta stage)
- * without the post-step filter, written to rhs_out (GRMHD_NV * num_points doubles). */
+ * without the post-step filter, written to rhs_out (grmhd_num_vars * num_points doubles). */
 int grmhd_rhs(grmhd_ctx* ctx, double* rhs_out, int on_device);
 
 /* Primitive recovery of the current state into prim_out (GRMHD_NPRIM * num_points
@@ -205,8 +218,11 @@ int grmhd_kernel_times(grmhd_ctx* ctx, int reps, double* ms_out, double* flops_o
 int grmhd_batch_create(int n, const grmhd_grid* grids, const grmhd_physics* phys,
                        const grmhd_opts* opts, void* cuda_stream, grmhd_batch** out);
 int grmhd_batch_num_groups(const grmhd_batch* b);
-/* nodes of instance i (its canonical arrays have GRMHD_NV * that many doubles) */
+/* nodes of instance i (its canonical arrays have grmhd_batch_num_vars(b, i) * that many
+ * doubles) */
 long long grmhd_batch_num_points(const grmhd_batch* b, int i);
+/* evolved variables of instance i (32, or 33 with GLM cleaning); -1 on a bad index */
+int grmhd_batch_num_vars(const grmhd_batch* b, int i);
 /* node coordinates of instance i (host arrays of num_points doubles, any may be NULL) */
 int grmhd_batch_coords(const grmhd_batch* b, int i, double* r, double* theta, double* phi);
 /* initial data of instance i from primitives on its nodes (as grmhd_init_prims) */

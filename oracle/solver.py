@@ -29,6 +29,17 @@ Chebyshev-Fourier grids" without stating the coupling):
   updated fluid (first-order Lie splitting; the paper's "half-step" is read as the
   fluid half of the split step, both halves advancing by dt, since a fluid advanced by
   dt/2 per step would fall behind the metric);
+* GLM divergence cleaning ("GLM Constraint Damping Source"), option glm = 1: a 33rd
+  variable psi with d_t psi = alpha (-c_h^2 D_i B^i - psi / tau), D_i B^i =
+  d_i(sqrt(gamma) B^i) / sqrt(gamma) the covariant divergence, and the source
+  -alpha sqrt(gamma) gamma^ij d_j psi added to the right-hand side of sqrt(gamma) B^i
+  (readings: the paper's flat-space "div B" is the covariant divergence; both terms
+  carry the lapse, as every source of the Valencia system does; the field source has
+  the sign of Dedner et al. 2002, -grad psi, since the printed +d_i psi makes the psi-B
+  subsystem anti-damped instead of a wave equation; c_h = 1, tau = 1 by default, the
+  paper states no values).  Radial derivatives of psi and the divergence are averaged
+  at interfaces, psi is filtered with the Valencia variables and averaged at duplicated
+  nodes after the filter, like the BSSN variables;
 * post-step filter: exponential (alpha = 36, p = 8) on the Chebyshev modes in r
   (per element) and theta and on the Fourier modes in phi, plus the 2/3 rule in
   phi; then the BSSN variables of duplicated interface nodes are averaged.
@@ -50,6 +61,7 @@ SYM = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
 # canonical variable slots
 I_GT, I_PHI, I_AT, I_K, I_GAM, I_ALPHA, I_BETA, I_BG = 0, 6, 7, 13, 14, 17, 18, 21
 I_D, I_S, I_TAU, I_B = 24, 25, 28, 29
+I_PSI = 32                      # GLM scalar (glm = 1 only: 33 variables)
 N_BSSN = 24
 # fields whose first derivatives are taken (all BSSN + gauge except the driver B^i)
 DERIV1 = list(range(0, 21))
@@ -85,6 +97,9 @@ class Params:
     eps_atm: float = 1e-10       # floor of the specific internal energy
     coupling: int = 0            # 0 unsplit method of lines, 1 the paper's split loop
     evolve_fluid: int = 1        # 0: Valencia right-hand side zero (BSSN half of a split step)
+    glm: int = 0                 # 1: GLM divergence cleaning with the scalar psi (variable 32)
+    glm_ch: float = 1.0
+    glm_tau: float = 1.0
 
     @classmethod
     def from_config(cls, cfg, **kw):
@@ -283,6 +298,15 @@ def rhs_from_prims(U, prim, g: Grid, p: Params, freeze_outer=True):
     rhs[I_S:I_S + 3] += np.moveaxis(asg[..., None] * S_S, -1, 0)
     rhs[I_TAU] += asg * S_tau
 
+    # ---- GLM divergence cleaning
+    if p.glm:
+        psi = U[I_PSI]
+        dpsi = np.stack([g.average_interfaces(g.d_r(psi)), g.d_t(psi), g.d_p(psi)], axis=-1)
+        divB = g.average_interfaces(g.d_r(U[I_B]) + g.d_t(U[I_B + 1]) + g.d_p(U[I_B + 2]))
+        ginv = ks.inv3(gam)
+        rhs[I_PSI] = alpha * (-p.glm_ch ** 2 * divB / sqg - psi / p.glm_tau)
+        rhs[I_B:I_B + 3] += np.moveaxis(-asg[..., None] * np.einsum("...ij,...j->...i", ginv, dpsi), -1, 0)
+
     # interface penalty (Rusanov) for the Valencia variables
     if E > 1:
         wend = cc_end_weight(p.n_r)
@@ -315,7 +339,7 @@ def rhs_from_prims(U, prim, g: Grid, p: Params, freeze_outer=True):
         rhs[I_ALPHA] = r["alpha"]
 
     if not p.evolve_fluid:
-        rhs[I_D:I_D + 8] = 0.0
+        rhs[I_D:] = 0.0
     # frozen outer boundary
     if freeze_outer:
         rhs[:, E - 1, -1] = 0.0
@@ -339,7 +363,7 @@ def apply_filter(U, g: Grid, p: Params):
     them by O(10%) (reading of the paper's "filter every mode")."""
     out = U.copy()
     m = p.filter_mask
-    for grp, sl in ((0, slice(N_BSSN, NV)), (3, slice(0, N_BSSN))):
+    for grp, sl in ((0, slice(N_BSSN, U.shape[0])), (3, slice(0, N_BSSN))):
         if m & (1 << grp):
             for e in range(p.n_elem):
                 out[sl, e] = sp.cheb_filter(out[sl, e], g.xr, axis=1, alpha=p.filt_alpha,
@@ -350,6 +374,8 @@ def apply_filter(U, g: Grid, p: Params):
             out[sl] = sp.fourier_filter(out[sl], axis=4, alpha=p.filt_alpha, p=p.filt_p,
                                         dealias23=bool(p.dealias23_phi))
     out[:N_BSSN] = g.average_interfaces(out[:N_BSSN])
+    if U.shape[0] > NV:
+        out[I_PSI] = g.average_interfaces(out[I_PSI])
     return out
 
 
@@ -437,7 +463,7 @@ def initial_state(g: Grid, p: Params, prim):
     field is B~^r = d_theta A_phi, B~^theta = -d_r A_phi, B~^phi = 0 (so that
     d_i B~^i = 0 for the tensor-product operators), B^i = B~^i / sqrt(gamma)."""
     ksd = ks.bssn_data(p.M, p.a, g.R, g.T)
-    U = np.zeros((NV,) + g.shape)
+    U = np.zeros((NV + (1 if p.glm else 0),) + g.shape)
     for n, (i, j) in enumerate(SYM):
         U[I_GT + n] = ksd["gt"][..., i, j]
         U[I_AT + n] = ksd["At"][..., i, j]

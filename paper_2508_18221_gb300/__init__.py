@@ -34,7 +34,8 @@ class Opts(C.Structure):
                 ("gauge", C.c_int), ("eta", C.c_double), ("cfl", C.c_double),
                 ("filter", C.c_int), ("filt_alpha", C.c_double), ("filt_p", C.c_double),
                 ("dealias23_phi", C.c_int), ("c2p_maxit", C.c_int), ("c2p_tol", C.c_double),
-                ("contraction", C.c_int), ("coupling", C.c_int)]
+                ("contraction", C.c_int), ("coupling", C.c_int), ("glm", C.c_int),
+                ("glm_ch", C.c_double), ("glm_tau", C.c_double)]
 
 
 _P = C.c_void_p
@@ -46,6 +47,7 @@ SIGNATURES = {
                                C.POINTER(_P)]),
     "grmhd_destroy": (C.c_int, [_P]),
     "grmhd_num_points": (C.c_longlong, [_P]),
+    "grmhd_num_vars": (C.c_int, [_P]),
     "grmhd_coords": (C.c_int, [_P, _P, _P, _P]),
     "grmhd_init_prims": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "grmhd_set_state": (C.c_int, [_P, _P, C.c_int]),
@@ -61,6 +63,7 @@ SIGNATURES = {
                                      C.POINTER(Opts), _P, C.POINTER(_P)]),
     "grmhd_batch_num_groups": (C.c_int, [_P]),
     "grmhd_batch_num_points": (C.c_longlong, [_P, C.c_int]),
+    "grmhd_batch_num_vars": (C.c_int, [_P, C.c_int]),
     "grmhd_batch_coords": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "grmhd_batch_init_prims": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P]),
     "grmhd_batch_set_state": (C.c_int, [_P, C.c_int, _P, C.c_int]),
@@ -137,6 +140,7 @@ class Context:
         self.h = h
         self.grid, self.phys, self.opts = grid, phys, opts
         self.n_points = int(self.lib.grmhd_num_points(h))
+        self.nv = int(self.lib.grmhd_num_vars(h))
 
     def close(self):
         if self.h:
@@ -237,6 +241,9 @@ class Batch:
 
     def num_points(self, i):
         return int(self.lib.grmhd_batch_num_points(self.h, i))
+
+    def num_vars(self, i):
+        return int(self.lib.grmhd_batch_num_vars(self.h, i))
 
     def coords(self, i):
         import numpy as np

@@ -39,7 +39,9 @@ struct grmhd_ctx {
     double* d1;
     double* d2;
     double* divF;
-    double* scratch;         // NV * P
+    double* scratch;         // nv * P
+    double* divB;            // d_i (sqrt(gamma) B^i) (GLM only)
+    int nv;                  // evolved variables: GRMHD_NV, + 1 (psi) with GLM
     double* Dr;              // Nr x Nr reference CGL matrix on [-1, 1]
     double* Dt;              // Nt x Nt Gauss matrix scaled to [theta_min, theta_max]
     double* Dp;              // circulant row
@@ -135,6 +137,7 @@ extern "C" int grmhd_defaults(grmhd_grid* g, grmhd_physics* ph, grmhd_opts* o) {
         o->dealias23_phi = 1; o->c2p_maxit = 60; o->c2p_tol = 1e-15;
         o->contraction = 0;
         o->coupling = 0;
+        o->glm = 0; o->glm_ch = 1.0; o->glm_tau = 1.0;
     }
     return GRMHD_OK;
 }
@@ -164,6 +167,8 @@ static int validate(const grmhd_grid* g, const grmhd_physics* ph, const grmhd_op
     if (o->filter < 0 || o->filter > 63) { strcpy(msg, "filter mask must be in [0, 63]"); return GRMHD_EINVAL; }
     if (o->contraction != 0 && o->contraction != 1) { strcpy(msg, "contraction must be 0 or 1"); return GRMHD_EINVAL; }
     if (o->coupling != 0 && o->coupling != 1) { strcpy(msg, "coupling must be 0 or 1"); return GRMHD_EINVAL; }
+    if (o->glm != 0 && o->glm != 1) { strcpy(msg, "glm must be 0 or 1"); return GRMHD_EINVAL; }
+    if (o->glm && (!(o->glm_ch >= 0.0) || !(o->glm_tau > 0.0))) { strcpy(msg, "need glm_ch >= 0 and glm_tau > 0"); return GRMHD_EINVAL; }
     return GRMHD_OK;
 }
 
@@ -172,7 +177,7 @@ static void free_ctx(grmhd_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     double** bufs[] = {&c->U[0], &c->U[1], &c->U[2], &c->acc, &c->prim, &c->flux, &c->tmn, &c->lam,
                        &c->d1, &c->d2, &c->divF, &c->scratch, &c->Dr, &c->Dt, &c->Dp, &c->Fr,
-                       &c->Ft, &c->Fp, &c->r_scale, &c->wq, &c->hmin, &c->dt, &c->diag};
+                       &c->Ft, &c->Fp, &c->r_scale, &c->wq, &c->hmin, &c->dt, &c->diag, &c->divB};
     for (double** b : bufs)
         if (*b) cudaFree(*b);
     for (int k = 0; k < 3; k++) {
@@ -264,6 +269,11 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
     c->pp.rho_atm = phys->rho_atm; c->pp.eps_atm = phys->eps_atm;
     c->pp.eta = opts->eta; c->pp.gauge = opts->gauge; c->pp.evolve_metric = opts->evolve_metric;
     c->pp.evolve_fluid = 1;
+    c->pp.glm = opts->glm;
+    c->pp.glm_ch2 = opts->glm_ch * opts->glm_ch;
+    c->pp.glm_itau = 1.0 / opts->glm_tau;
+    c->nv = NV + opts->glm;
+    const int nv = c->nv, glm = opts->glm;
     c->pp.c2p_maxit = opts->c2p_maxit; c->pp.c2p_tol = opts->c2p_tol;
     std::vector<double> wcgl = quad_weights(Nr, true);
     c->pp.w_end = wcgl[0];
@@ -325,16 +335,17 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
     // device memory
     cudaError_t ce = cudaSuccess;
 #define AL(ptr, n) if (ce == cudaSuccess) ce = dalloc(&(ptr), (size_t)(n))
-    for (int b = 0; b < 3; b++) AL(c->U[b], NV * P);
-    if (opts->integrator == 1) AL(c->acc, NV * P);
+    for (int b = 0; b < 3; b++) AL(c->U[b], nv * P);
+    if (opts->integrator == 1) AL(c->acc, nv * P);
     AL(c->prim, N_PRIM * P);
     AL(c->flux, N_FLUX * P);
     AL(c->tmn, N_TMN * P);
     AL(c->lam, P);
-    AL(c->d1, N_D1 * 3 * P);
+    AL(c->d1, (N_D1 + glm) * 3 * P);
+    if (glm) AL(c->divB, P);
     AL(c->d2, N_D2 * 6 * P);
     AL(c->divF, 8 * P);
-    AL(c->scratch, NV * P);
+    AL(c->scratch, nv * P);
     AL(c->Dr, Nr * Nr); AL(c->Dt, Nt * Nt); AL(c->Dp, Np);
     AL(c->Fr, Nr * Nr); AL(c->Ft, Nt * Nt); AL(c->Fp, Np);
     AL(c->r_scale, E); AL(c->wq, P); AL(c->hmin, ninst); AL(c->dt, ninst); AL(c->diag, 8);
@@ -354,9 +365,11 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         for (int dir = 0; dir < 3; dir++) {
             c->job_first[b][dir] = (int)jobs.size();
             for (int f = 0; f < N_D1; f++) add(c->U[b] + (long long)f * P, c->d1 + ((long long)f * 3 + dir) * P, 0);
+            if (glm) add(c->U[b] + (long long)V_PSI * P, c->d1 + ((long long)N_D1 * 3 + dir) * P, 0);
             for (int v = 0; v < 8; v++) add(c->flux + ((long long)dir * 8 + v) * P, c->divF + (long long)v * P, dir > 0);
+            if (glm) add(c->U[b] + (long long)(V_B + dir) * P, c->divB, dir > 0);
         }
-    c->job_first_n = N_D1 + 8;
+    c->job_first_n = N_D1 + 8 + 2 * glm;
     const int vars2[N_D2] = {0, 1, 2, 3, 4, 5, 6, 17, 18, 19, 20};
     // second derivatives, each mixed pair with the cheaper outer operator (same map: the
     // operators commute, and D_theta commutes with the interface mean):
@@ -389,8 +402,8 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
                 c->job_filter[b][dir][grp] = (int)jobs.size();
                 const double* src = dir == 0 ? c->U[b] : (dir == 1 ? c->scratch : c->U[b]);
                 double* dst = dir == 0 ? c->scratch : (dir == 1 ? c->U[b] : c->U[0]);
-                int v0 = grp == 0 ? V_D : 0, nv = grp == 0 ? 8 : N_BSSN;
-                for (int v = v0; v < v0 + nv; v++) add(src + (long long)v * P, dst + (long long)v * P, 0);
+                int v0 = grp == 0 ? V_D : 0, ng = grp == 0 ? 8 + glm : N_BSSN;
+                for (int v = v0; v < v0 + ng; v++) add(src + (long long)v * P, dst + (long long)v * P, 0);
             }
     c->job_dbg = (int)jobs.size();
     for (int k = 0; k < 64; k++) add(nullptr, nullptr, 0);
@@ -406,7 +419,7 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         cudaMemcpyAsync(c->iface_dev, iface.data(), E, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(c->elem_inst_dev, c->elem_inst.data(), sizeof(int) * E, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(c->prim, 0, sizeof(double) * N_PRIM * P, s) != cudaSuccess ||
-        cudaMemsetAsync(c->U[0], 0, sizeof(double) * NV * P, s) != cudaSuccess ||
+        cudaMemsetAsync(c->U[0], 0, sizeof(double) * nv * P, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         free_ctx(c);
         return GRMHD_ECUDA;
@@ -482,7 +495,9 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
             for (int dir = 0; dir < 3; dir++) {
                 c->tc_first[b][dir] = (int)tj.size();
                 for (int f = 0; f < N_D1; f++) addt(c->U[b] + (long long)f * P, d1f + ((long long)f * 3 + dir) * P, 0);
+                if (opts->glm) addt(c->U[b] + (long long)V_PSI * P, d1f + ((long long)N_D1 * 3 + dir) * P, 0);
                 for (int v = 0; v < 8; v++) addt(c->flux + ((long long)dir * 8 + v) * P, dFf + (long long)v * P, dir > 0);
+                if (opts->glm) addt(c->U[b] + (long long)(V_B + dir) * P, reinterpret_cast<float*>(c->divB), dir > 0);
             }
         const int vars2[N_D2] = {0, 1, 2, 3, 4, 5, 6, 17, 18, 19, 20};
         c->tc_second[0] = (int)tj.size();
@@ -525,6 +540,8 @@ extern "C" int grmhd_destroy(grmhd_ctx* c) {
 
 extern "C" long long grmhd_num_points(const grmhd_ctx* c) { return c ? c->d.P : -1; }
 
+extern "C" int grmhd_num_vars(const grmhd_ctx* c) { return c ? c->nv : -1; }
+
 extern "C" int grmhd_coords(const grmhd_ctx* c, double* r, double* th, double* ph) {
     if (!c) return GRMHD_EINVAL;
     const Dims& d = c->d;
@@ -562,20 +579,28 @@ static int enqueue_first_derivs(grmhd_ctx* c, int b) {
     if (c->opts.precision > 0) {
         const int tf32 = c->opts.precision == 2;
         for (int dir = 0; dir < 3; dir++) {
-            CK(launch_contract_tc(dir, 0, c->d, c->tcjobs + c->tc_first[b][dir], N_D1 + 8, c->tc_img[dir], tf32,
+            CK(launch_contract_tc(dir, 0, c->d, c->tcjobs + c->tc_first[b][dir], c->job_first_n, c->tc_img[dir], tf32,
                                   c->r_scale, c->tc_err, c->stream));
             c->launches_tmp++;
         }
-        CK(launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d1), 3 * c->d.P, N_D1, c->stream));
+        CK(launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d1), 3 * c->d.P, N_D1 + c->pp.glm, c->stream));
         c->launches_tmp++;
+        if (c->pp.glm) {
+            CK(launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->divB), c->d.P, 1, c->stream));
+            if (c->d.E > 1) c->launches_tmp++;
+        }
         return GRMHD_OK;
     }
     for (int dir = 0; dir < 3; dir++) {
         CK(contract(c, dir, 0, c->jobs + c->job_first[b][dir], c->job_first_n));
         c->launches_tmp++;
     }
-    CK(launch_iface_avg(c->d, c->d1, 3 * c->d.P, N_D1, c->stream));
+    CK(launch_iface_avg(c->d, c->d1, 3 * c->d.P, N_D1 + c->pp.glm, c->stream));
     c->launches_tmp++;
+    if (c->pp.glm) {
+        CK(launch_iface_avg(c->d, c->divB, c->d.P, 1, c->stream));
+        if (c->d.E > 1) c->launches_tmp++;
+    }
     return GRMHD_OK;
 }
 
@@ -615,7 +640,7 @@ static int enqueue_stage(grmhd_ctx* c, int b, RKCoef co, double* out, const Phys
         if (st) return st;
     }
     CK(launch_rhs(c->d, pp, c->U[0], c->U[b], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
-                  c->divF, c->opts.precision > 0, c->r_scale, c->dt, co, out, c->acc, c->stream));
+                  c->divF, c->divB, c->opts.precision > 0, c->r_scale, c->dt, co, out, c->acc, c->stream));
     c->launches_tmp++;
     return GRMHD_OK;
 }
@@ -629,17 +654,22 @@ static int enqueue_filter(grmhd_ctx* c, int b) {
         double* dst = dir == 0 ? c->scratch : (dir == 1 ? c->U[b] : c->U[0]);
         for (int grp = 0; grp < 2; grp++) {
             int bit = (grp == 0 ? 1 : 8) << dir;
-            int v0 = grp == 0 ? V_D : 0, nv = grp == 0 ? 8 : N_BSSN;
+            // the Valencia group carries psi (variable 32, right after them) with GLM
+            int v0 = grp == 0 ? V_D : 0, ng = grp == 0 ? 8 + c->pp.glm : N_BSSN;
             if (m & bit) {
-                CK(contract(c, dir, 1, c->jobs + c->job_filter[b][dir][grp], nv));
+                CK(contract(c, dir, 1, c->jobs + c->job_filter[b][dir][grp], ng));
                 c->launches_tmp++;
             } else if (src != dst) {
-                CK(cudaMemcpyAsync(dst + v0 * P, src + v0 * P, sizeof(double) * nv * P, cudaMemcpyDeviceToDevice, c->stream));
+                CK(cudaMemcpyAsync(dst + v0 * P, src + v0 * P, sizeof(double) * ng * P, cudaMemcpyDeviceToDevice, c->stream));
             }
         }
     }
     CK(launch_iface_avg(c->d, c->U[0], P, N_BSSN, c->stream));
     c->launches_tmp++;
+    if (c->pp.glm) {
+        CK(launch_iface_avg(c->d, c->U[0] + (long long)V_PSI * P, P, 1, c->stream));
+        if (c->d.E > 1) c->launches_tmp++;
+    }
     return GRMHD_OK;
 }
 
@@ -674,7 +704,7 @@ static int enqueue_step(grmhd_ctx* c) {
         last = nb;
     }
     if (c->opts.filter) return enqueue_filter(c, last);
-    CK(cudaMemcpyAsync(c->U[0], c->U[last], sizeof(double) * NV * c->d.P, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->U[0], c->U[last], sizeof(double) * c->nv * c->d.P, cudaMemcpyDeviceToDevice, c->stream));
     return GRMHD_OK;
 }
 
@@ -693,12 +723,12 @@ static int copy_out(grmhd_ctx* c, double* dst, const double* src, size_t n, int 
 extern "C" int grmhd_set_state(grmhd_ctx* c, const double* state, int on_device) {
     if (!c || !state) return GRMHD_EINVAL;
     CK(cudaMemsetAsync(c->prim, 0, sizeof(double) * N_PRIM * c->d.P, c->stream));
-    return copy_in(c, c->U[0], state, (size_t)NV * c->d.P, on_device);
+    return copy_in(c, c->U[0], state, (size_t)c->nv * c->d.P, on_device);
 }
 
 extern "C" int grmhd_get_state(grmhd_ctx* c, double* state, int on_device) {
     if (!c || !state) return GRMHD_EINVAL;
-    return copy_out(c, state, c->U[0], (size_t)NV * c->d.P, on_device);
+    return copy_out(c, state, c->U[0], (size_t)c->nv * c->d.P, on_device);
 }
 
 // Canonical state (GRMHD_NV x P_i, instance-local layout) of instance `in` of the group:
@@ -710,7 +740,7 @@ static void build_instance_state(const grmhd_ctx* c, int in, const double* rho, 
     const Dims& d = c->d;
     const int Ei = c->inst_E[in], off = c->inst_off[in];
     const long long Pi = (long long)Ei * d.elem;
-    U.assign((size_t)NV * Pi, 0.0);
+    U.assign((size_t)c->nv * Pi, 0.0);   // psi (GLM) starts at zero
     double bssn[24];
     // Kerr-Schild BSSN data depends on (r, theta) only
     for (int e = 0; e < Ei; e++)
@@ -773,7 +803,7 @@ static int inst_set_state(grmhd_ctx* c, int in, const double* state, int on_devi
     // reset this instance's primitive guess (the next recovery starts from a bracket)
     CK(cudaMemset2DAsync(c->prim + (long long)c->inst_off[in] * c->d.elem, (size_t)c->d.P * sizeof(double), 0,
                          (size_t)Pi * sizeof(double), N_PRIM, c->stream));
-    return inst_copy(c, in, c->U[0], NV, state, nullptr, on_device, 1);
+    return inst_copy(c, in, c->U[0], c->nv, state, nullptr, on_device, 1);
 }
 
 extern "C" int grmhd_init_prims(grmhd_ctx* c, const double* rho, const double* p, const double* vr,
@@ -798,7 +828,7 @@ extern "C" int grmhd_rhs(grmhd_ctx* c, double* out, int on_device) {
     int st = enqueue_stage(c, 0, co, dst, c->pp);
     if (st) return st;
     c->launches_per_call = c->launches_tmp;
-    if (!on_device) return copy_out(c, out, c->scratch, (size_t)NV * c->d.P, 0);
+    if (!on_device) return copy_out(c, out, c->scratch, (size_t)c->nv * c->d.P, 0);
     return GRMHD_OK;
 }
 
@@ -863,7 +893,7 @@ extern "C" int grmhd_step(grmhd_ctx* c, double dt, int nsteps, double* dt_used) 
     CK(cudaMemsetAsync(c->nfail, 0, sizeof(unsigned long long), c->stream));
     CK(cudaGraphLaunch(c->gexec, c->stream));
     CK(cudaMemsetAsync(c->nan_flag, 0, sizeof(int), c->stream));
-    CK(launch_nan_check((long long)NV * c->d.P, c->U[0], c->nan_flag, c->stream));
+    CK(launch_nan_check((long long)c->nv * c->d.P, c->U[0], c->nan_flag, c->stream));
     int flag = 0;
     double dtv = dt;
     CK(cudaMemcpyAsync(&flag, c->nan_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -946,8 +976,8 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     // keep the state: U[1] <- U[0], work on U[1], U[2] holds the saved copy
-    CK(cudaMemcpyAsync(c->U[2], c->U[0], sizeof(double) * NV * P, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->U[1], c->U[0], sizeof(double) * NV * P, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->U[2], c->U[0], sizeof(double) * c->nv * P, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->U[1], c->U[0], sizeof(double) * c->nv * P, cudaMemcpyDeviceToDevice, c->stream));
     RKCoef co = {0, 0, 0, 0, -1};
     int st = GRMHD_OK;
     for (int k = 0; k < GRMHD_NKT && st == GRMHD_OK; k++) {
@@ -960,18 +990,18 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
             else if (k >= 1 && k <= 3) {
                 int dir = k - 1;
                 if (mixed) {
-                    e = launch_contract_tc(dir, 0, c->d, c->tcjobs + c->tc_first[1][dir], N_D1 + 8, c->tc_img[dir], tf32,
+                    e = launch_contract_tc(dir, 0, c->d, c->tcjobs + c->tc_first[1][dir], c->job_first_n, c->tc_img[dir], tf32,
                                            c->r_scale, c->tc_err, c->stream);
-                    fl[k] = tc_flops(c, dir) * (N_D1 + 8);
-                    by[k] = (double)P * (N_D1 + 8) * (8.0 + 4.0) + (dir > 0 ? 8.0 * 4.0 * P : 0.0);
+                    fl[k] = tc_flops(c, dir) * c->job_first_n;
+                    by[k] = (double)P * c->job_first_n * (8.0 + 4.0) + (dir > 0 ? (8.0 + c->pp.glm) * 4.0 * P : 0.0);
                 } else {
                     e = contract(c, dir, 0, c->jobs + c->job_first[1][dir], c->job_first_n);
                     fl[k] = contraction_flops(c, dir, 0) * c->job_first_n;
                     by[k] = (double)P * c->job_first_n * 16.0 + (dir > 0 ? 8.0 * 8.0 * P : 0.0);
                 }
             } else if (k == 4) {
-                e = mixed ? launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d1), 3 * P, N_D1, c->stream)
-                          : launch_iface_avg(c->d, c->d1, 3 * P, N_D1, c->stream);
+                e = mixed ? launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d1), 3 * P, N_D1 + c->pp.glm, c->stream)
+                          : launch_iface_avg(c->d, c->d1, 3 * P, N_D1 + c->pp.glm, c->stream);
             } else if (k >= 5 && k <= 7) {
                 int dir = k - 5;
                 const int nj[3] = {3 * N_D2, 2 * N_D2, N_D2};
@@ -991,15 +1021,15 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
                               : launch_iface_avg(c->d, c->d2 + x * P, 6 * P, N_D2, c->stream);
             }
             else if (k == 9) e = launch_rhs(c->d, c->pp, c->U[0], c->U[1], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
-                                            c->divF, c->opts.precision > 0, c->r_scale, c->dt, co, c->scratch,
+                                            c->divF, c->divB, c->opts.precision > 0, c->r_scale, c->dt, co, c->scratch,
                                             c->acc, c->stream);
             else {
                 int dir = k - 10;
                 // filter contraction of all 32 variables of U[1] (scratch <-> U[1] chain)
                 e = contract(c, dir, 1, c->jobs + c->job_filter[1][dir][1], N_BSSN);
-                if (e == cudaSuccess) e = contract(c, dir, 1, c->jobs + c->job_filter[1][dir][0], 8);
-                fl[k] = contraction_flops(c, dir, 1) * NV;
-                by[k] = (double)P * NV * 16.0;
+                if (e == cudaSuccess) e = contract(c, dir, 1, c->jobs + c->job_filter[1][dir][0], 8 + c->pp.glm);
+                fl[k] = contraction_flops(c, dir, 1) * c->nv;
+                by[k] = (double)P * c->nv * 16.0;
             }
             if (e != cudaSuccess) { st = set_err(c, GRMHD_ECUDA, "kernel_times: %s", cudaGetErrorString(e)); break; }
         }
@@ -1011,7 +1041,7 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    CK(cudaMemcpyAsync(c->U[0], c->U[2], sizeof(double) * NV * P, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->U[0], c->U[2], sizeof(double) * c->nv * P, cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (st) return st;
     for (int k = 0; k < n; k++) {
@@ -1110,6 +1140,11 @@ extern "C" long long grmhd_batch_num_points(const grmhd_batch* b, int i) {
     return (long long)c->inst_E[b->idx[i]] * c->d.elem;
 }
 
+extern "C" int grmhd_batch_num_vars(const grmhd_batch* b, int i) {
+    if (!b || i < 0 || i >= b->n) return -1;
+    return b->groups[b->grp[i]]->nv;
+}
+
 extern "C" int grmhd_batch_coords(const grmhd_batch* b, int i, double* r, double* th, double* ph) {
     if (!b || i < 0 || i >= b->n) return GRMHD_EINVAL;
     const grmhd_ctx* c = b->groups[b->grp[i]];
@@ -1145,7 +1180,7 @@ extern "C" int grmhd_batch_set_state(grmhd_batch* b, int i, const double* state,
 extern "C" int grmhd_batch_get_state(grmhd_batch* b, int i, double* state, int on_device) {
     if (!b || i < 0 || i >= b->n || !state) return GRMHD_EINVAL;
     grmhd_ctx* c = b->groups[b->grp[i]];
-    return inst_copy(c, b->idx[i], c->U[0], NV, nullptr, state, on_device, 0);
+    return inst_copy(c, b->idx[i], c->U[0], c->nv, nullptr, state, on_device, 0);
 }
 
 extern "C" int grmhd_batch_cfl_dt(grmhd_batch* b, double* dt_out) {

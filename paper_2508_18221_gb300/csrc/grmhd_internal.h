@@ -13,6 +13,7 @@ enum {
     NV = 32,
     V_GT = 0, V_PHI = 6, V_AT = 7, V_K = 13, V_GAM = 14, V_ALPHA = 17, V_BETA = 18, V_BG = 21,
     V_D = 24, V_S = 25, V_TAU = 28, V_B = 29, N_BSSN = 24, N_VAL = 8,
+    V_PSI = 32, NV_MAX = 33,   // GLM scalar (glm = 1: 33 variables)
     // differentiated fields: canonical variables 0..20 (all BSSN + gauge but B^i)
     N_D1 = 21,
     // second derivatives of gammatilde_ij (0..5), phi (6), alpha (17), beta^i (18..20)
@@ -43,6 +44,8 @@ struct PhysParams {
     double eta;
     int gauge, evolve_metric;
     int evolve_fluid;     // 0: Valencia right-hand side zero (BSSN half of a split step)
+    int glm;              // 1: GLM cleaning with psi (variable 32)
+    double glm_ch2, glm_itau;
     int c2p_maxit;
     double c2p_tol;
     double w_end;         // Clenshaw-Curtis end weight on [-1, 1] for n_r CGL nodes
@@ -76,7 +79,7 @@ struct RKCoef { double a, b, c, w; int acc_mode; };  // out = a U0 + b Us + c dt
 cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, const double* Us,
                        const double* prim, const double* flux, const double* tmn,
                        const double* lam, const void* d1, const void* d2,
-                       const void* divF, int deriv_fp32, const double* r_scale_dev,
+                       const void* divF, const void* divB, int deriv_fp32, const double* r_scale_dev,
                        const double* dt_dev, RKCoef co, double* out, double* acc, cudaStream_t s);
 // tensor-core contraction (kernels_tc.cu); op_img in the kernel's shared-memory layout
 cudaError_t launch_contract_tc(int dir, int in_fp32, const Dims& d, const TcJob* jobs, int njobs,

@@ -297,6 +297,7 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
                                              const DT* __restrict__ d1,
                                              const DT* __restrict__ d2,
                                              const DT* __restrict__ divF,
+                                             const DT* __restrict__ divB,
                                              const double* __restrict__ r_scale,
                                              const double* __restrict__ dt_dev, RKCoef co,
                                              double* __restrict__ out, double* __restrict__ acc) {
@@ -305,7 +306,8 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
     if (p >= P) return;
     const R PI = R(3.141592653589793);
     const R third = R(1.0 / 3.0), sixth = R(1.0 / 6.0), two3 = R(2.0 / 3.0);
-    R rhs[NV];
+    const int nv = NV + pp.glm;
+    R rhs[NV_MAX];
 
     // ------------------------------------------------------------ state and metric
     R gt[3][3], At[3][3];
@@ -434,6 +436,17 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
         rhs[V_D] = -(R)divF[0 * P + p];
         rhs[V_TAU] = -(R)divF[4 * P + p] + asg * Stau;
         for (int k = 0; k < 3; k++) rhs[V_B + k] = -(R)divF[(5 + k) * P + p];
+        // GLM cleaning: d_t psi = alpha (-c_h^2 D_i B^i - psi / tau) with the covariant
+        // divergence d_i(sqrt(gamma) B^i) / sqrt(gamma); field source -alpha sqrt(gamma)
+        // gamma^ij d_j psi (d psi: d1 field N_D1)
+        if (pp.glm) {
+            const R psi = (R)Us[(long long)V_PSI * P + p];
+            R dpsi[3];
+            for (int k = 0; k < 3; k++) dpsi[k] = (R)d1[((long long)N_D1 * 3 + k) * P + p];
+            rhs[V_PSI] = alpha * (-(R)pp.glm_ch2 * (R)divB[p] / sqg - psi * (R)pp.glm_itau);
+            for (int i = 0; i < 3; i++)
+                rhs[V_B + i] -= asg * (gi[i][0] * dpsi[0] + gi[i][1] * dpsi[1] + gi[i][2] * dpsi[2]);
+        }
 
         // interface penalty (Rusanov flux, strong form) at duplicated element-end nodes
         const long long shell = d.NtNp;
@@ -652,22 +665,22 @@ __global__ void __launch_bounds__(128) k_rhs(Dims d, PhysParams pp, const double
     }
 
     if (!pp.evolve_fluid)
-        for (int v = V_D; v < NV; v++) rhs[v] = R(0);
+        for (int v = V_D; v < nv; v++) rhs[v] = R(0);
     // frozen outer boundary node of each instance
     const int elem_id = (int)(p / d.elem);
     {
         const long long ir = (p / d.NtNp) % d.Nr;
         if (ir == d.Nr - 1 && !d.iface_next[elem_id])
-            for (int v = 0; v < NV; v++) rhs[v] = R(0);
+            for (int v = 0; v < nv; v++) rhs[v] = R(0);
     }
 
     // ------------------------------------------------------------ output
     const double dt = dt_dev ? dt_dev[d.elem_inst[elem_id]] : 0.0;
     if (co.acc_mode < 0) {
-        for (int v = 0; v < NV; v++) out[v * P + p] = (double)rhs[v];
+        for (int v = 0; v < nv; v++) out[v * P + p] = (double)rhs[v];
         return;
     }
-    for (int v = 0; v < NV; v++) {
+    for (int v = 0; v < nv; v++) {
         long long ix = v * P + p;
         double L = (double)rhs[v];
         double o;
@@ -699,18 +712,18 @@ cudaError_t launch_prep(const Dims& d, const PhysParams& pp, const double* U, do
 cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, const double* Us,
                        const double* prim, const double* flux, const double* tmn,
                        const double* lam, const void* d1, const void* d2,
-                       const void* divF, int deriv_fp32, const double* r_scale_dev,
+                       const void* divF, const void* divB, int deriv_fp32, const double* r_scale_dev,
                        const double* dt_dev, RKCoef co, double* out, double* acc, cudaStream_t s) {
     int bs = 128;
     long long nb = (d.P + bs - 1) / bs;
     if (deriv_fp32)
         k_rhs<float, float><<<(unsigned)nb, bs, 0, s>>>(d, pp, U0, Us, prim, flux, tmn, lam, (const float*)d1,
-                                                 (const float*)d2, (const float*)divF, r_scale_dev, dt_dev,
-                                                 co, out, acc);
+                                                 (const float*)d2, (const float*)divF, (const float*)divB,
+                                                 r_scale_dev, dt_dev, co, out, acc);
     else
         k_rhs<double, double><<<(unsigned)nb, bs, 0, s>>>(d, pp, U0, Us, prim, flux, tmn, lam, (const double*)d1,
-                                                  (const double*)d2, (const double*)divF, r_scale_dev,
-                                                  dt_dev, co, out, acc);
+                                                  (const double*)d2, (const double*)divF, (const double*)divB,
+                                                  r_scale_dev, dt_dev, co, out, acc);
     return cudaGetLastError();
 }
 

@@ -37,7 +37,7 @@ def pkg():
 
 def _ctx(pkg, cfg, **kw):
     import torch
-    opt_keys = ("evolve_metric", "gauge", "integrator", "filter", "contraction", "coupling")
+    opt_keys = ("evolve_metric", "gauge", "integrator", "filter", "contraction", "coupling", "glm", "precision")
     grid, phys, opts = pkg.make_structs(cfg, **{k: v for k, v in kw.items() if k in opt_keys})
     return pkg.Context(grid, phys, opts, torch.cuda.current_stream().cuda_stream)
 
