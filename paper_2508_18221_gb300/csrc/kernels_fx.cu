@@ -200,20 +200,15 @@ __device__ __forceinline__ double stg_at(const double* stg, int m, int k, int N)
     return DIR == 2 ? stg[m * stg_rs<DIR>(N) * 2 + k] : stg[k * 128 + m];
 }
 
-// 256 threads: warp w serves TMEM lane quadrant w & 3 (lines 32 (w & 3) .. + 31, one line
-// per lane) and half h = w >> 2 of the work of each line: digits of K values 8h .. 8h + 7
-// of every 16-wide K chunk, output columns h Np/2 .. (h + 1) Np/2 - 1 in the epilogue.
-//
-// Shared memory (bytes): [nstg staging buffers | A digits 7 x 128 x 16 x 2 |
-//   B digits 7 x Np x 16 x 2 | row exponents Np x 4 | line exponents 2 x 128 x 4 |
-//   mbarriers (staging x2, B, MMA) | tmem address]
 struct FxParams {
     const DerivJob* jobs;
     const uint8_t* img;
     long long img_estride;
     int N, Np, Kp, tmem_cols, nstg, njobs;
     int Npp;                 // output columns per pass (Np, or 64 when Np = 128)
-    long long ntiles;
+    int npass;               // Np / Npp
+    int b_all;               // 1: the operator digits of all K chunks stay in shared memory
+    long long ntiles;        // 128-line tiles of one field
     uint32_t stg_bytes;
     int* err;
 };
@@ -260,29 +255,111 @@ __device__ __forceinline__ void fx_stage(const Dims& d, const FxTile& tl, int N,
     }
 }
 
+
+// Warp roles (320 threads):
+//   warps 0-3  convert: thread m = line m of the item's tile; line exponent, operator row
+//              exponents, then the seven digit slices of each 16-wide K chunk into a
+//              two-stage ring of A buffers;
+//   warps 4-7  epilogue: thread m reads TMEM lane m (warp w serves lane quadrant w & 3),
+//              combines the five accumulators and stores the FP64 results;
+//   warp 8     stages the FP64 tiles in shared memory (bulk copies);
+//   warp 9     one thread loads the operator digits and issues the MMAs.
+// A work item is (field, 128-line tile, column pass); the CTA walks items blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Every role follows the same item sequence; they hand over
+// through mbarriers (full / empty pairs), so conversion of one item overlaps the MMAs
+// and the epilogue of the previous one.  Every wait is bounded in time (globaltimer);
+// after a timeout the CTA raises an abort flag, every role leaves its loop, and *err is
+// set.
+//
+// Shared memory (bytes): [staging x nstg | A ring 2 x (7 x 128 x 16 x 2) |
+//   B digits of all chunks (nchunks x 7 x Np x 16 x 2) | sEL 2 x 128 x 4 | sF 2 x 128 x 4 |
+//   barriers | tmem address | abort flag]
+constexpr int FXW_THREADS = 320;
+constexpr int NA_RING = 2;
+
+// exponents and their barriers alternate between two sets by item parity, so that the
+// converters write item k's line exponents while the epilogue still reads item k - 1's
+struct FxBars {
+    uint64_t stg_full[2], stg_empty[2], a_full[NA_RING], a_empty[NA_RING];
+    uint64_t acc_full, acc_empty[2], el_ready[2], b_full;
+};
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for the phase with the given parity, at most ~0.5 s; false on timeout or abort
+__device__ __forceinline__ bool bwait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    const uint64_t t0 = gtimer();
+    for (;;) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        if (done) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > 500000000ull) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void barrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 template <int DIR>
-__global__ void __launch_bounds__(256) k_contract_fx(Dims d, FxParams fp) {
+__device__ __forceinline__ void fx_item(const FxParams& fp, const Dims& d, long long it, FxTile* tl, int* pass,
+                                        int* job) {
+    const long long per_job = fp.ntiles * fp.npass;
+    *job = (int)(it / per_job);
+    const long long r = it - (long long)(*job) * per_job;
+    *pass = (int)(r % fp.npass);
+    fx_tile<DIR>(d, r / fp.npass, fp.N, tl);
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams fp) {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quad = warp & 3, half = warp >> 2;
-    const int m = quad * 32 + lane;  // this thread's line within the tile
-    const int N = fp.N, Np = fp.Np;
+    const int N = fp.N, Np = fp.Np, Npp = fp.Npp;
     constexpr int KC = 16, kcores = 2;
-    const uint32_t a_bytes = 128u * KC * 2;
+    const uint32_t a_bytes = 128u * KC * 2;            // one digit slice of one chunk
+    const uint32_t a_stage = NDIG * a_bytes;
     const uint32_t b_bytes = (uint32_t)Np * KC * 2;
     const uint32_t chunk_bytes = NDIG * b_bytes;
     const int nchunks = fp.Kp / KC;
+    const uint32_t op_bytes = (uint32_t)nchunks * chunk_bytes;
+    const uint32_t sb_bytes = fp.b_all ? op_bytes : chunk_bytes;
     uint8_t* sA = sm + fp.nstg * fp.stg_bytes;
-    uint8_t* sB = sA + NDIG * a_bytes;
-    int* sF = reinterpret_cast<int*>(sB + chunk_bytes);
-    int* sEL = sF + Np;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sEL + 256);  // [0,1] staging, [2] B, [3] MMA
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
-    const long long nitems = fp.ntiles * fp.njobs;
+    uint8_t* sB = sA + NA_RING * a_stage;
+    int* sEL = reinterpret_cast<int*>(sB + sb_bytes);   // [2][128]
+    int* sF = sEL + 256;                                // [2][128]
+    FxBars* bars = reinterpret_cast<FxBars*>(sF + 256);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const long long nitems = fp.ntiles * fp.npass * fp.njobs;
 
     if (tid == 0) {
-        for (int b = 0; b < 4; b++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[b])));
+        for (int b = 0; b < 2; b++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars->stg_full[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars->stg_empty[b])));
+        }
+        for (int a = 0; a < NA_RING; a++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars->a_full[a])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars->a_empty[a])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars->acc_full)));
+        for (int t = 0; t < 2; t++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars->acc_empty[t])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars->el_ready[t])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars->b_full)));
         asm volatile("fence.mbarrier_init.release.cluster;");
+        *abort_flag = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -294,200 +371,254 @@ __global__ void __launch_bounds__(256) k_contract_fx(Dims d, FxParams fp) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
-    bool ok = true;
-    uint32_t n_commit = 0, n_bload = 0;  // completed phases of the MMA and B barriers
-    long long it = blockIdx.x;
-    if (warp == 0 && it < nitems) {
-        FxTile t;
-        fx_tile<DIR>(d, it % fp.ntiles, N, &t);
-        fx_stage<DIR>(d, t, N, fp.jobs[it / fp.ntiles].src, reinterpret_cast<double*>(sm), &bars[0], lane);
-    }
-    for (int li = 0; it < nitems; it += gridDim.x, li++) {
-        const int buf = li % fp.nstg;
-        const double* stg = reinterpret_cast<const double*>(sm + buf * fp.stg_bytes);
-        const long long nxt = it + gridDim.x;
-        const DerivJob job = fp.jobs[it / fp.ntiles];
-        FxTile tl;
-        fx_tile<DIR>(d, it % fp.ntiles, N, &tl);
-        // with two staging buffers the next item's tile is fetched now (its buffer was last
-        // read by the previous item, before that item's final MMA)
-        if (fp.nstg == 2 && warp == 0 && nxt < nitems) {
-            FxTile t;
-            fx_tile<DIR>(d, nxt % fp.ntiles, N, &t);
-            fx_stage<DIR>(d, t, N, fp.jobs[nxt / fp.ntiles].src,
-                          reinterpret_cast<double*>(sm + (buf ^ 1) * fp.stg_bytes), &bars[buf ^ 1], lane);
-        }
-        long long base;
-        long long stride;
-        const uint8_t* op = fp.img;
-        if (DIR == 0) {
-            base = (long long)tl.e * d.elem + tl.t0 + m;
-            stride = d.NtNp;
-            op = fp.img + tl.e * fp.img_estride;
-        } else {
-            const long long t = tl.t0 + m;
-            if (DIR == 1) {
-                const long long eil = t / d.Np;
-                base = eil * d.NtNp + (t - eil * d.Np);
-                stride = d.Np;
-            } else {
-                base = t * N;
-                stride = 1;
+    if (warp == 8) {
+        // ---------------------------------------------------------------- staging
+        int k = 0;
+        for (long long it = blockIdx.x; it < nitems; it += gridDim.x, k++) {
+            const int b = k % fp.nstg;
+            if (k >= fp.nstg) {
+                bool ok = true;
+                if (lane == 0) ok = bwait(&bars->stg_empty[b], (uint32_t)((k / fp.nstg - 1) & 1), abort_flag);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok) break;
             }
+            FxTile tl;
+            int pass, job;
+            fx_item<DIR>(fp, d, it, &tl, &pass, &job);
+            fx_stage<DIR>(d, tl, N, fp.jobs[job].src, reinterpret_cast<double*>(sm + b * fp.stg_bytes),
+                          &bars->stg_full[b], lane);
         }
-        const bool valid = m < tl.nlines;
-        const int* op_exp = reinterpret_cast<const int*>(op + (size_t)nchunks * chunk_bytes);
-        for (int n = tid; n < Np; n += 256) sF[n] = op_exp[n];
-        if (!mbar_wait(&bars[buf], (uint32_t)((li / fp.nstg) & 1))) ok = false;
-
-        // the line's largest biased exponent (each half scans half of the line)
-        {
-            int el = 0;
-            if (valid)
-                for (int j = half; j < N; j += 2)
-                    el = max(el, (int)((__double_as_longlong(stg_at<DIR>(stg, m, j, N)) >> 52) & 0x7FF));
-            sEL[half * 128 + m] = el;
-        }
-        __syncthreads();
-        const int EL = max(sEL[m], sEL[128 + m]);
-        const bool line_bad = EL == 0x7FF;
-
-        const int Npp = fp.Npp, npass = Np / Npp;
-        for (int ch = 0; ch < npass; ch++) {
-        for (int kc = 0; kc < nchunks; kc++) {
-            // the previous MMAs (previous chunk, pass or item) have finished reading A and B
-            if (n_commit > 0 && !mbar_wait(&bars[3], (n_commit - 1) & 1)) ok = false;
-            if (tid == 0) {
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bars[2])),
-                             "r"(chunk_bytes) : "memory");
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(sB)),
-                    "l"(op + (size_t)kc * chunk_bytes), "r"(chunk_bytes), "r"(smem_u32(&bars[2]))
-                    : "memory");
-            }
-            // this half's 8 K values of the chunk: one 16-byte core-matrix row per digit
-            {
-                const int k0 = kc * KC + half * 8;
-                uint32_t w[NDIG][4];
-                if (k0 >= N || !valid) {
-#pragma unroll
-                    for (int q = 0; q < NDIG; q++) w[q][0] = w[q][1] = w[q][2] = w[q][3] = 0u;
-                } else {
-#pragma unroll
-                    for (int h = 0; h < 4; h++) {
-                        const int k = k0 + 2 * h;
-                        const double u0 = k < N ? stg_at<DIR>(stg, m, k, N) : 0.0;
-                        const double u1 = k + 1 < N ? stg_at<DIR>(stg, m, k + 1, N) : 0.0;
-                        const unsigned long long z0 = digit_word(u0, EL), z1 = digit_word(u1, EL);
-                        const uint32_t l0 = (uint32_t)z0, h0 = (uint32_t)(z0 >> 32);
-                        const uint32_t l1 = (uint32_t)z1, h1 = (uint32_t)(z1 >> 32);
-                        // digit q (1 = most significant) is byte 7 - q of Z
-                        w[0][h] = pack_bf16(digit_val<1>(h0, 2), digit_val<1>(h1, 2));
-                        w[1][h] = pack_bf16(digit_val<2>(h0, 1), digit_val<2>(h1, 1));
-                        w[2][h] = pack_bf16(digit_val<3>(h0, 0), digit_val<3>(h1, 0));
-                        w[3][h] = pack_bf16(digit_val<4>(l0, 3), digit_val<4>(l1, 3));
-                        w[4][h] = pack_bf16(digit_val<5>(l0, 2), digit_val<5>(l1, 2));
-                        w[5][h] = pack_bf16(digit_val<6>(l0, 1), digit_val<6>(l1, 1));
-                        w[6][h] = pack_bf16(digit_val<7>(l0, 0), digit_val<7>(l1, 0));
-                    }
+    } else if (warp == 9) {
+        // ---------------------------------------------------------------- MMA issue
+        if (lane == 0) {
+            const uint32_t id = instr_desc_bf16(128, Npp);
+            const uint32_t lbo = 128u, sbo = (uint32_t)kcores * 128u;
+            int k = 0, cur_e = -1;
+            uint32_t n_b = 0;
+            for (long long it = blockIdx.x; it < nitems; it += gridDim.x, k++) {
+                FxTile tl;
+                int pass, job;
+                fx_item<DIR>(fp, d, it, &tl, &pass, &job);
+                // the previous item's MMAs have finished with TMEM and the operator
+                if (k > 0 && !bwait(&bars->acc_empty[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), abort_flag)) break;
+                const uint8_t* op = fp.img + (DIR == 0 ? tl.e * fp.img_estride : 0);
+                if (fp.b_all && cur_e != tl.e) {  // radial: per-element operator; theta, phi: once
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                                     smem_u32(&bars->b_full)),
+                                 "r"(op_bytes) : "memory");
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_u32(sB)),
+                        "l"(op), "r"(op_bytes), "r"(smem_u32(&bars->b_full))
+                        : "memory");
+                    n_b++;
+                    cur_e = tl.e;
                 }
-                const uint32_t off = (uint32_t)(((m >> 3) * kcores + half) * 128 + (m & 7) * 16);
-#pragma unroll
-                for (int q = 0; q < NDIG; q++)
-                    *reinterpret_cast<uint4*>(sA + q * a_bytes + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            // with one staging buffer the next item's tile is fetched once the last chunk of
-            // this one is converted
-            if (fp.nstg == 1 && ch == npass - 1 && kc == nchunks - 1 && warp == 0 && nxt < nitems) {
-                FxTile t;
-                fx_tile<DIR>(d, nxt % fp.ntiles, N, &t);
-                fx_stage<DIR>(d, t, N, fp.jobs[nxt / fp.ntiles].src, reinterpret_cast<double*>(sm), &bars[0],
-                              lane);
-            }
-            if (tid == 0) {
-                if (mbar_wait(&bars[2], n_bload & 1)) {
-                    const uint32_t id = instr_desc_bf16(128, Npp);
-                    const uint32_t lbo = 128u, sbo = (uint32_t)kcores * 128u;
-                    // this pass's operator rows ch Npp .. : whole 8-row core-matrix groups
-                    const uint32_t brow = (uint32_t)(ch * Npp / 8) * sbo;
-                    // digit pairs (q, l), 0-based, s = q + l <= 6 into accumulator min(s, 4);
-                    // within the folded accumulator the smallest terms first
+                if (fp.b_all && !bwait(&bars->b_full, (n_b - 1) & 1, abort_flag)) break;
+                const uint32_t brow = (uint32_t)(pass * Npp / 8) * sbo;
+                bool stop = false;
+                for (int kc = 0; kc < nchunks; kc++) {
+                    const int cg = k * nchunks + kc, a = cg % NA_RING;
+                    if (!fp.b_all) {
+                        // one chunk of the operator at a time: the previous chunk's MMAs (the
+                        // previous item's are done: acc_empty) have finished reading it
+                        if (kc > 0) {
+                            const int cp = cg - 1;
+                            if (!bwait(&bars->a_empty[cp % NA_RING], (uint32_t)((cp / NA_RING) & 1), abort_flag)) {
+                                stop = true;
+                                break;
+                            }
+                        }
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                                         smem_u32(&bars->b_full)),
+                                     "r"(chunk_bytes) : "memory");
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                smem_u32(sB)),
+                            "l"(op + (size_t)kc * chunk_bytes), "r"(chunk_bytes), "r"(smem_u32(&bars->b_full))
+                            : "memory");
+                        n_b++;
+                        if (!bwait(&bars->b_full, (n_b - 1) & 1, abort_flag)) { stop = true; break; }
+                    }
+                    if (!bwait(&bars->a_full[a], (uint32_t)((cg / NA_RING) & 1), abort_flag)) { stop = true; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t a0 = smem_u32(sA + a * a_stage);
+                    const uint32_t b0 = smem_u32(sB + (fp.b_all ? kc * chunk_bytes : 0)) + brow;
                     for (int sd = NDIG - 1; sd >= 0; sd--) {
                         const int g = sd < NACC - 1 ? sd : NACC - 1;
                         for (int q = 0; q <= sd; q++) {
                             const int l = sd - q;
                             const bool first = kc == 0 && q == 0 && (sd < NACC - 1 || sd == NDIG - 1);
-                            const uint64_t da = smem_desc(smem_u32(sA + q * a_bytes), lbo, sbo);
-                            const uint64_t db = smem_desc(smem_u32(sB + l * b_bytes) + brow, lbo, sbo);
-                            mma_bf16(tmem + (uint32_t)(g * Npp), da, db, id, first ? 0u : 1u);
+                            mma_bf16(tmem + (uint32_t)(g * Npp), smem_desc(a0 + q * a_bytes, lbo, sbo),
+                                     smem_desc(b0 + l * b_bytes, lbo, sbo), id, first ? 0u : 1u);
                         }
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        smem_u32(&bars[3])));
-                } else {
-                    ok = false;
-                    atomicExch(fp.err, 1);
-                    // let the copy in flight land before the shared memory is reused
-                    mbar_wait(&bars[2], n_bload & 1);
-                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bars[3])) : "memory");
+                        smem_u32(&bars->a_empty[a])));
                 }
-            }
-            n_bload++;
-            n_commit++;
-        }
-        if (!mbar_wait(&bars[3], (n_commit - 1) & 1)) ok = false;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-
-        // epilogue: TMEM lane m (this thread's line), this half's output columns of the
-        // pass, 8 at a time
-        const int c0 = ch * Npp + half * (Npp / 2), c1 = c0 + Npp / 2;
-        for (int cb = c0; cb < c1; cb += 8) {
-            uint32_t r[NACC][8];
-#pragma unroll
-            for (int g = 0; g < NACC; g++) {
-                const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * Npp + cb - ch * Npp);
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                             : "=r"(r[g][0]), "=r"(r[g][1]), "=r"(r[g][2]), "=r"(r[g][3]), "=r"(r[g][4]),
-                               "=r"(r[g][5]), "=r"(r[g][6]), "=r"(r[g][7])
-                             : "r"(ta));
-            }
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (ok && valid) {
-                double v[8];
-#pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    const long long R = combine(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]),
-                                                __uint_as_float(r[2][j]), __uint_as_float(r[3][j]),
-                                                __uint_as_float(r[4][j]), fp.Kp > 64);
-                    v[j] = scale_int(R, EL + sF[cb + j] - 2096);
-                }
-                if (line_bad)
-#pragma unroll
-                    for (int j = 0; j < 8; j++) v[j] = __longlong_as_double(0x7FF8000000000000ll);
-                double* p = job.dst + base + (long long)cb * stride;
-                if (job.accumulate) {
-#pragma unroll
-                    for (int j = 0; j < 8; j++)
-                        if (cb + j < N) p[(long long)j * stride] += v[j];
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 8; j++)
-                        if (cb + j < N) p[(long long)j * stride] = v[j];
-                }
+                if (stop) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&bars->acc_full)));
             }
         }
-        // TMEM (and, after the last pass, sF and sEL) free for the next pass or item
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncwarp();
+    } else if (warp < 4) {
+        // ---------------------------------------------------------------- conversion
+        const int m = tid;
+        int k = 0;
+        for (long long it = blockIdx.x; it < nitems; it += gridDim.x, k++) {
+            FxTile tl;
+            int pass, job;
+            fx_item<DIR>(fp, d, it, &tl, &pass, &job);
+            const int b = k % fp.nstg;
+            const double* stg = reinterpret_cast<const double*>(sm + b * fp.stg_bytes);
+            const bool valid = m < tl.nlines;
+            if (!bwait(&bars->stg_full[b], (uint32_t)((k / fp.nstg) & 1), abort_flag)) break;
+            int EL = 0;
+            if (valid)
+                for (int j = 0; j < N; j++)
+                    EL = max(EL, (int)((__double_as_longlong(stg_at<DIR>(stg, m, j, N)) >> 52) & 0x7FF));
+            // the epilogue of item k - 2 has read this set of sEL and sF
+            const int t = k & 1;
+            if (k > 1 && !bwait(&bars->acc_empty[t], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
+            sEL[t * 128 + m] = EL;
+            if (m < Np) {
+                const uint8_t* op = fp.img + (DIR == 0 ? tl.e * fp.img_estride : 0);
+                sF[t * 128 + m] = reinterpret_cast<const int*>(op + (size_t)op_bytes)[m];
+            }
+            __syncwarp();
+            if (lane == 0) barrive(&bars->el_ready[t]);
+            bool stop = false;
+            for (int kc = 0; kc < nchunks; kc++) {
+                const int cg = k * nchunks + kc, a = cg % NA_RING;
+                if (cg >= NA_RING && !bwait(&bars->a_empty[a], (uint32_t)((cg / NA_RING - 1) & 1), abort_flag)) {
+                    stop = true;
+                    break;
+                }
+                uint8_t* dstA = sA + a * a_stage;
+#pragma unroll
+                for (int g8 = 0; g8 < kcores; g8++) {
+                    const int k0 = kc * KC + g8 * 8;
+                    uint32_t w[NDIG][4];
+                    if (k0 >= N || !valid) {
+#pragma unroll
+                        for (int q = 0; q < NDIG; q++) w[q][0] = w[q][1] = w[q][2] = w[q][3] = 0u;
+                    } else {
+#pragma unroll
+                        for (int h = 0; h < 4; h++) {
+                            const int kk = k0 + 2 * h;
+                            const double u0 = kk < N ? stg_at<DIR>(stg, m, kk, N) : 0.0;
+                            const double u1 = kk + 1 < N ? stg_at<DIR>(stg, m, kk + 1, N) : 0.0;
+                            const unsigned long long z0 = digit_word(u0, EL), z1 = digit_word(u1, EL);
+                            const uint32_t l0 = (uint32_t)z0, h0 = (uint32_t)(z0 >> 32);
+                            const uint32_t l1 = (uint32_t)z1, h1 = (uint32_t)(z1 >> 32);
+                            w[0][h] = pack_bf16(digit_val<1>(h0, 2), digit_val<1>(h1, 2));
+                            w[1][h] = pack_bf16(digit_val<2>(h0, 1), digit_val<2>(h1, 1));
+                            w[2][h] = pack_bf16(digit_val<3>(h0, 0), digit_val<3>(h1, 0));
+                            w[3][h] = pack_bf16(digit_val<4>(l0, 3), digit_val<4>(l1, 3));
+                            w[4][h] = pack_bf16(digit_val<5>(l0, 2), digit_val<5>(l1, 2));
+                            w[5][h] = pack_bf16(digit_val<6>(l0, 1), digit_val<6>(l1, 1));
+                            w[6][h] = pack_bf16(digit_val<7>(l0, 0), digit_val<7>(l1, 0));
+                        }
+                    }
+                    const uint32_t off = (uint32_t)(((m >> 3) * kcores + g8) * 128 + (m & 7) * 16);
+#pragma unroll
+                    for (int q = 0; q < NDIG; q++)
+                        *reinterpret_cast<uint4*>(dstA + q * a_bytes + off) =
+                            make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) barrive(&bars->a_full[a]);
+            }
+            if (stop) break;
+            // this item's staging buffer is no longer read
+            __syncwarp();
+            if (lane == 0) barrive(&bars->stg_empty[b]);
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int quad = warp & 3, m = quad * 32 + lane;
+        const bool wide = fp.Kp > 64;
+        int k = 0;
+        for (long long it = blockIdx.x; it < nitems; it += gridDim.x, k++) {
+            FxTile tl;
+            int pass, job;
+            fx_item<DIR>(fp, d, it, &tl, &pass, &job);
+            const int t = k & 1;
+            if (!bwait(&bars->el_ready[t], (uint32_t)((k >> 1) & 1), abort_flag)) break;
+            if (!bwait(&bars->acc_full, (uint32_t)(k & 1), abort_flag)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const DerivJob jb = fp.jobs[job];
+            const bool valid = m < tl.nlines;
+            long long base, stride;
+            if (DIR == 0) {
+                base = (long long)tl.e * d.elem + tl.t0 + m;
+                stride = d.NtNp;
+            } else {
+                const long long t = tl.t0 + m;
+                if (DIR == 1) {
+                    const long long eil = t / d.Np;
+                    base = eil * d.NtNp + (t - eil * d.Np);
+                    stride = d.Np;
+                } else {
+                    base = t * N;
+                    stride = 1;
+                }
+            }
+            const int EL = sEL[t * 128 + m];
+            const bool line_bad = EL == 0x7FF;
+            for (int cb = 0; cb < Npp; cb += 8) {
+                uint32_t r[NACC][8];
+#pragma unroll
+                for (int g = 0; g < NACC; g++) {
+                    const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * Npp + cb);
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                 : "=r"(r[g][0]), "=r"(r[g][1]), "=r"(r[g][2]), "=r"(r[g][3]), "=r"(r[g][4]),
+                                   "=r"(r[g][5]), "=r"(r[g][6]), "=r"(r[g][7])
+                                 : "r"(ta));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int c0 = pass * Npp + cb;  // output column of r[.][0]
+                if (valid) {
+                    double v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        const long long R = combine(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]),
+                                                    __uint_as_float(r[2][j]), __uint_as_float(r[3][j]),
+                                                    __uint_as_float(r[4][j]), wide);
+                        v[j] = scale_int(R, EL + sF[t * 128 + c0 + j] - 2096);
+                    }
+                    if (line_bad)
+#pragma unroll
+                        for (int j = 0; j < 8; j++) v[j] = __longlong_as_double(0x7FF8000000000000ll);
+                    double* pd = jb.dst + base + (long long)c0 * stride;
+                    if (jb.accumulate) {
+#pragma unroll
+                        for (int j = 0; j < 8; j++)
+                            if (c0 + j < N) pd[(long long)j * stride] += v[j];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; j++)
+                            if (c0 + j < N) pd[(long long)j * stride] = v[j];
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) barrive(&bars->acc_empty[t]);
         }
     }
-    if (!ok && lane == 0) atomicExch(fp.err, 1);
+
+    // wind down: every role has left its loop; let bulk copies in flight land, then free TMEM
+    __syncthreads();
+    if (tid == 0 && *abort_flag) atomicExch(fp.err, 1);
+    if (*abort_flag) {
+        // bulk copies issued before the abort land within microseconds: give them 2 ms
+        const uint64_t t0 = gtimer();
+        while (gtimer() - t0 < 2000000ull) {
+        }
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(fp.tmem_cols));
@@ -507,17 +638,21 @@ static uint32_t fx_stg_bytes(int dir, int N) {
     return 128u * (uint32_t)N * 8u;
 }
 
-// everything but the staging buffers
-static size_t fx_rest_bytes(int Np) {
-    return (size_t)NDIG * (128u * 16 * 2 + (size_t)Np * 16 * 2) + (size_t)Np * 4 + 256 * 4 + 4 * sizeof(uint64_t) + 16;
+// everything but the staging buffers: the A ring, B digits (all K chunks when b_all, else
+// one chunk), exponents, barriers, TMEM address, abort flag
+static size_t fx_rest_bytes(int N, int b_all) {
+    int Np, Kp, KC;
+    fx_geometry(N, &Np, &Kp, &KC);
+    return (size_t)NA_RING * NDIG * 128u * KC * 2 + (size_t)NDIG * Np * (b_all ? Kp : KC) * 2 + 2 * 128 * 4 +
+           2 * 128 * 4 + sizeof(FxBars) + 16;
 }
 
-// CTAs per SM (TMEM: 5 Np columns, rounded to a power of two, from 512), staging buffers
+// CTAs per SM (TMEM: 5 Npp columns rounded to a power of two, from 512), staging buffers
 // (two when they fit the per-CTA share of the SM's 228 KB, 1 KB reserved per CTA) and the
 // dynamic shared memory, at least 1/(ctas + 1) of the SM so that no further CTA co-resides
 // (its TMEM allocation would wait for a CTA to finish all of its work)
 struct FxCfg {
-    int cols, ctas, nstg;
+    int cols, ctas, nstg, b_all;
     size_t smem;
 };
 static FxCfg fx_cfg(int dir, int N) {
@@ -528,8 +663,15 @@ static FxCfg fx_cfg(int dir, int N) {
     const int need = NACC * Npp;
     c.cols = need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : (need <= 256 ? 256 : 512)));
     c.ctas = c.cols <= 256 ? 2 : 1;
-    const size_t share = 233472 / c.ctas - 1024;
-    const size_t stg = fx_stg_bytes(dir, N), rest = fx_rest_bytes(Np);
+    size_t share = 233472 / c.ctas - 1024;
+    const size_t stg = fx_stg_bytes(dir, N);
+    c.b_all = stg + fx_rest_bytes(N, 1) <= share;
+    if (!c.b_all && c.ctas == 2) {  // try one CTA per SM with all chunks resident
+        c.ctas = 1;
+        share = 233472 - 1024;
+        c.b_all = stg + fx_rest_bytes(N, 1) <= share;
+    }
+    const size_t rest = fx_rest_bytes(N, c.b_all);
     c.nstg = 2 * stg + rest <= share ? 2 : 1;
     const size_t b = c.nstg * stg + rest;
     const size_t floor_ = 233472 / (c.ctas + 1) + 1;
@@ -573,9 +715,11 @@ cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int
     fp.Np = Np;
     fp.Kp = Kp;
     fp.Npp = Np > 64 ? 64 : Np;
+    fp.npass = Np / fp.Npp;
     const FxCfg cfg = fx_cfg(dir, N);
     fp.tmem_cols = cfg.cols;
     fp.nstg = cfg.nstg;
+    fp.b_all = cfg.b_all;
     fp.njobs = njobs;
     fp.stg_bytes = fx_stg_bytes(dir, N);
     fp.err = err;
@@ -586,12 +730,12 @@ cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long long nitems = fp.ntiles * njobs;
+    const long long nitems = fp.ntiles * fp.npass * njobs;
     const long long grid = nitems < (long long)cfg.ctas * nsm ? nitems : (long long)cfg.ctas * nsm;
     const size_t sm = cfg.smem;
-    if (dir == 0) k_contract_fx<0><<<(unsigned)grid, 256, sm, s>>>(d, fp);
-    else if (dir == 1) k_contract_fx<1><<<(unsigned)grid, 256, sm, s>>>(d, fp);
-    else k_contract_fx<2><<<(unsigned)grid, 256, sm, s>>>(d, fp);
+    if (dir == 0) k_contract_fx<0><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
+    else if (dir == 1) k_contract_fx<1><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
+    else k_contract_fx<2><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
     return cudaGetLastError();
 }
 
