@@ -21,14 +21,13 @@
 // bound of an FP64 dot product of these lengths.  A line holding Inf or NaN yields NaN
 // outputs; values below 2^-1022 (subnormals) enter as zero.
 //
-// Work item: 128 lines (tile) of one field (job) x K <= 64, processed in K chunks of
-// KC = 16.  The kernel is persistent: two CTAs per SM (one when five accumulators of 64
-// columns need all 512 TMEM columns) loop over the work items, each holding its TMEM
-// accumulators for its lifetime and staging the next item's FP64 tile while it computes
-// the current one.  The operator's seven digit slices for a chunk are
-// prepared on the host in the K-major core-matrix layout (8 rows x 16 bytes per core
-// matrix) and fetched with one cp.async.bulk; the line digits are formed by the threads
-// from the FP64 bits.  Waits are bounded and report through *err.
+// Work item: 128 lines (tile) of one field (job) x K <= 128, one pass of at most 64 output
+// columns, processed in K chunks of 16.  The kernel is persistent and warp-specialised
+// (roles below k_contract_fx): two CTAs per SM up to 32 nodes, one above, each holding
+// its TMEM accumulators for its lifetime.  The operator's seven digit slices are prepared
+// on the host in the K-major core-matrix layout (8 rows x 16 bytes per core matrix) and
+// fetched by cp.async.bulk; the line digits are formed by the converter warps from the
+// FP64 bits.  Waits are bounded in time and report through *err.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -58,14 +57,6 @@ __device__ __forceinline__ uint32_t instr_desc_bf16(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 22) && !done; it++)
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     "selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done) : "r"(smem_u32(bar)), "r"(phase) : "memory");
-    return done != 0;
-}
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t id, uint32_t acc) {
     asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -290,14 +281,16 @@ __device__ __forceinline__ uint64_t gtimer() {
     return t;
 }
 
-// wait for the phase with the given parity, at most ~0.5 s; false on timeout or abort
+// wait for the phase with the given parity, at most ~0.5 s; false on timeout or abort.
+// The suspend-time hint parks the warp in hardware until the phase completes (up to
+// 100 us per try), so waiting roles do not take issue slots from working ones.
 __device__ __forceinline__ bool bwait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
     const uint64_t t0 = gtimer();
     for (;;) {
         uint32_t done;
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
                      "selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+                     : "=r"(done) : "r"(smem_u32(bar)), "r"(parity), "r"(100000u) : "memory");
         if (done) return true;
         if (*abort_flag) return false;
         if (gtimer() - t0 > 500000000ull) {

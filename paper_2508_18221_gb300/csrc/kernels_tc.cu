@@ -48,10 +48,11 @@ __device__ __forceinline__ uint32_t core_off(int row, int k, int kcores, int es)
 
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
     uint32_t done = 0;
-    for (int it = 0; it < (1 << 22) && !done; it++)
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+    // 2^16 tries, each parking the warp up to 20 us (about 1.3 s in all)
+    for (int it = 0; it < (1 << 16) && !done; it++)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
                      "selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done) : "r"(smem_u32(bar)), "r"(phase) : "memory");
+                     : "=r"(done) : "r"(smem_u32(bar)), "r"(phase), "r"(20000u) : "memory");
     return done != 0;
 }
 
