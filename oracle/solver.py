@@ -42,7 +42,17 @@ Chebyshev-Fourier grids" without stating the coupling):
   nodes after the filter, like the BSSN variables;
 * post-step filter: exponential (alpha = 36, p = 8) on the Chebyshev modes in r
   (per element) and theta and on the Fourier modes in phi, plus the 2/3 rule in
-  phi; then the BSSN variables of duplicated interface nodes are averaged.
+  phi; then the BSSN variables of duplicated interface nodes are averaged;
+* theta_basis = 1, the paper's own polar discretisation ("Pseudo-spectral theta
+  derivative": Fourier on an evenly spaced theta grid): theta_k = (k + 1/2) pi / N_theta
+  on the whole of (0, pi), and every theta derivative and theta filter acts on the
+  double-Fourier extension of the line over [0, 2 pi), the values at 2 pi - theta being
+  s u(theta, phi + pi) with the parity s of the component (-1 per theta index of a
+  coordinate-basis component, and -1 once more for a sqrt(gamma)-weighted density, which
+  behaves like sin(theta) on the axis); the theta filter uses k_max = N_theta and, with
+  dealias23_theta, the 2/3 rule of the extended line.  The derivative of a component with
+  parity s has parity -s, so second derivatives are compositions with the parity of
+  the inner result.
 """
 from __future__ import annotations
 
@@ -67,6 +77,42 @@ N_BSSN = 24
 DERIV1 = list(range(0, 21))
 # fields whose second derivatives are taken: gammatilde_ij, phi, alpha, beta^i
 DERIV2 = [0, 1, 2, 3, 4, 5, 6, 17, 18, 19, 20]
+
+
+def theta_parity(nv=NV + 1):
+    """Sign of each canonical variable under the double-Fourier extension in theta.
+
+    The extension maps the chart (theta, phi) to (-theta, phi + pi), whose Jacobian is
+    diag(1, -1, 1) in (r, theta, phi): a coordinate-basis component changes sign once for
+    every theta index it carries.  The evolved Valencia variables are densities
+    sqrt(gamma) U, and sqrt(gamma) = r^2 sin(theta) x (a smooth even factor) changes sign
+    with sin(theta), so they take one more sign (reading: the extension is chosen to be
+    smooth across the axis)."""
+    par = np.ones(nv)
+    th = lambda *idx: (-1.0) ** sum(1 for i in idx if i == 1)
+    for n, (i, j) in enumerate(SYM):
+        par[I_GT + n] = th(i, j)
+        par[I_AT + n] = th(i, j)
+    for i in range(3):
+        par[I_GAM + i] = th(i)
+        par[I_BETA + i] = th(i)
+        par[I_BG + i] = th(i)
+        par[I_S + i] = -th(i)
+        par[I_B + i] = -th(i)
+    par[I_D] = -1.0
+    par[I_TAU] = -1.0
+    return par
+
+
+THETA_PAR = theta_parity()
+# parity of the theta flux sqrt(gamma) F^theta of each Valencia variable: one more
+# theta index than the variable itself
+FLUX_T_PAR = -THETA_PAR[I_D:I_D + 8]
+
+
+def _bc(par):
+    """Parity vector broadcast over the four grid axes."""
+    return np.asarray(par)[:, None, None, None, None]
 
 
 @dataclasses.dataclass
@@ -100,13 +146,16 @@ class Params:
     glm: int = 0                 # 1: GLM divergence cleaning with the scalar psi (variable 32)
     glm_ch: float = 1.0
     glm_tau: float = 1.0
+    theta_basis: int = 0         # 0 Chebyshev-Gauss in theta, 1 the paper's Fourier theta
+    dealias23_theta: int = 1     # 2/3 rule in the theta filter (theta_basis = 1 only)
 
     @classmethod
     def from_config(cls, cfg, **kw):
         base = dict(M=cfg.M, a=cfg.a, gamma_eos=cfg.gamma_eos, n_elem=cfg.n_elem,
                     r_min=cfg.r_min, r_max=cfg.r_max, elem_map=cfg.elem_map, n_r=cfg.n_r,
                     n_theta=cfg.n_theta, n_phi=cfg.n_phi, theta_min=cfg.theta_min,
-                    theta_max=cfg.theta_max, cfl=cfg.cfl)
+                    theta_max=cfg.theta_max, cfl=cfg.cfl,
+                    theta_basis=getattr(cfg, "theta_basis", 0))
         base.update(kw)
         return cls(**base)
 
@@ -127,8 +176,15 @@ class Grid:
         a_, b_ = self.bounds[:-1], self.bounds[1:]
         self.r = 0.5 * (a_ + b_)[:, None] + 0.5 * (b_ - a_)[:, None] * self.xr[None, :]
         self.r_scale = 2.0 / (b_ - a_)                       # dx/dr per element
-        self.theta = (p.theta_min + 0.5 * (p.theta_max - p.theta_min) * (1.0 + self.xt))
-        self.t_scale = 2.0 / (p.theta_max - p.theta_min)
+        self.fourier_theta = p.theta_basis == 1
+        if self.fourier_theta:
+            if abs(p.theta_min) > 1e-12 or abs(p.theta_max - np.pi) > 1e-12:
+                raise ValueError("the Fourier theta basis covers the whole of [0, pi]")
+            self.theta = sp.uniform_theta_nodes(p.n_theta)
+            self.t_scale = 1.0
+        else:
+            self.theta = (p.theta_min + 0.5 * (p.theta_max - p.theta_min) * (1.0 + self.xt))
+            self.t_scale = 2.0 / (p.theta_max - p.theta_min)
         self.phi = sp.fourier_nodes(p.n_phi)
         self.shape = (E, p.n_r, p.n_theta, p.n_phi)
         R = self.r[:, :, None, None]
@@ -144,7 +200,14 @@ class Grid:
                                                  scale=self.r_scale[e])
         return out
 
-    def d_t(self, u):
+    def d_t(self, u, parity=None):
+        """theta derivative; parity (scalar or broadcastable to u) is the sign of the
+        component under the double-Fourier extension and must be given for the Fourier
+        basis (ignored by the Chebyshev basis)."""
+        if self.fourier_theta:
+            if parity is None:
+                raise ValueError("the Fourier theta derivative needs the parity of the field")
+            return sp.fourier_theta_deriv(u, u.ndim - 2, u.ndim - 1, parity)
         return sp.cheb_deriv(u, self.xt, axis=u.ndim - 2, scale=self.t_scale)
 
     def d_p(self, u):
@@ -203,16 +266,18 @@ def _derivs(g: Grid, U):
     """First derivatives of the 21 differentiated BSSN fields, radial ones averaged at
     interfaces; second derivatives of the 11 second-order fields."""
     src = U[DERIV1]
+    par1 = _bc(THETA_PAR[DERIV1])
     dr = g.average_interfaces(g.d_r(src))
-    dt = g.d_t(src)
+    dt = g.d_t(src, par1)
     dp = g.d_p(src)
     d1 = np.stack([dr, dt, dp], axis=0)           # [3(d), 21, E, Nr, Nt, Np]
     idx2 = [DERIV1.index(v) for v in DERIV2]
+    par2 = _bc(THETA_PAR[DERIV2])
     a_r, a_t, a_p = dr[idx2], dt[idx2], dp[idx2]
     d_rr = g.average_interfaces(g.d_r(a_r))
-    d_rt = g.d_t(a_r)
+    d_rt = g.d_t(a_r, par2)
     d_rp = g.d_p(a_r)
-    d_tt = g.d_t(a_t)
+    d_tt = g.d_t(a_t, -par2)                      # d_theta u has the opposite parity
     d_tp = g.d_p(a_t)
     d_pp = g.d_p(a_p)
     d2 = np.empty((3, 3) + a_r.shape)
@@ -287,7 +352,7 @@ def rhs_from_prims(U, prim, g: Grid, p: Params, freeze_outer=True):
     Fr = np.moveaxis(F[..., 0, :], -1, 0)
     Ft = np.moveaxis(F[..., 1, :], -1, 0)
     Fp = np.moveaxis(F[..., 2, :], -1, 0)
-    div = g.d_r(Fr) + g.d_t(Ft) + g.d_p(Fp)
+    div = g.d_r(Fr) + g.d_t(Ft, _bc(FLUX_T_PAR)) + g.d_p(Fp)
     e4 = np.exp(4.0 * f["phi"])
     dgam = e4[..., None, None, None] * (D1["gt"] + 4.0 * np.einsum("...ij,...d->...dij",
                                                                       f["gt"], D1["phi"]))
@@ -301,8 +366,10 @@ def rhs_from_prims(U, prim, g: Grid, p: Params, freeze_outer=True):
     # ---- GLM divergence cleaning
     if p.glm:
         psi = U[I_PSI]
-        dpsi = np.stack([g.average_interfaces(g.d_r(psi)), g.d_t(psi), g.d_p(psi)], axis=-1)
-        divB = g.average_interfaces(g.d_r(U[I_B]) + g.d_t(U[I_B + 1]) + g.d_p(U[I_B + 2]))
+        dpsi = np.stack([g.average_interfaces(g.d_r(psi)), g.d_t(psi, THETA_PAR[I_PSI]),
+                         g.d_p(psi)], axis=-1)
+        divB = g.average_interfaces(g.d_r(U[I_B]) + g.d_t(U[I_B + 1], THETA_PAR[I_B + 1])
+                                    + g.d_p(U[I_B + 2]))
         ginv = ks.inv3(gam)
         rhs[I_PSI] = alpha * (-p.glm_ch ** 2 * divB / sqg - psi / p.glm_tau)
         rhs[I_B:I_B + 3] += np.moveaxis(-asg[..., None] * np.einsum("...ij,...j->...i", ginv, dpsi), -1, 0)
@@ -369,7 +436,12 @@ def apply_filter(U, g: Grid, p: Params):
                 out[sl, e] = sp.cheb_filter(out[sl, e], g.xr, axis=1, alpha=p.filt_alpha,
                                             p=p.filt_p)
         if m & (2 << grp):
-            out[sl] = sp.cheb_filter(out[sl], g.xt, axis=3, alpha=p.filt_alpha, p=p.filt_p)
+            if g.fourier_theta:
+                par = _bc(THETA_PAR[sl][:out[sl].shape[0]])
+                out[sl] = sp.fourier_theta_filter(out[sl], 3, 4, par, alpha=p.filt_alpha,
+                                                  p=p.filt_p, dealias23=bool(p.dealias23_theta))
+            else:
+                out[sl] = sp.cheb_filter(out[sl], g.xt, axis=3, alpha=p.filt_alpha, p=p.filt_p)
         if m & (4 << grp):
             out[sl] = sp.fourier_filter(out[sl], axis=4, alpha=p.filt_alpha, p=p.filt_p,
                                         dealias23=bool(p.dealias23_phi))
@@ -431,9 +503,14 @@ def cfl_dt(U, g: Grid, p: Params):
 
 # ---------------------------------------------------------------------- diagnostics
 def quadrature_weights(g: Grid):
-    """w_r J_e (Clenshaw-Curtis per element) x w_theta (Fejer) / t_scale x 2 pi / N_phi."""
+    """w_r J_e (Clenshaw-Curtis per element) x w_theta x 2 pi / N_phi, with w_theta the
+    Fejer weights / t_scale (Chebyshev theta) or the Fejer weights in x = -cos(theta)
+    divided by sin(theta) (Fourier theta; exact for sqrt(gamma)-weighted integrands)."""
     wr = sp.clenshaw_curtis_weights(g.p.n_r)[None, :] / g.r_scale[:, None]
-    wt = sp.fejer_weights(g.p.n_theta) / g.t_scale
+    if g.fourier_theta:
+        wt = sp.fourier_theta_weights(g.p.n_theta)
+    else:
+        wt = sp.fejer_weights(g.p.n_theta) / g.t_scale
     wp = 2.0 * np.pi / g.p.n_phi
     return wr[:, :, None, None] * wt[None, None, :, None] * wp
 
@@ -451,7 +528,7 @@ def diagnostics(U, g: Grid, p: Params):
     mass = np.sum(w * U[I_D])
     s = np.log(prim["p"] / prim["rho"] ** p.gamma_eos) / (p.gamma_eos - 1.0)
     ent = np.sum(w * prim["rho"] * s * sqg)
-    divB = g.d_r(U[I_B]) + g.d_t(U[I_B + 1]) + g.d_p(U[I_B + 2])
+    divB = g.d_r(U[I_B]) + g.d_t(U[I_B + 1], THETA_PAR[I_B + 1]) + g.d_p(U[I_B + 2])
     return np.array([mass, ent, np.max(np.abs(divB)), float(np.sum(~prim["ok"]))])
 
 
@@ -476,7 +553,8 @@ def initial_state(g: Grid, p: Params, prim):
     f = unpack_bssn(U)
     gam, sqg = metric_from_bssn(f)
     A = prim["A_phi"]
-    Bt = np.stack([g.d_t(A), -g.d_r(A), np.zeros_like(A)], axis=-1)
+    # A_phi is a covariant phi component: parity +1 under the theta extension
+    Bt = np.stack([g.d_t(A, 1.0), -g.d_r(A), np.zeros_like(A)], axis=-1)
     B_u = Bt / sqg[..., None]
     v_u = np.stack([prim["vr"], prim["vth"], prim["vph"]], axis=-1)
     eps = prim["p"] / ((p.gamma_eos - 1.0) * prim["rho"])

@@ -193,3 +193,51 @@ def fejer_weights(n: int) -> np.ndarray:
     k = np.arange(n)
     mom = np.where(k % 2 == 0, 2.0 / (1.0 - k.astype(float) ** 2 + (k % 2)), 0.0)
     return np.linalg.solve(V.T, mom)
+
+
+# ------------------------------------------------------------ Fourier theta (double Fourier)
+def uniform_theta_nodes(n: int) -> np.ndarray:
+    """theta_k = (k + 1/2) pi / n, k = 0..n-1: the paper's uniform polar grid on [0, pi]
+    ("Grid Discretization", "Pseudo-spectral theta derivative") shifted by half a spacing,
+    so that no node lies on the axis, where the spherical metric is singular (reading:
+    the printed k pi / (N_theta - 1) puts the first and last node on the poles)."""
+    return (np.arange(n) + 0.5) * np.pi / n
+
+
+def parity_extend(u: np.ndarray, axis_t: int, axis_p: int, parity) -> np.ndarray:
+    """Periodic line of length 2n over theta in [0, 2 pi) (double Fourier sphere).
+
+    The point (2 pi - theta, phi) of the extended torus is the point (theta, phi + pi)
+    of the sphere, reached across a pole; a component with parity s (s = -1 for each
+    theta index, and once more for a sqrt(gamma)-weighted density, which behaves like
+    sin(theta) on the axis) takes the value s u(theta, phi + pi) there.  The nodes
+    2 pi - theta_k are the extended nodes n + (n - 1 - k), so the second half is the
+    phi-shifted line in reversed order."""
+    n_p = u.shape[axis_p]
+    partner = np.roll(u, -(n_p // 2), axis=axis_p)          # value at phi + pi
+    mirrored = np.flip(partner, axis=axis_t) * parity
+    return np.concatenate([u, mirrored], axis=axis_t)
+
+
+def fourier_theta_deriv(u, axis_t: int, axis_p: int, parity, order: int = 1):
+    """d^order u / dtheta^order: the paper's Fourier derivative ((i k)^d on the DFT) of
+    the parity-extended line, read back on the n nodes of (0, pi)."""
+    n = u.shape[axis_t]
+    g = parity_extend(u, axis_t, axis_p, parity)
+    return np.take(fourier_deriv(g, axis=axis_t, order=order), np.arange(n), axis=axis_t)
+
+
+def fourier_theta_filter(u, axis_t: int, axis_p: int, parity, alpha=36.0, p=8.0, dealias23=True):
+    """Exponential filter (k_max = n, the Nyquist number of the 2n extended nodes) and the
+    2/3 rule (|k| > 2n/3 zeroed) on the parity-extended line, read back on (0, pi)."""
+    n = u.shape[axis_t]
+    g = parity_extend(u, axis_t, axis_p, parity)
+    return np.take(fourier_filter(g, axis=axis_t, alpha=alpha, p=p, dealias23=dealias23),
+                   np.arange(n), axis=axis_t)
+
+
+def fourier_theta_weights(n: int) -> np.ndarray:
+    """Quadrature of int_0^pi f dtheta on the uniform nodes for f = sin(theta) g(cos theta):
+    with x = -cos(theta) the nodes are the Chebyshev-Gauss points, and the integral is
+    int_{-1}^{1} f / sin(theta) dx, so w_k = (Fejer weight)_k / sin(theta_k)."""
+    return fejer_weights(n) / np.sin(uniform_theta_nodes(n))

@@ -44,6 +44,9 @@ class Config:
     # spherical coordinates, so the grid stops short of the poles
     theta_min: float = math.pi / 8
     theta_max: float = 7 * math.pi / 8
+    # 0: Chebyshev-Gauss nodes on [theta_min, theta_max]; 1: the paper's uniform theta grid
+    # with a Fourier derivative (whole sphere, theta_min = 0, theta_max = pi)
+    theta_basis: int = 0
     gamma_eos: float = 4.0 / 3.0
     profile: str = "powerlaw"  # "powerlaw" | "torus" | "bondi"
     rho0: float = 1e-2         # power-law amplitude
