@@ -232,7 +232,7 @@ def run_reference(args):
 # on the 393,216-node workload; the kernels recompute nothing, so this is their algorithmic
 # FP64 work.  The primitive-recovery count is taken inside the time stepping (Newton
 # started from the previous stage's primitives).
-FP64_FLOPS_PER_NODE = {"k_rhs<double>": 2610.0, "k_prep": 1094.0}
+FP64_FLOPS_PER_NODE = {"k_rhs<double>": 2618.0, "k_prep": 1031.0}
 # Nominal FP64 peak of GB300 from its unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop
 # x 2.07 GHz (a probe of dependent DFMA chains on all SMs measured 1.198 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -247,7 +247,7 @@ def _kernel_names(cfg, precision):
     names = {"prep": "k_prep", "iface_d1": "k_iface_avg", "iface_d2": "k_iface_avg",
              "rhs": "k_rhs<double>" if precision == 0 else "k_rhs<float>"}
     for d, dn in enumerate(("r", "theta", "phi")):
-        fx = 2 <= ns[d] <= 64
+        fx = 2 <= ns[d] <= 128 and (d != 2 or ns[d] % 2 == 0)
         fp64 = f"k_contract_fx<{d}>" if fx else f"k_deriv_eo<{d}>"
         for c in ("d1", "d2"):
             names[f"{c}_{dn}"] = fp64 if precision == 0 else f"k_contract_tc<{d}>"
@@ -304,10 +304,11 @@ def roofline(kt_full, P, precision, names):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of
-# the current kernel code inside the time stepping of the 393,216-node workload); absent =
-# not captured since the kernel last changed.  k_rhs<double> moves ~2.9 KB per node, about
-# twice its algorithmic bytes: register spills (it is FP64-bound, the bytes are not).
-TRAFFIC = {"k_rhs<double>": 1.16e9, "k_prep": 1.39e8}
+# the current kernel code inside the time stepping of the 393,216-node workload, mean of the
+# three stages of a step); absent = not captured since the kernel last changed.
+# k_rhs<double> moves ~2.7 KB per node, about twice its algorithmic bytes: register spills
+# (it is FP64-bound, the bytes are not).
+TRAFFIC = {"k_rhs<double>": 1.08e9, "k_prep": 1.38e8, "k_rhs<float>": 5.95e8}
 
 
 def run_gpu(args):
