@@ -51,17 +51,24 @@ enum { GRMHD_NV = 32, GRMHD_NPRIM = 7, GRMHD_NDIAG = 8 };
 
 /* Grid (Methods, "Grid Discretization").  Radial elements [r_e, r_{e+1}] with
  * r_e = r_min (r_max/r_min)^(e/E) (elem_map = 1) or equal widths (elem_map = 0); each
- * element carries n_r Chebyshev-Gauss-Lobatto nodes under an affine map.  theta uses
- * n_theta Chebyshev-Gauss nodes on [theta_min, theta_max] (no node on a pole), phi
- * n_phi uniform nodes 2 pi l / n_phi.  Limits: 1 <= n_elem, 4 <= n_r <= 64,
- * 4 <= n_theta <= 128, 4 <= n_phi <= 256 and even, 0 < r_min < r_max,
- * 0 <= theta_min < theta_max <= pi. */
+ * element carries n_r Chebyshev-Gauss-Lobatto nodes under an affine map.  theta_basis 0
+ * (default): theta uses n_theta Chebyshev-Gauss nodes on [theta_min, theta_max] (no node
+ * on a pole).  theta_basis 1: the paper's uniform theta grid with a Fourier derivative
+ * ("Pseudo-spectral theta derivative"): theta_k = (k + 1/2) pi / n_theta over the whole
+ * sphere (theta_min = 0 and theta_max = pi required; the half-node shift keeps nodes off
+ * the axis), every theta derivative and the theta filter acting on the double-Fourier
+ * extension of the line over [0, 2 pi), whose values at 2 pi - theta are s u(theta,
+ * phi + pi), s = -1 per theta index of a coordinate-basis component and -1 once more for
+ * the sqrt(gamma)-weighted Valencia variables.  phi uses n_phi uniform nodes
+ * 2 pi l / n_phi.  Limits: 1 <= n_elem, 4 <= n_r <= 64, 4 <= n_theta <= 128,
+ * 4 <= n_phi <= 256 and even, 0 < r_min < r_max, 0 <= theta_min < theta_max <= pi. */
 typedef struct {
     int n_elem;
     double r_min, r_max;
     int elem_map;
     int n_r, n_theta, n_phi;
     double theta_min, theta_max;
+    int theta_basis;
 } grmhd_grid;
 
 /* Physics: Kerr-Schild mass M and spin a (|a| < M), Gamma-law index (p = (Gamma-1) rho
@@ -82,12 +89,13 @@ typedef struct {
  * filter: bits 0/1/2 filter the Valencia variables in r/theta/phi, bits 3/4/5 the BSSN
  * variables in r/theta/phi (default 47: all but theta for BSSN); filt_alpha, filt_p are
  * the exponential-filter constants (paper: 36, 8); dealias23_phi applies the 2/3 rule
- * in phi.  cfl: Courant factor for dt <= 0.  c2p_maxit, c2p_tol: Newton iteration
+ * in phi, dealias23_theta in theta under theta_basis 1 (|k| > 2 n_theta / 3 of the
+ * extended line zeroed; default 1; the Chebyshev theta filter has no 2/3 rule).  cfl: Courant factor for dt <= 0.  c2p_maxit, c2p_tol: Newton iteration
  * limit and relative tolerance of the primitive recovery.  contraction: how the FP64
  * spectral contractions (all derivatives at precision 0, the filter at every precision)
  * run: 0 (default) on the BF16 tensor cores with exact base-256 digit slices of the
- * FP64 values (Ozaki splitting; error about 2^-53 of sum_j |D_ij| max_j |u_j|, directions
- * with more than 64 nodes fall back to 1), 1 on the FP64 units.  coupling: 0 (default) one
+ * FP64 values (Ozaki splitting; error about 2^-53 of sum_j |D_ij| max_j |u_j|; up to 128
+ * nodes per direction), 1 on the FP64 units.  coupling: 0 (default) one
  * unsplit right-hand side over all 32 variables per Runge-Kutta stage; 1 the paper's
  * coupled loop ("Coupled Main Loop"): per step the fluid is advanced by the selected
  * Runge-Kutta scheme on the frozen metric, then BSSN + gauge take one forward-Euler step
@@ -113,6 +121,7 @@ typedef struct {
     int coupling;
     int glm;
     double glm_ch, glm_tau;
+    int dealias23_theta;
 } grmhd_opts;
 
 typedef struct grmhd_ctx grmhd_ctx;
@@ -245,6 +254,14 @@ const char* grmhd_batch_last_error(const grmhd_batch* b);
  * `nfields` canonical fields (nfields * num_points doubles) with the library's
  * operators (radial: per element, one-sided at element ends).  Device pointers. */
 int grmhd_debug_deriv(grmhd_ctx* ctx, const double* in, double* out, int nfields, int dir);
+
+/* Test hook: the theta derivative (filter = 0) or the theta filter (filter = 1) of
+ * `nfields` canonical fields (device pointers, nfields * num_points doubles each), field f
+ * taken with parity[f] = +1 or -1 (host array) under theta_basis 1 (ignored under the
+ * Chebyshev basis).  GRMHD_EINVAL for other parities or more fields than the context's
+ * folding buffers hold (at least 24). */
+int grmhd_debug_theta(grmhd_ctx* ctx, const double* in, double* out, int nfields, const int* parity,
+                      int filter);
 
 /* Allocation-free CFL time step (the paper has no counterpart: this is a service of the
  * library).  Some callers cannot call cudaMalloc: hosts that own every byte of device

@@ -21,7 +21,8 @@ NV, NPRIM, NDIAG = 32, 7, 8
 class Grid(C.Structure):
     _fields_ = [("n_elem", C.c_int), ("r_min", C.c_double), ("r_max", C.c_double),
                 ("elem_map", C.c_int), ("n_r", C.c_int), ("n_theta", C.c_int),
-                ("n_phi", C.c_int), ("theta_min", C.c_double), ("theta_max", C.c_double)]
+                ("n_phi", C.c_int), ("theta_min", C.c_double), ("theta_max", C.c_double),
+                ("theta_basis", C.c_int)]
 
 
 class Physics(C.Structure):
@@ -35,7 +36,7 @@ class Opts(C.Structure):
                 ("filter", C.c_int), ("filt_alpha", C.c_double), ("filt_p", C.c_double),
                 ("dealias23_phi", C.c_int), ("c2p_maxit", C.c_int), ("c2p_tol", C.c_double),
                 ("contraction", C.c_int), ("coupling", C.c_int), ("glm", C.c_int),
-                ("glm_ch", C.c_double), ("glm_tau", C.c_double)]
+                ("glm_ch", C.c_double), ("glm_tau", C.c_double), ("dealias23_theta", C.c_int)]
 
 
 _P = C.c_void_p
@@ -74,6 +75,7 @@ SIGNATURES = {
     "grmhd_batch_destroy": (C.c_int, [_P]),
     "grmhd_batch_last_error": (C.c_char_p, [_P]),
     "grmhd_debug_deriv": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
+    "grmhd_debug_theta": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "grmhd_cfl_dt_noalloc": (C.c_int, [_P, C.c_longlong, C.c_double, C.c_double, _P, _P]),
     "grmhd_strerror": (C.c_char_p, [C.c_int]),
     "grmhd_last_error": (C.c_char_p, [_P]),
@@ -216,6 +218,13 @@ class Context:
     def debug_deriv(self, src, dst, nfields: int, direction: int):
         self._chk(self.lib.grmhd_debug_deriv(self.h, _ptr(src), _ptr(dst), nfields, direction))
 
+    def debug_theta(self, src, dst, parities, filter: bool = False):
+        """theta derivative (or theta filter) of len(parities) fields, field f with the
+        extension parity parities[f] (Fourier theta basis)"""
+        n = len(parities)
+        arr = (C.c_int * n)(*[int(x) for x in parities])
+        self._chk(self.lib.grmhd_debug_theta(self.h, _ptr(src), _ptr(dst), n, arr, int(filter)))
+
 
 class Batch:
     """Many independent instances advanced together (grmhd_batch_*)."""
@@ -294,6 +303,7 @@ def make_structs(cfg, **opt_overrides):
     g.n_elem, g.r_min, g.r_max, g.elem_map = cfg.n_elem, cfg.r_min, cfg.r_max, cfg.elem_map
     g.n_r, g.n_theta, g.n_phi = cfg.n_r, cfg.n_theta, cfg.n_phi
     g.theta_min, g.theta_max = cfg.theta_min, cfg.theta_max
+    g.theta_basis = getattr(cfg, "theta_basis", 0)
     p.M, p.a, p.gamma_eos = cfg.M, cfg.a, cfg.gamma_eos
     o.cfl = cfg.cfl
     for k, v in opt_overrides.items():

@@ -78,6 +78,26 @@ struct grmhd_ctx {
     int job_second_n[3];
     int job_filter[3][3][2]; // [buffer][dir][group] offset (8 or 24 jobs)
     int job_dbg;
+    // Fourier theta basis (grid.theta_basis = 1): theta contractions fold the phi pairs
+    // (l, l + N_phi/2) into half sums / differences, contract each half with the even or
+    // odd extension operator, and unfold (kernels_deriv.cu)
+    int ft;                  // 1: Fourier theta basis
+    Dims dh;                 // one folded half: N_phi / 2 lines per (element, r, theta) row
+    int nfold;               // fields the folding buffers hold
+    double* Y;               // folded inputs, nfold x P values (double, or float)
+    double* Z;               // folded contraction results
+    double* Dt2[2];          // dense even / odd extension operators: derivative
+    double* Ft2[2];          //   and filter
+    double* Dts[2];          // reflection-split copies (nullptr: dense only)
+    double* Fts[2];
+    uint8_t* fx_dt[2];       // digit-slice images (nullptr: FP64 units)
+    uint8_t* fx_ft[2];
+    uint8_t* tc_t[2];        // mixed-precision images of the derivative operators
+    FoldJob* fjobs;          // fold / unfold job lists (offsets below)
+    int fj_first[3], fj_first_u[3], fj_second, fj_second_u, fj_filter[3][2], fj_filter_u[3][2];
+    int fj_dbg, fj_dbg_u;
+    int job_fy[2];           // FP64 contraction jobs over the folded halves (even, odd)
+    int tc_fy[2][2];         // [source FP64 / FP32][even, odd] tensor-core jobs over the halves
     // host copies
     std::vector<double> r_nodes, th_nodes, ph_nodes, rscale_h;
     // instances of the group (concatenated along r)
@@ -124,11 +144,32 @@ static int set_err(grmhd_ctx* c, int code, const char* fmt, ...) {
             return set_err(c, GRMHD_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+// Sign of each canonical variable under the double-Fourier extension of the Fourier theta
+// basis, i.e. under the chart change (theta, phi) -> (-theta, phi + pi) that reaches a point
+// across the pole: -1 per theta index of a coordinate-basis component, and -1 once more
+// for the sqrt(gamma)-weighted Valencia variables (sqrt(gamma) changes sign with
+// sin(theta), so the odd extension is the smooth one).
+static const int kThetaParity[NV_MAX] = {
+    1, -1, 1, 1, -1, 1,   // gammatilde_{rr, r th, r ph, th th, th ph, ph ph}
+    1,                    // conformal factor phi
+    1, -1, 1, 1, -1, 1,   // Atilde_ij
+    1,                    // K
+    1, -1, 1,             // Gammatilde^i
+    1,                    // alpha
+    1, -1, 1,             // beta^i
+    1, -1, 1,             // B^i (Gamma-driver)
+    -1,                   // sqrt(gamma) D
+    -1, 1, -1,            // sqrt(gamma) S_i
+    -1,                   // sqrt(gamma) tau
+    -1, 1, -1,            // sqrt(gamma) B^i
+    1};                   // psi (GLM)
+
 extern "C" int grmhd_defaults(grmhd_grid* g, grmhd_physics* ph, grmhd_opts* o) {
     if (g) {
         g->n_elem = 2; g->r_min = 1.8; g->r_max = 20.0; g->elem_map = 1;
         g->n_r = 12; g->n_theta = 12; g->n_phi = 16;
         g->theta_min = M_PI / 8; g->theta_max = 7 * M_PI / 8;
+        g->theta_basis = 0;
     }
     if (ph) { ph->M = 1.0; ph->a = 0.5; ph->gamma_eos = 4.0 / 3.0; ph->rho_atm = 1e-12; ph->eps_atm = 1e-10; }
     if (o) {
@@ -138,6 +179,7 @@ extern "C" int grmhd_defaults(grmhd_grid* g, grmhd_physics* ph, grmhd_opts* o) {
         o->contraction = 0;
         o->coupling = 0;
         o->glm = 0; o->glm_ch = 1.0; o->glm_tau = 1.0;
+        o->dealias23_theta = 1;
     }
     return GRMHD_OK;
 }
@@ -153,6 +195,10 @@ static int validate(const grmhd_grid* g, const grmhd_physics* ph, const grmhd_op
         strcpy(msg, "need 0 <= theta_min < theta_max <= pi"); return GRMHD_EINVAL;
     }
     if (g->elem_map != 0 && g->elem_map != 1) { strcpy(msg, "elem_map must be 0 or 1"); return GRMHD_EINVAL; }
+    if (g->theta_basis != 0 && g->theta_basis != 1) { strcpy(msg, "theta_basis must be 0 or 1"); return GRMHD_EINVAL; }
+    if (g->theta_basis == 1 && (g->theta_min != 0.0 || std::fabs(g->theta_max - M_PI) > 1e-12)) {
+        strcpy(msg, "the Fourier theta basis covers the sphere: theta_min = 0, theta_max = pi"); return GRMHD_EINVAL;
+    }
     if (!(ph->M > 0.0) || !(std::fabs(ph->a) < ph->M)) { strcpy(msg, "need M > 0 and |a| < M"); return GRMHD_EINVAL; }
     if (!(ph->gamma_eos > 1.0)) { strcpy(msg, "gamma_eos must exceed 1"); return GRMHD_EINVAL; }
     if (!(ph->rho_atm > 0.0) || !(ph->eps_atm >= 0.0)) { strcpy(msg, "bad floors"); return GRMHD_EINVAL; }
@@ -169,6 +215,7 @@ static int validate(const grmhd_grid* g, const grmhd_physics* ph, const grmhd_op
     if (o->coupling != 0 && o->coupling != 1) { strcpy(msg, "coupling must be 0 or 1"); return GRMHD_EINVAL; }
     if (o->glm != 0 && o->glm != 1) { strcpy(msg, "glm must be 0 or 1"); return GRMHD_EINVAL; }
     if (o->glm && (!(o->glm_ch >= 0.0) || !(o->glm_tau > 0.0))) { strcpy(msg, "need glm_ch >= 0 and glm_tau > 0"); return GRMHD_EINVAL; }
+    if (o->dealias23_theta != 0 && o->dealias23_theta != 1) { strcpy(msg, "dealias23_theta must be 0 or 1"); return GRMHD_EINVAL; }
     return GRMHD_OK;
 }
 
@@ -197,6 +244,16 @@ static void free_ctx(grmhd_ctx* c) {
     }
     if (c->tcjobs) cudaFree(c->tcjobs);
     if (c->tc_err) cudaFree(c->tc_err);
+    double** fbufs[] = {&c->Y, &c->Z, &c->Dt2[0], &c->Dt2[1], &c->Ft2[0], &c->Ft2[1], &c->Dts[0], &c->Dts[1],
+                        &c->Fts[0], &c->Fts[1]};
+    for (double** b : fbufs)
+        if (*b) cudaFree(*b);
+    for (int k = 0; k < 2; k++) {
+        if (c->fx_dt[k]) cudaFree(c->fx_dt[k]);
+        if (c->fx_ft[k]) cudaFree(c->fx_ft[k]);
+        if (c->tc_t[k]) cudaFree(c->tc_t[k]);
+    }
+    if (c->fjobs) cudaFree(c->fjobs);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -218,7 +275,7 @@ static cudaError_t upload(double* dst, const std::vector<double>& v, cudaStream_
 static bool same_group(const grmhd_grid& g0, const grmhd_physics& p0, const grmhd_grid& g,
                        const grmhd_physics& p) {
     return g.n_r == g0.n_r && g.n_theta == g0.n_theta && g.n_phi == g0.n_phi &&
-           g.theta_min == g0.theta_min && g.theta_max == g0.theta_max &&
+           g.theta_min == g0.theta_min && g.theta_max == g0.theta_max && g.theta_basis == g0.theta_basis &&
            p.gamma_eos == p0.gamma_eos && p.rho_atm == p0.rho_atm && p.eps_atm == p0.eps_atm;
 }
 
@@ -301,9 +358,11 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         }
     }
     double tscale = 2.0 / (grid->theta_max - grid->theta_min);
+    c->ft = grid->theta_basis == 1;
     c->th_nodes.resize(Nt);
     for (int k = 0; k < Nt; k++)
-        c->th_nodes[k] = grid->theta_min + 0.5 * (grid->theta_max - grid->theta_min) * (1.0 + xt[k]);
+        c->th_nodes[k] = c->ft ? (k + 0.5) * M_PI / Nt
+                               : grid->theta_min + 0.5 * (grid->theta_max - grid->theta_min) * (1.0 + xt[k]);
     c->ph_nodes.resize(Np);
     for (int l = 0; l < Np; l++) c->ph_nodes[l] = 2.0 * M_PI * l / Np;
 
@@ -313,7 +372,12 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
     std::vector<double> Ft = cheb_filter_matrix(Nt, false, opts->filt_alpha, opts->filt_p);
     std::vector<double> Fp = fourier_filter_row(Np, opts->filt_alpha, opts->filt_p, opts->dealias23_phi != 0);
     // quadrature weights and the CFL spacing
+    // theta weights: Fejer weights of the Chebyshev-Gauss nodes, divided by the map's
+    // d theta / dx (Chebyshev basis) or, Fourier basis, by sin(theta) (x = -cos(theta)
+    // carries the uniform nodes into the Chebyshev-Gauss points; exact for
+    // sqrt(gamma)-weighted integrands)
     std::vector<double> wt = quad_weights(Nt, false);
+    for (int k = 0; k < Nt; k++) wt[k] = c->ft ? wt[k] / std::sin(c->th_nodes[k]) : wt[k] / tscale;
     std::vector<double> wq((size_t)P);
     std::vector<double> hmin(ninst, 1e300);
     for (int e = 0; e < E; e++)
@@ -328,7 +392,7 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
                 hmin[c->elem_inst[e]] = std::fmin(hmin[c->elem_inst[e]], h);
                 for (int l = 0; l < Np; l++)
                     wq[(((size_t)e * Nr + i) * Nt + k) * Np + l] =
-                        wcgl[i] / c->rscale_h[e] * wt[k] / tscale * (2.0 * M_PI / Np);
+                        wcgl[i] / c->rscale_h[e] * wt[k] * (2.0 * M_PI / Np);
             }
         }
 
@@ -351,6 +415,10 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
     AL(c->r_scale, E); AL(c->wq, P); AL(c->hmin, ninst); AL(c->dt, ninst); AL(c->diag, 8);
     AL(c->nfail, 1); AL(c->lam_bits, ninst); AL(c->nan_flag, 1); AL(c->tc_err, 1);
     AL(c->iface_dev, E); AL(c->elem_inst_dev, E);
+    // folding buffers of the Fourier theta basis: the largest theta job list (first
+    // derivatives: 21 fields + 8 fluxes, + psi and B^theta with GLM)
+    c->nfold = N_D1 + 8 + 2 * glm;
+    if (c->ft) { AL(c->Y, (long long)c->nfold * P); AL(c->Z, (long long)c->nfold * P); }
 #undef AL
     if (ce != cudaSuccess) {
         free_ctx(c);
@@ -407,6 +475,14 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
             }
     c->job_dbg = (int)jobs.size();
     for (int k = 0; k < 64; k++) add(nullptr, nullptr, 0);
+    // Fourier theta: contractions of the folded halves, field i at Y / Z + i P (the half
+    // for the even operator first, P / 2 values each)
+    for (int h = 0; h < 2; h++) {
+        c->job_fy[h] = (int)jobs.size();
+        if (c->ft)
+            for (int i = 0; i < c->nfold; i++)
+                add(c->Y + (long long)i * P + h * (P / 2), c->Z + (long long)i * P + h * (P / 2), 0);
+    }
     if (dalloc(&c->jobs, jobs.size()) != cudaSuccess) { free_ctx(c); return GRMHD_ENOMEM; }
     cudaStream_t s = c->stream;
     if (cudaMemcpyAsync(c->jobs, jobs.data(), jobs.size() * sizeof(DerivJob), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -441,6 +517,50 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         }
         if (cudaStreamSynchronize(s) != cudaSuccess) { free_ctx(c); return GRMHD_ECUDA; }
     }
+    // Fourier theta: even / odd extension operators (dense, reflection-split, digit slices)
+    std::vector<double> ext_d[2], ext_f[2];
+    if (c->ft) {
+        c->dh = c->d;
+        c->dh.Np = Np / 2;
+        c->dh.NtNp = (long long)Nt * (Np / 2);
+        c->dh.elem = c->dh.NtNp * Nr;
+        c->dh.P = P / 2;
+        theta_extension_ops(fourier_D_row(2 * Nt), Nt, &ext_d[0], &ext_d[1]);
+        theta_extension_ops(fourier_filter_row(2 * Nt, opts->filt_alpha, opts->filt_p, opts->dealias23_theta != 0), Nt,
+                            &ext_f[0], &ext_f[1]);
+        // the digit-slice kernel stages lines with 16-byte bulk copies: the folded halves
+        // need an even number of lines per row
+        const bool fx_ok = opts->contraction == 0 && fx_supported(1, Nt) && (Np / 2) % 2 == 0;
+        int np_ = 0, kp_ = 0, kc_ = 0;
+        fx_geometry(Nt, &np_, &kp_, &kc_);
+        for (int h = 0; h < 2; h++) {
+            if (dalloc(&c->Dt2[h], (size_t)Nt * Nt) != cudaSuccess || dalloc(&c->Ft2[h], (size_t)Nt * Nt) != cudaSuccess ||
+                upload(c->Dt2[h], ext_d[h], s) != cudaSuccess || upload(c->Ft2[h], ext_f[h], s) != cudaSuccess) {
+                free_ctx(c);
+                return GRMHD_ENOMEM;
+            }
+            if (eo_supported(1, Nt)) {
+                std::vector<double> sd = split_operator(ext_d[h], Nt, 0), sf = split_operator(ext_f[h], Nt, 0);
+                if (dalloc(&c->Dts[h], sd.size()) != cudaSuccess || dalloc(&c->Fts[h], sf.size()) != cudaSuccess ||
+                    upload(c->Dts[h], sd, s) != cudaSuccess || upload(c->Fts[h], sf, s) != cudaSuccess) {
+                    free_ctx(c);
+                    return GRMHD_ENOMEM;
+                }
+            }
+            if (fx_ok) {
+                std::vector<uint8_t> id = fx_operator_image(ext_d[h], Nt, 1.0, np_, kp_, kc_);
+                std::vector<uint8_t> iff = fx_operator_image(ext_f[h], Nt, 1.0, np_, kp_, kc_);
+                if (cudaMalloc(&c->fx_dt[h], id.size()) != cudaSuccess || cudaMalloc(&c->fx_ft[h], iff.size()) != cudaSuccess ||
+                    cudaMemcpyAsync(c->fx_dt[h], id.data(), id.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                    cudaMemcpyAsync(c->fx_ft[h], iff.data(), iff.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess) {
+                    free_ctx(c);
+                    return GRMHD_ENOMEM;
+                }
+            }
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) { free_ctx(c); return GRMHD_ECUDA; }
+    }
     if (kernels_init() != cudaSuccess) { free_ctx(c); return GRMHD_ECUDA; }
     if (cudaMemsetAsync(c->tc_err, 0, sizeof(int), s) != cudaSuccess) { free_ctx(c); return GRMHD_ECUDA; }
     // digit-slice images of the FP64 operators (every direction with at most 64 nodes)
@@ -449,7 +569,7 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         std::vector<double> dense_d[3] = {Dr, Dt, circulant(Dp)};
         std::vector<double> dense_f[3] = {Fr, Ft, circulant(Fp)};
         for (int k = 0; k < 3; k++) {
-            if (!fx_supported(k, Ns[k])) continue;
+            if (!fx_supported(k, Ns[k]) || (k == 1 && c->ft)) continue;
             int np_, kp_, kc_;
             fx_geometry(Ns[k], &np_, &kp_, &kc_);
             std::vector<uint8_t> img_f = fx_operator_image(dense_f[k], Ns[k], 1.0, np_, kp_, kc_);
@@ -474,10 +594,22 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         }
     }
     // tensor-core operator images and job lists (mixed-precision modes)
+    std::vector<TcJob> tj;
+    auto addt = [&](const void* src, float* dst, int acc) { TcJob j; j.src = src; j.dst = dst; j.accumulate = acc; j.pad = 0; tj.push_back(j); };
     if (opts->precision > 0) {
         const int tf32 = opts->precision == 2;
         const int Ns[3] = {Nr, Nt, Np};
         std::vector<double> dense_d[3] = {Dr, Dt, circulant(Dp)};
+        if (c->ft)
+            for (int h = 0; h < 2; h++) {
+                std::vector<uint8_t> img = tc_operator_image(ext_d[h], Nt, tf32);
+                if (cudaMalloc(&c->tc_t[h], img.size()) != cudaSuccess ||
+                    cudaMemcpyAsync(c->tc_t[h], img.data(), img.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess) {
+                    free_ctx(c);
+                    return GRMHD_ENOMEM;
+                }
+            }
         for (int k = 0; k < 3; k++) {
             std::vector<uint8_t> img = tc_operator_image(dense_d[k], Ns[k], tf32);
             if (cudaMalloc(&c->tc_img[k], img.size()) != cudaSuccess ||
@@ -489,8 +621,6 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         float* d1f = reinterpret_cast<float*>(c->d1);
         float* d2f = reinterpret_cast<float*>(c->d2);
         float* dFf = reinterpret_cast<float*>(c->divF);
-        std::vector<TcJob> tj;
-        auto addt = [&](const void* src, float* dst, int acc) { TcJob j; j.src = src; j.dst = dst; j.accumulate = acc; j.pad = 0; tj.push_back(j); };
         for (int b = 0; b < 3; b++)
             for (int dir = 0; dir < 3; dir++) {
                 c->tc_first[b][dir] = (int)tj.size();
@@ -512,9 +642,95 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         c->tc_second[2] = (int)tj.size();
         for (int q = 0; q < N_D2; q++)
             addt(d1f + ((long long)vars2[q] * 3 + 2) * P, d2f + ((long long)q * 6 + 5) * P, 0);
+        // Fourier theta: the folded halves, FP64 (first derivatives) or FP32 (second) inputs,
+        // FP32 results
+        float* Yf = reinterpret_cast<float*>(c->Y);
+        float* Zf = reinterpret_cast<float*>(c->Z);
+        for (int src32 = 0; src32 < 2; src32++)
+            for (int h = 0; h < 2; h++) {
+                c->tc_fy[src32][h] = (int)tj.size();
+                if (c->ft)
+                    for (int i = 0; i < c->nfold; i++) {
+                        const long long o = (long long)i * P + h * (P / 2);
+                        addt(src32 ? (const void*)(Yf + o) : (const void*)(c->Y + o), Zf + o, 0);
+                    }
+            }
         if (cudaMalloc(&c->tcjobs, tj.size() * sizeof(TcJob)) != cudaSuccess ||
             cudaMemcpyAsync(c->tcjobs, tj.data(), tj.size() * sizeof(TcJob), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(c->tc_err, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+            free_ctx(c);
+            return GRMHD_ENOMEM;
+        }
+    }
+    // Fourier theta: fold / unfold job lists of every theta contraction of the pipeline
+    if (c->ft) {
+        std::vector<FoldJob> fj;
+        auto addf = [&](const void* src, void* dst, int par, int acc) {
+            FoldJob j; j.src = src; j.dst = dst; j.parity = par; j.accumulate = acc; fj.push_back(j);
+        };
+        const int mixed = opts->precision > 0;
+        float* Yf = reinterpret_cast<float*>(c->Y);
+        float* Zf = reinterpret_cast<float*>(c->Z);
+        // parity of the i-th job of a first-derivative list: 21 fields (+ psi), the theta
+        // fluxes of the 8 Valencia variables (one more theta index), sqrt(gamma) B^theta
+        std::vector<int> par1;
+        for (int f = 0; f < N_D1; f++) par1.push_back(kThetaParity[f]);
+        if (glm) par1.push_back(kThetaParity[V_PSI]);
+        for (int v = 0; v < 8; v++) par1.push_back(-kThetaParity[V_D + v]);
+        if (glm) par1.push_back(kThetaParity[V_B + 1]);
+        const int n1 = c->job_first_n;
+        for (int b = 0; b < 3; b++) {
+            const DerivJob* jl = &jobs[c->job_first[b][1]];
+            c->fj_first[b] = (int)fj.size();
+            for (int i = 0; i < n1; i++) addf(jl[i].src, c->Y + (long long)i * P, par1[i], 0);
+            c->fj_first_u[b] = (int)fj.size();
+            for (int i = 0; i < n1; i++) {
+                if (mixed) {
+                    const TcJob& t = tj[c->tc_first[b][1] + i];
+                    addf(Zf + (long long)i * P, t.dst, par1[i], t.accumulate);
+                } else {
+                    addf(c->Z + (long long)i * P, jl[i].dst, par1[i], jl[i].accumulate);
+                }
+            }
+        }
+        // second derivatives: theta-theta = D_theta(d_theta u) (d_theta u has parity -s),
+        // theta-phi = D_theta(d_phi u) (parity s); d2 slots 3 and 4 of each field
+        const int v2[N_D2] = {0, 1, 2, 3, 4, 5, 6, 17, 18, 19, 20};
+        c->fj_second = (int)fj.size();
+        for (int q = 0; q < N_D2; q++)
+            for (int x = 0; x < 2; x++) {
+                const long long i = 2 * q + x, so = ((long long)v2[q] * 3 + 1 + x) * P;
+                const int par = x == 0 ? -kThetaParity[v2[q]] : kThetaParity[v2[q]];
+                if (mixed) addf(reinterpret_cast<const float*>(c->d1) + so, Yf + i * P, par, 0);
+                else addf(c->d1 + so, c->Y + i * P, par, 0);
+            }
+        c->fj_second_u = (int)fj.size();
+        for (int q = 0; q < N_D2; q++)
+            for (int x = 0; x < 2; x++) {
+                const long long i = 2 * q + x, dof = ((long long)q * 6 + 3 + x) * P;
+                const int par = x == 0 ? -kThetaParity[v2[q]] : kThetaParity[v2[q]];
+                if (mixed) addf(Zf + i * P, reinterpret_cast<float*>(c->d2) + dof, par, 0);
+                else addf(c->Z + i * P, c->d2 + dof, par, 0);
+            }
+        // filter, theta link of the chain scratch -> U[b] (FP64 at every precision)
+        for (int b = 0; b < 3; b++)
+            for (int grp = 0; grp < 2; grp++) {
+                const int v0 = grp == 0 ? V_D : 0, ng = grp == 0 ? 8 + glm : N_BSSN;
+                c->fj_filter[b][grp] = (int)fj.size();
+                for (int i = 0; i < ng; i++)
+                    addf(c->scratch + (long long)(v0 + i) * P, c->Y + (long long)i * P, kThetaParity[v0 + i], 0);
+                c->fj_filter_u[b][grp] = (int)fj.size();
+                for (int i = 0; i < ng; i++)
+                    addf(c->Z + (long long)i * P, c->U[b] + (long long)(v0 + i) * P, kThetaParity[v0 + i], 0);
+            }
+        // test hook and diagnostics entries, filled per call
+        c->fj_dbg = (int)fj.size();
+        for (int i = 0; i < c->nfold; i++) addf(nullptr, nullptr, 1, 0);
+        c->fj_dbg_u = (int)fj.size();
+        for (int i = 0; i < c->nfold; i++) addf(nullptr, nullptr, 1, 0);
+        if (cudaMalloc(&c->fjobs, fj.size() * sizeof(FoldJob)) != cudaSuccess ||
+            cudaMemcpyAsync(c->fjobs, fj.data(), fj.size() * sizeof(FoldJob), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
             free_ctx(c);
             return GRMHD_ENOMEM;
         }
@@ -564,6 +780,7 @@ extern "C" int grmhd_coords(const grmhd_ctx* c, double* r, double* th, double* p
 // kernel.  filter = 1 uses the modal filter operator (unscaled), 0 the derivative
 // (radial: scaled per element).
 static cudaError_t contract(grmhd_ctx* c, int dir, int filter, const DerivJob* jobs, int njobs) {
+    if (dir == 1 && c->ft) return cudaErrorInvalidValue;   // theta_fourier below
     const uint8_t* fx = filter ? c->fx_f[dir] : c->fx_d[dir];
     if (fx) return launch_contract_fx(dir, c->d, jobs, njobs, fx, (dir == 0 && !filter) ? c->fx_estride : 0,
                                       c->tc_err, c->stream);
@@ -575,12 +792,40 @@ static cudaError_t contract(grmhd_ctx* c, int dir, int filter, const DerivJob* j
     return launch_deriv(dir, c->d, jobs, njobs, dense, rs, c->stream);
 }
 
+// Theta contraction of n fields under the Fourier basis: fold the phi pairs, contract
+// the two halves along theta with the even and the odd extension operator, unfold into
+// the destinations (4 launches).  stage < 0: FP64 values (digit-slice, reflection-split or
+// dense kernel); 0 / 1: the mixed-precision tensor-core kernel on FP64 / FP32 inputs.
+static cudaError_t theta_fourier(grmhd_ctx* c, int filter, int stage, int fold_off, int unfold_off, int n) {
+    cudaError_t e = launch_theta_fold(c->d, c->fjobs + fold_off, n, stage == 1, c->stream);
+    if (e != cudaSuccess) return e;
+    for (int h = 0; h < 2; h++) {
+        if (stage >= 0) {
+            e = launch_contract_tc(1, stage, c->dh, c->tcjobs + c->tc_fy[stage][h], n, c->tc_t[h],
+                                   c->opts.precision == 2, c->r_scale, c->tc_err, c->stream);
+        } else {
+            const uint8_t* fx = filter ? c->fx_ft[h] : c->fx_dt[h];
+            const double* split = filter ? c->Fts[h] : c->Dts[h];
+            const DerivJob* jb = c->jobs + c->job_fy[h];
+            if (fx) e = launch_contract_fx(1, c->dh, jb, n, fx, 0, c->tc_err, c->stream);
+            else if (split) e = launch_deriv_eo(1, c->dh, jb, n, split, filter ? 1 : -1, nullptr, c->stream);
+            else e = launch_deriv(1, c->dh, jb, n, filter ? c->Ft2[h] : c->Dt2[h], nullptr, c->stream);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    c->launches_tmp += 3;   // the caller counts the fourth
+    return launch_theta_unfold(c->d, c->fjobs + unfold_off, n, stage >= 0, c->stream);
+}
+
 static int enqueue_first_derivs(grmhd_ctx* c, int b) {
     if (c->opts.precision > 0) {
         const int tf32 = c->opts.precision == 2;
         for (int dir = 0; dir < 3; dir++) {
-            CK(launch_contract_tc(dir, 0, c->d, c->tcjobs + c->tc_first[b][dir], c->job_first_n, c->tc_img[dir], tf32,
-                                  c->r_scale, c->tc_err, c->stream));
+            if (dir == 1 && c->ft)
+                CK(theta_fourier(c, 0, 0, c->fj_first[b], c->fj_first_u[b], c->job_first_n));
+            else
+                CK(launch_contract_tc(dir, 0, c->d, c->tcjobs + c->tc_first[b][dir], c->job_first_n, c->tc_img[dir], tf32,
+                                      c->r_scale, c->tc_err, c->stream));
             c->launches_tmp++;
         }
         CK(launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d1), 3 * c->d.P, N_D1 + c->pp.glm, c->stream));
@@ -592,7 +837,8 @@ static int enqueue_first_derivs(grmhd_ctx* c, int b) {
         return GRMHD_OK;
     }
     for (int dir = 0; dir < 3; dir++) {
-        CK(contract(c, dir, 0, c->jobs + c->job_first[b][dir], c->job_first_n));
+        if (dir == 1 && c->ft) CK(theta_fourier(c, 0, -1, c->fj_first[b], c->fj_first_u[b], c->job_first_n));
+        else CK(contract(c, dir, 0, c->jobs + c->job_first[b][dir], c->job_first_n));
         c->launches_tmp++;
     }
     CK(launch_iface_avg(c->d, c->d1, 3 * c->d.P, N_D1 + c->pp.glm, c->stream));
@@ -609,8 +855,11 @@ static int enqueue_second_derivs(grmhd_ctx* c) {
         const int tf32 = c->opts.precision == 2;
         const int n[3] = {3 * N_D2, 2 * N_D2, N_D2};
         for (int dir = 0; dir < 3; dir++) {
-            CK(launch_contract_tc(dir, 1, c->d, c->tcjobs + c->tc_second[dir], n[dir], c->tc_img[dir], tf32,
-                                  c->r_scale, c->tc_err, c->stream));
+            if (dir == 1 && c->ft)
+                CK(theta_fourier(c, 0, 1, c->fj_second, c->fj_second_u, n[dir]));
+            else
+                CK(launch_contract_tc(dir, 1, c->d, c->tcjobs + c->tc_second[dir], n[dir], c->tc_img[dir], tf32,
+                                      c->r_scale, c->tc_err, c->stream));
             c->launches_tmp++;
         }
         for (int x = 0; x < 3; x++)
@@ -619,7 +868,8 @@ static int enqueue_second_derivs(grmhd_ctx* c) {
         return GRMHD_OK;
     }
     for (int dir = 0; dir < 3; dir++) {
-        CK(contract(c, dir, 0, c->jobs + c->job_second[dir], c->job_second_n[dir]));
+        if (dir == 1 && c->ft) CK(theta_fourier(c, 0, -1, c->fj_second, c->fj_second_u, c->job_second_n[dir]));
+        else CK(contract(c, dir, 0, c->jobs + c->job_second[dir], c->job_second_n[dir]));
         c->launches_tmp++;
     }
     for (int x = 0; x < 3; x++)
@@ -657,7 +907,8 @@ static int enqueue_filter(grmhd_ctx* c, int b) {
             // the Valencia group carries psi (variable 32, right after them) with GLM
             int v0 = grp == 0 ? V_D : 0, ng = grp == 0 ? 8 + c->pp.glm : N_BSSN;
             if (m & bit) {
-                CK(contract(c, dir, 1, c->jobs + c->job_filter[b][dir][grp], ng));
+                if (dir == 1 && c->ft) CK(theta_fourier(c, 1, -1, c->fj_filter[b][grp], c->fj_filter_u[b][grp], ng));
+                else CK(contract(c, dir, 1, c->jobs + c->job_filter[b][dir][grp], ng));
                 c->launches_tmp++;
             } else if (src != dst) {
                 CK(cudaMemcpyAsync(dst + v0 * P, src + v0 * P, sizeof(double) * ng * P, cudaMemcpyDeviceToDevice, c->stream));
@@ -754,14 +1005,27 @@ static void build_instance_state(const grmhd_ctx* c, int in, const double* rho, 
             }
     std::vector<double> Dr = cheb_lobatto_D(d.Nr), Dt = cheb_gauss_D(d.Nt);
     double tscale = 2.0 / (c->grid.theta_max - c->grid.theta_min);
+    // Fourier theta basis: A_phi (a covariant phi component, parity +1) differentiated on
+    // its double-Fourier extension, d_theta A(theta_k, phi_l) = sum_j c[(k - j) mod 2n]
+    // A(theta_j, phi_l) + c[(k + j + 1) mod 2n] A(theta_j, phi_l + pi)
+    const int n2 = 2 * d.Nt;
+    std::vector<double> crow = fourier_D_row(n2);
+    if (c->ft) tscale = 1.0;
     for (int e = 0; e < Ei; e++)
         for (int i = 0; i < d.Nr; i++)
             for (int k = 0; k < d.Nt; k++)
                 for (int l = 0; l < d.Np; l++) {
                     size_t pt = (((size_t)e * d.Nr + i) * d.Nt + k) * d.Np + l;
                     double dth = 0.0, drr = 0.0;
-                    for (int j = 0; j < d.Nt; j++)
-                        dth += Dt[(size_t)k * d.Nt + j] * A_phi[(((size_t)e * d.Nr + i) * d.Nt + j) * d.Np + l];
+                    const int lp = (l + d.Np / 2) % d.Np;
+                    for (int j = 0; j < d.Nt; j++) {
+                        const size_t row = ((size_t)e * d.Nr + i) * d.Nt + j;
+                        if (c->ft)
+                            dth += crow[((k - j) % n2 + n2) % n2] * A_phi[row * d.Np + l] +
+                                   crow[(k + j + 1) % n2] * A_phi[row * d.Np + lp];
+                        else
+                            dth += Dt[(size_t)k * d.Nt + j] * A_phi[row * d.Np + l];
+                    }
                     for (int j = 0; j < d.Nr; j++)
                         drr += Dr[(size_t)i * d.Nr + j] * A_phi[(((size_t)e * d.Nr + j) * d.Nt + k) * d.Np + l];
                     U[(size_t)V_B * Pi + pt] = dth * tscale;
@@ -921,7 +1185,19 @@ extern "C" int grmhd_diag(grmhd_ctx* c, double out[GRMHD_NDIAG]) {
     DerivJob jb[3];
     for (int dir = 0; dir < 3; dir++) { jb[dir].src = c->U[0] + (V_B + dir) * P; jb[dir].dst = c->scratch; jb[dir].accumulate = dir > 0; jb[dir].pad = 0; }
     CK(cudaMemcpyAsync(c->jobs + c->job_dbg, jb, sizeof(jb), cudaMemcpyHostToDevice, c->stream));
-    for (int dir = 0; dir < 3; dir++) CK(contract(c, dir, 0, c->jobs + c->job_dbg + dir, 1));
+    for (int dir = 0; dir < 3; dir++) {
+        if (dir == 1 && c->ft) {
+            // Fourier theta: sqrt(gamma) B^theta through the fold, added into scratch
+            FoldJob fj[2];
+            fj[0].src = jb[1].src; fj[0].dst = c->Y; fj[0].parity = kThetaParity[V_B + 1]; fj[0].accumulate = 0;
+            fj[1].src = c->Z; fj[1].dst = c->scratch; fj[1].parity = kThetaParity[V_B + 1]; fj[1].accumulate = 1;
+            CK(cudaMemcpyAsync(c->fjobs + c->fj_dbg, &fj[0], sizeof(FoldJob), cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->fjobs + c->fj_dbg_u, &fj[1], sizeof(FoldJob), cudaMemcpyHostToDevice, c->stream));
+            CK(theta_fourier(c, 0, -1, c->fj_dbg, c->fj_dbg_u, 1));
+        } else {
+            CK(contract(c, dir, 0, c->jobs + c->job_dbg + dir, 1));
+        }
+    }
     CK(cudaMemsetAsync(c->diag, 0, sizeof(double) * 8, c->stream));
     CK(launch_diag(c->d, c->pp, c->U[0], c->prim, c->wq, c->scratch, c->diag, c->stream));
     double h[8];
@@ -949,7 +1225,7 @@ static double contraction_flops(const grmhd_ctx* c, int dir, int filter) {
     const int Ns[3] = {c->d.Nr, c->d.Nt, c->d.Np};
     const int N = Ns[dir];
     const double P = (double)c->d.P;
-    const double* split = filter ? c->Fs[dir] : c->Ds[dir];
+    const double* split = (dir == 1 && c->ft) ? (filter ? c->Fts[0] : c->Dts[0]) : (filter ? c->Fs[dir] : c->Ds[dir]);
     if (!split) return 2.0 * N * P;
     double np = dir == 2 ? N / 2 - 1 : N / 2, nf = dir == 2 ? 2 : N % 2;
     double per_line = 2 * np + np * (4 * np + 2 * nf + 5) + nf * (2 * np + 2 * nf + 1);
@@ -989,7 +1265,11 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
             if (k == 0) e = launch_prep(c->d, c->pp, c->U[1], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream);
             else if (k >= 1 && k <= 3) {
                 int dir = k - 1;
-                if (mixed) {
+                if (dir == 1 && c->ft) {
+                    e = theta_fourier(c, 0, mixed ? 0 : -1, c->fj_first[1], c->fj_first_u[1], c->job_first_n);
+                    fl[k] = mixed ? tc_flops(c, dir) * c->job_first_n : contraction_flops(c, dir, 0) * c->job_first_n;
+                    by[k] = (double)P * c->job_first_n * (mixed ? 8.0 + 4.0 : 16.0) + 8.0 * 8.0 * P;
+                } else if (mixed) {
                     e = launch_contract_tc(dir, 0, c->d, c->tcjobs + c->tc_first[1][dir], c->job_first_n, c->tc_img[dir], tf32,
                                            c->r_scale, c->tc_err, c->stream);
                     fl[k] = tc_flops(c, dir) * c->job_first_n;
@@ -1005,7 +1285,11 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
             } else if (k >= 5 && k <= 7) {
                 int dir = k - 5;
                 const int nj[3] = {3 * N_D2, 2 * N_D2, N_D2};
-                if (mixed) {
+                if (dir == 1 && c->ft) {
+                    e = theta_fourier(c, 0, mixed ? 1 : -1, c->fj_second, c->fj_second_u, nj[dir]);
+                    fl[k] = (mixed ? tc_flops(c, dir) : contraction_flops(c, dir, 0)) * nj[dir];
+                    by[k] = (double)P * nj[dir] * (mixed ? 8.0 : 16.0);
+                } else if (mixed) {
                     e = launch_contract_tc(dir, 1, c->d, c->tcjobs + c->tc_second[dir], nj[dir], c->tc_img[dir], tf32,
                                            c->r_scale, c->tc_err, c->stream);
                     fl[k] = tc_flops(c, dir) * nj[dir];
@@ -1026,8 +1310,14 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
             else {
                 int dir = k - 10;
                 // filter contraction of all 32 variables of U[1] (scratch <-> U[1] chain)
-                e = contract(c, dir, 1, c->jobs + c->job_filter[1][dir][1], N_BSSN);
-                if (e == cudaSuccess) e = contract(c, dir, 1, c->jobs + c->job_filter[1][dir][0], 8 + c->pp.glm);
+                if (dir == 1 && c->ft) {
+                    e = theta_fourier(c, 1, -1, c->fj_filter[1][1], c->fj_filter_u[1][1], N_BSSN);
+                    if (e == cudaSuccess)
+                        e = theta_fourier(c, 1, -1, c->fj_filter[1][0], c->fj_filter_u[1][0], 8 + c->pp.glm);
+                } else {
+                    e = contract(c, dir, 1, c->jobs + c->job_filter[1][dir][1], N_BSSN);
+                    if (e == cudaSuccess) e = contract(c, dir, 1, c->jobs + c->job_filter[1][dir][0], 8 + c->pp.glm);
+                }
                 fl[k] = contraction_flops(c, dir, 1) * c->nv;
                 by[k] = (double)P * c->nv * 16.0;
             }
@@ -1057,8 +1347,42 @@ extern "C" int grmhd_debug_deriv(grmhd_ctx* c, const double* in, double* out, in
     const long long P = c->d.P;
     std::vector<DerivJob> jb(nfields);
     for (int f = 0; f < nfields; f++) { jb[f].src = in + f * P; jb[f].dst = out + f * P; jb[f].accumulate = 0; jb[f].pad = 0; }
+    if (dir == 1 && c->ft) {
+        std::vector<int> par(nfields, 1);
+        return grmhd_debug_theta(c, in, out, nfields, par.data(), 0);
+    }
     CK(cudaMemcpyAsync(c->jobs + c->job_dbg, jb.data(), sizeof(DerivJob) * nfields, cudaMemcpyHostToDevice, c->stream));
     CK(contract(c, dir, 0, c->jobs + c->job_dbg, nfields));
+    CK(cudaStreamSynchronize(c->stream));
+    return GRMHD_OK;
+}
+
+extern "C" int grmhd_debug_theta(grmhd_ctx* c, const double* in, double* out, int nfields, const int* parity,
+                                 int filter) {
+    if (!c || !in || !out || !parity || nfields < 1 || (filter != 0 && filter != 1)) return GRMHD_EINVAL;
+    const long long P = c->d.P;
+    if (!c->ft) {
+        if (nfields > 64) return GRMHD_EINVAL;
+        std::vector<DerivJob> jb(nfields);
+        for (int f = 0; f < nfields; f++) { jb[f].src = in + f * P; jb[f].dst = out + f * P; jb[f].accumulate = 0; jb[f].pad = 0; }
+        CK(cudaMemcpyAsync(c->jobs + c->job_dbg, jb.data(), sizeof(DerivJob) * nfields, cudaMemcpyHostToDevice, c->stream));
+        CK(contract(c, 1, filter, c->jobs + c->job_dbg, nfields));
+        CK(cudaStreamSynchronize(c->stream));
+        return GRMHD_OK;
+    }
+    if (nfields > c->nfold) return GRMHD_EINVAL;
+    std::vector<FoldJob> fj(2 * (size_t)nfields);
+    for (int f = 0; f < nfields; f++) {
+        if (parity[f] != 1 && parity[f] != -1) return GRMHD_EINVAL;
+        fj[f].src = in + f * P; fj[f].dst = c->Y + f * P; fj[f].parity = parity[f]; fj[f].accumulate = 0;
+        FoldJob& u = fj[nfields + f];
+        u.src = c->Z + f * P; u.dst = out + f * P; u.parity = parity[f]; u.accumulate = 0;
+    }
+    // the fold and unfold entries are contiguous blocks of nfold slots each
+    CK(cudaMemcpyAsync(c->fjobs + c->fj_dbg, fj.data(), sizeof(FoldJob) * nfields, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->fjobs + c->fj_dbg_u, fj.data() + nfields, sizeof(FoldJob) * nfields, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(theta_fourier(c, filter, -1, c->fj_dbg, c->fj_dbg_u, nfields));
     CK(cudaStreamSynchronize(c->stream));
     return GRMHD_OK;
 }

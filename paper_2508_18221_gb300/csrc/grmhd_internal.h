@@ -66,6 +66,16 @@ struct TcJob {
     int pad;
 };
 
+// Fourier theta basis: one field of a fold (src = canonical field, dst = folded pair of
+// halves) or unfold (src = folded contraction result, dst = canonical field) pass; double
+// or float values as the launch says; parity +1 / -1 of the field under the extension
+struct FoldJob {
+    const void* src;
+    void* dst;
+    int parity;
+    int accumulate;       // unfold only: 0 dst = result, 1 dst += result
+};
+
 // ---- kernel launchers (defined in kernels_*.cu); all return cudaGetLastError()
 // one-time function-attribute setup (shared-memory opt-in); call outside stream capture
 cudaError_t kernels_init();
@@ -89,7 +99,7 @@ cudaError_t launch_contract_tc(int dir, int in_fp32, const Dims& d, const TcJob*
 // slices of the FP64 values; op_img from fx_operator_image, img_estride = bytes between
 // per-element images (radial direction) or 0; Np, Kp, KC from fx_geometry
 void fx_geometry(int N, int* Np, int* Kp, int* KC);
-bool fx_supported(int dir, int N);   // 2..64 nodes (even in phi)
+bool fx_supported(int dir, int N);   // 2..128 nodes (even in phi)
 cudaError_t fx_init();
 cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int njobs, const uint8_t* op_img,
                                long long img_estride, int* err, cudaStream_t s);
@@ -103,6 +113,11 @@ cudaError_t launch_deriv_eo(int dir, const Dims& d, const DerivJob* jobs, int nj
                             cudaStream_t s);
 cudaError_t launch_iface_avg(const Dims& d, double* base, long long field_stride, int nfields,
                              cudaStream_t s);
+// Fourier theta: fold the phi pairs (l, l + N_phi/2) of every job's field into two halves
+// [E][Nr][Nt][N_phi/2] (first the half the even extension operator takes), and the
+// inverse; d are the full grid's dims; fp32 selects float values
+cudaError_t launch_theta_fold(const Dims& d, const FoldJob* jobs, int njobs, int fp32, cudaStream_t s);
+cudaError_t launch_theta_unfold(const Dims& d, const FoldJob* jobs, int njobs, int fp32, cudaStream_t s);
 cudaError_t launch_iface_avg_f(const Dims& d, float* base, long long field_stride, int nfields,
                                cudaStream_t s);
 // per instance: dt[i] = cfl * hmin[i] / max over its nodes of lambda

@@ -128,6 +128,30 @@ std::vector<double> quad_weights(int n, bool lobatto) {
     return w;
 }
 
+// ---------------------------------------------------------------- Fourier theta
+// Double-Fourier extension (the paper's Fourier theta derivative on theta_k = (k + 1/2) pi
+// / n): the 2n extended nodes hold u_k (k < n) and s u'_{2n-1-k} (n <= k < 2n), u' the
+// line at phi + pi and s the component's parity, so with the circulant operator
+// C_ij = c[(i - j) mod 2n] of the extended nodes
+//   (C g)_i = sum_k A_ik u_k + s sum_k B_ik u'_k,  A_ik = c[(i - k) mod 2n],
+//   B_ik = c[(i + k + 1) mod 2n].
+// Writing u = p + m, u' = p - m (p, m the half sum and half difference of the phi pair)
+// gives (C g)_i = ((A + s B) p)_i + ((A - s B) m)_i at phi and the same with -m at
+// phi + pi: the sums take A + B for s = +1 (A - B for s = -1), the differences the other.
+void theta_extension_ops(const std::vector<double>& c, int n, std::vector<double>* even,
+                         std::vector<double>* odd) {
+    const int n2 = 2 * n;
+    even->assign((size_t)n * n, 0.0);
+    odd->assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; i++)
+        for (int k = 0; k < n; k++) {
+            const double a = c[((i - k) % n2 + n2) % n2];
+            const double b = c[(i + k + 1) % n2];
+            (*even)[(size_t)i * n + k] = a + b;
+            (*odd)[(size_t)i * n + k] = a - b;
+        }
+}
+
 // ---------------------------------------------------------------- reflection split
 // Index pairs and fixed points of the node reflection (see kernels_eo.cu):
 // kind 0 (Chebyshev nodes): pairs (ip, N-1-ip), ip < N/2; fixed N/2 when N is odd.

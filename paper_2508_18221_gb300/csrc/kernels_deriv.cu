@@ -118,6 +118,78 @@ cudaError_t launch_iface_avg_f(const Dims& d, float* base, long long fstride, in
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- Fourier theta folding
+// The theta derivative (or filter) of the double-Fourier extension couples the lines at
+// phi and phi + pi: out(phi) = A u(phi) + s B u(phi + pi) with the parity s of the field.
+// With the half sum p and half difference m of the pair, out(phi) = (A + s B) p + (A - s B) m
+// and out(phi + pi) = (A + s B) p - (A - s B) m, so the fold writes p and m into two
+// halves of N_phi / 2 lines per row (the half for the even operator A + B first: p when
+// s = +1, m when s = -1), each half is contracted along theta with one operator, and the
+// unfold adds and subtracts the two results.  Pure streaming: one coalesced read and write
+// per value.
+template <typename T>
+__global__ void k_theta_fold(Dims d, const FoldJob* __restrict__ jobs) {
+    const FoldJob jb = jobs[blockIdx.y];
+    const T* __restrict__ src = static_cast<const T*>(jb.src);
+    T* __restrict__ dst = static_cast<T*>(jb.dst);
+    const int h = d.Np / 2;
+    const long long half = d.P / 2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < half;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long row = t / h;
+        const long long i0 = row * d.Np + (t - row * h);
+        const T a = src[i0], b = src[i0 + h];
+        const T p = (T)0.5 * (a + b), m = (T)0.5 * (a - b);
+        dst[t] = jb.parity > 0 ? p : m;
+        dst[half + t] = jb.parity > 0 ? m : p;
+    }
+}
+
+template <typename T>
+__global__ void k_theta_unfold(Dims d, const FoldJob* __restrict__ jobs) {
+    const FoldJob jb = jobs[blockIdx.y];
+    const T* __restrict__ src = static_cast<const T*>(jb.src);
+    T* __restrict__ dst = static_cast<T*>(jb.dst);
+    const int h = d.Np / 2;
+    const long long half = d.P / 2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < half;
+         t += (long long)gridDim.x * blockDim.x) {
+        const T z0 = src[t], z1 = src[half + t];
+        const T zp = jb.parity > 0 ? z0 : z1, zm = jb.parity > 0 ? z1 : z0;
+        const long long row = t / h;
+        const long long i0 = row * d.Np + (t - row * h);
+        if (jb.accumulate) {
+            dst[i0] += zp + zm;
+            dst[i0 + h] += zp - zm;
+        } else {
+            dst[i0] = zp + zm;
+            dst[i0 + h] = zp - zm;
+        }
+    }
+}
+
+static dim3 fold_grid(const Dims& d, int njobs) {
+    long long nb = (d.P / 2 + 255) / 256;
+    if (nb > 152LL * 16) nb = 152LL * 16;
+    return dim3((unsigned)nb, (unsigned)njobs);
+}
+
+cudaError_t launch_theta_fold(const Dims& d, const FoldJob* jobs, int njobs, int fp32, cudaStream_t s) {
+    if (njobs <= 0 || d.P <= 0) return cudaSuccess;
+    if (d.Np % 2) return cudaErrorInvalidValue;
+    if (fp32) k_theta_fold<float><<<fold_grid(d, njobs), 256, 0, s>>>(d, jobs);
+    else k_theta_fold<double><<<fold_grid(d, njobs), 256, 0, s>>>(d, jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_theta_unfold(const Dims& d, const FoldJob* jobs, int njobs, int fp32, cudaStream_t s) {
+    if (njobs <= 0 || d.P <= 0) return cudaSuccess;
+    if (d.Np % 2) return cudaErrorInvalidValue;
+    if (fp32) k_theta_unfold<float><<<fold_grid(d, njobs), 256, 0, s>>>(d, jobs);
+    else k_theta_unfold<double><<<fold_grid(d, njobs), 256, 0, s>>>(d, jobs);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- CFL time step
 // lambda = |beta|_gamma + max(alpha, sqrt(2 alpha)); max over nodes by atomicMax on the
 // bit pattern (order-preserving for non-negative doubles); dt = cfl hmin / lambda_max.

@@ -698,6 +698,9 @@ cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int
     if (njobs <= 0) return cudaSuccess;
     const int N = dir == 0 ? d.Nr : (dir == 1 ? d.Nt : d.Np);
     if (!fx_supported(dir, N)) return cudaErrorNotSupported;
+    // r and theta tiles are staged with bulk copies of row segments: 16-byte alignment
+    // needs an even number of phi lines per row
+    if (dir < 2 && (d.Np % 2)) return cudaErrorNotSupported;
     int Np, Kp, KC;
     fx_geometry(N, &Np, &Kp, &KC);
     FxParams fp;

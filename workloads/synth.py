@@ -79,6 +79,11 @@ CONFIGS = {
     # precision variant of c1
     "c3": Config("c3", a=0.5, n_elem=2, r_min=1.8, r_max=20.0, n_r=12, n_theta=12,
                  n_phi=16, profile="powerlaw", A0=0.093, seed=1001, nsteps=100),
+    # c2's instance on the paper's Fourier theta basis: N_theta = 32 uniform pole-free nodes
+    # over the whole sphere (393,216 points), 100 steps
+    "c2f": Config("c2f", a=0.9, n_elem=8, r_min=1.5, r_max=100.0, n_r=24, n_theta=32,
+                  n_phi=64, theta_min=0.0, theta_max=math.pi, theta_basis=1,
+                  profile="torus", A0=8.4e-3, seed=1002, nsteps=100),
     # large single instance: 16 elements, 32 x 64 x 128 (4,194,304 points), 200 steps
     "c5": Config("c5", a=0.94, n_elem=16, r_min=1.3, r_max=500.0, n_r=32, n_theta=64,
                  n_phi=128, profile="torus", rho_cut=0.2, A0=8.2e-4, vphi_amp=0.5,
