@@ -20,6 +20,7 @@ def main(argv=None):
     ap.add_argument("--precision", type=int, default=0, help="0 FP64, 1 split BF16 x3, 2 TF32")
     ap.add_argument("--coupling", type=int, default=0, help="0 unsplit, 1 split (fluid RK, BSSN Euler)")
     ap.add_argument("--integrator", type=int, default=0, help="0 SSP-RK3, 1 RK4")
+    ap.add_argument("--dt-scale", type=float, default=1.0, help="time step as a fraction of the CFL step")
     a = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -42,7 +43,7 @@ def main(argv=None):
     for _ in range(a.rhs):
         ctx.rhs(out, True)
     if a.steps:
-        dt = ctx.cfl_dt()
+        dt = ctx.cfl_dt() * a.dt_scale
         ctx.step(dt, a.steps)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
