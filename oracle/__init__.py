@@ -16,6 +16,8 @@ Modules
   bssn         BSSN + gauge right-hand side at points
   solver       multi-element grid, full RHS with interface coupling, RK stages,
                post-step filter, CFL time step, diagnostics, initial data
+  xcts         approximate XCTS initial data: flat-Laplacian boundary-value problem,
+               fixed-point relaxation on psi, the conformally flat slice
 
 Parity pins live in tests/test_oracle_*.py; functions without one say
 "parity unpinned" in their docstring.

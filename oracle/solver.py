@@ -533,13 +533,14 @@ def diagnostics(U, g: Grid, p: Params):
 
 
 # ----------------------------------------------------------------- initial data
-def initial_state(g: Grid, p: Params, prim):
-    """Canonical state from Kerr-Schild BSSN data and primitive profiles.
+def initial_state(g: Grid, p: Params, prim, bssn=None):
+    """Canonical state from Kerr-Schild BSSN data (or the given BSSN data, e.g. the XCTS
+    slice) and primitive profiles.
 
     prim: dict with rho, p, vr, vth, vph, A_phi on the node grid.  The densitized
     field is B~^r = d_theta A_phi, B~^theta = -d_r A_phi, B~^phi = 0 (so that
     d_i B~^i = 0 for the tensor-product operators), B^i = B~^i / sqrt(gamma)."""
-    ksd = ks.bssn_data(p.M, p.a, g.R, g.T)
+    ksd = bssn if bssn is not None else ks.bssn_data(p.M, p.a, g.R, g.T)
     U = np.zeros((NV + (1 if p.glm else 0),) + g.shape)
     for n, (i, j) in enumerate(SYM):
         U[I_GT + n] = ksd["gt"][..., i, j]

@@ -84,6 +84,15 @@ CONFIGS = {
     "c2f": Config("c2f", a=0.9, n_elem=8, r_min=1.5, r_max=100.0, n_r=24, n_theta=32,
                   n_phi=64, theta_min=0.0, theta_max=math.pi, theta_basis=1,
                   profile="torus", A0=8.4e-3, seed=1002, nsteps=100),
+    # approximate XCTS initial data (whole sphere, Fourier theta): a dilute power-law gas
+    # around the puncture (rho0 = 1e-4: the paper's plain fixed point contracts; at the
+    # evolution workloads' densities it diverges); x1 small, x2 on c2f's grid
+    "x1": Config("x1", a=0.0, n_elem=2, r_min=1.8, r_max=20.0, n_r=12, n_theta=12, n_phi=16,
+                 theta_min=0.0, theta_max=math.pi, theta_basis=1, profile="powerlaw",
+                 rho0=1e-4, A0=0.0, seed=1011, nsteps=1),
+    "x2": Config("x2", a=0.0, n_elem=8, r_min=1.5, r_max=100.0, n_r=24, n_theta=32, n_phi=64,
+                 theta_min=0.0, theta_max=math.pi, theta_basis=1, profile="powerlaw",
+                 rho0=1e-4, A0=0.0, seed=1012, nsteps=1),
     # large single instance: 16 elements, 32 x 64 x 128 (4,194,304 points), 200 steps
     "c5": Config("c5", a=0.94, n_elem=16, r_min=1.3, r_max=500.0, n_r=32, n_theta=64,
                  n_phi=128, profile="torus", rho_cut=0.2, A0=8.2e-4, vphi_amp=0.5,
