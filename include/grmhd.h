@@ -250,6 +250,26 @@ int grmhd_batch_step(grmhd_batch* b, const double* dt, int nsteps);
 int grmhd_batch_destroy(grmhd_batch* b);
 const char* grmhd_batch_last_error(const grmhd_batch* b);
 
+/* Approximate XCTS initial data (paper: "Initial Data: Approximate XCTS Solution"): solves
+ * the conformal Hamiltonian constraint lap psi = -2 pi rho psi^5 (flat conformal metric,
+ * A_ij = 0) by the paper's fixed-point relaxation psi_{k+1} = L^-1(-2 pi rho psi_k^5) from
+ * the puncture psi = 1 + M / (2 r), with d_r psi = -M / (2 r_min^2) at r_min, psi + r d_r psi
+ * = 1 at r_max and C^1 matching at element interfaces, then sets the state to the slice
+ * gamma_ij = psi^4 (flat metric), K = 0 (lapse psi^-2, shift zero) carrying the fluid and
+ * field of the given primitives (as grmhd_init_prims).  Host arrays of num_points values in
+ * the canonical node order; rho is the primitive rest-mass density.  At most `iters`
+ * iterations, fewer when max |psi_{k+1} - psi_k| < tol (tol = 0: all).  psi_out (may be NULL)
+ * receives psi; changes (iters entries, may be NULL) the change of every iteration; stats
+ * (3 entries, may be NULL) the set-up time in ms (operator assembly and LU factorisation),
+ * the mean time per iteration and the iterations done.  Needs theta_basis = 1 and a
+ * single-instance context (GRMHD_EUNSUPPORTED otherwise, or when cuSOLVER cannot be
+ * opened: the dense per-phi-mode LU is its dgetrf / dgetrs); GRMHD_ENAN when the fixed
+ * point diverges (too dense a source).  Allocates (N_phi/2 + 1) (E n_r n_theta)^2 doubles
+ * of device memory for the call. */
+int grmhd_xcts_init(grmhd_ctx* ctx, const double* rho, const double* p, const double* vr,
+                    const double* vth, const double* vph, const double* A_phi, int iters, double tol,
+                    double* psi_out, double* changes, double* stats);
+
 /* Test hook: apply the first derivative along direction dir (0 r, 1 theta, 2 phi) to
  * `nfields` canonical fields (nfields * num_points doubles) with the library's
  * operators (radial: per element, one-sided at element ends).  Device pointers. */

@@ -74,6 +74,7 @@ SIGNATURES = {
     "grmhd_batch_launch_count": (C.c_longlong, [_P]),
     "grmhd_batch_destroy": (C.c_int, [_P]),
     "grmhd_batch_last_error": (C.c_char_p, [_P]),
+    "grmhd_xcts_init": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int, C.c_double, _P, _P, _P]),
     "grmhd_debug_deriv": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
     "grmhd_debug_theta": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "grmhd_cfl_dt_noalloc": (C.c_int, [_P, C.c_longlong, C.c_double, C.c_double, _P, _P]),
@@ -169,6 +170,18 @@ class Context:
         arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel()
                 for a in (rho, p, vr, vth, vph, A_phi)]
         self._chk(self.lib.grmhd_init_prims(self.h, *[_ptr(a) for a in arrs]))
+
+    def xcts_init(self, rho, p, vr, vth, vph, A_phi, iters: int = 20, tol: float = 0.0):
+        """Approximate XCTS initial data (grmhd_xcts_init); returns (psi, changes, stats)"""
+        import numpy as np
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel()
+                for a in (rho, p, vr, vth, vph, A_phi)]
+        psi = np.empty(self.n_points)
+        changes = np.zeros(iters)
+        stats = np.zeros(3)
+        self._chk(self.lib.grmhd_xcts_init(self.h, *[_ptr(a) for a in arrs], int(iters), float(tol),
+                                           _ptr(psi), _ptr(changes), _ptr(stats)))
+        return psi, changes[:int(stats[2])], stats
 
     def set_state(self, state, on_device: bool):
         self._chk(self.lib.grmhd_set_state(self.h, _ptr(state), int(on_device)))

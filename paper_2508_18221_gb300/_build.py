@@ -12,7 +12,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrmhd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["kernels_point.cu", "kernels_deriv.cu", "kernels_eo.cu", "kernels_tc.cu", "kernels_fx.cu", "api.cu",
-      "noalloc.cu"]
+      "noalloc.cu", "kernels_xcts.cu"]
 CPP = ["host_ops.cpp"]
 
 
@@ -46,7 +46,7 @@ def build(verbose: bool = False) -> str:
         logs = list(ex.map(_run, jobs))
     objs = [os.path.join(BUILD, f + ".o") for f in CU + CPP]
     tmp = LIB + ".tmp"
-    _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+    _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"])
     os.replace(tmp, LIB)
     if verbose:
         for lg in logs:

@@ -985,16 +985,38 @@ extern "C" int grmhd_get_state(grmhd_ctx* c, double* state, int on_device) {
 // Canonical state (GRMHD_NV x P_i, instance-local layout) of instance `in` of the group:
 // Kerr-Schild BSSN data of that instance's background, densitized field from A_phi with
 // the grid operators, conserved variables from the primitives (instance-local arrays).
+// psi != nullptr: the XCTS slice gamma_ij = psi^4 (flat spherical metric), K = 0 instead of
+// Kerr-Schild (conformal metric (r^4 sin^2 theta)^(-1/3) diag(1, r^2, r^2 sin^2 theta) with
+// det = 1, phi = ln psi + ln(r^4 sin^2 theta) / 12, Gammatilde^i = -d_j gammatilde^ij in closed
+// form, lapse psi^-2, shift and driver zero)
 static void build_instance_state(const grmhd_ctx* c, int in, const double* rho, const double* p,
                                  const double* vr, const double* vth, const double* vph,
-                                 const double* A_phi, std::vector<double>& U) {
+                                 const double* A_phi, std::vector<double>& U, const double* psi = nullptr) {
     const Dims& d = c->d;
     const int Ei = c->inst_E[in], off = c->inst_off[in];
     const long long Pi = (long long)Ei * d.elem;
     U.assign((size_t)c->nv * Pi, 0.0);   // psi (GLM) starts at zero
     double bssn[24];
     // Kerr-Schild BSSN data depends on (r, theta) only
-    for (int e = 0; e < Ei; e++)
+    for (int e = 0; e < Ei && psi; e++)
+        for (int i = 0; i < d.Nr; i++)
+            for (int k = 0; k < d.Nt; k++) {
+                const double r = c->r_nodes[(size_t)(off + e) * d.Nr + i], th = c->th_nodes[k];
+                const double st = std::sin(th), w = r * r * r * r * st * st, f = std::pow(w, -1.0 / 3.0);
+                for (int l = 0; l < d.Np; l++) {
+                    size_t pt = (((size_t)e * d.Nr + i) * d.Nt + k) * d.Np + l;
+                    double b[24] = {0.0};
+                    b[0] = f;
+                    b[3] = f * r * r;
+                    b[5] = f * r * r * st * st;
+                    b[6] = std::log(psi[pt]) + std::log(w) / 12.0;
+                    b[14] = -4.0 / 3.0 * std::cbrt(r) * std::pow(st, 2.0 / 3.0);
+                    b[15] = -2.0 / 3.0 * std::pow(r, -2.0 / 3.0) * std::pow(st, -1.0 / 3.0) * std::cos(th);
+                    b[17] = 1.0 / (psi[pt] * psi[pt]);
+                    for (int v = 0; v < 24; v++) U[(size_t)v * Pi + pt] = b[v];
+                }
+            }
+    for (int e = 0; e < Ei && !psi; e++)
         for (int i = 0; i < d.Nr; i++)
             for (int k = 0; k < d.Nt; k++) {
                 ks_bssn_point(c->inst_M[in], c->inst_a[in], c->r_nodes[(size_t)(off + e) * d.Nr + i], c->th_nodes[k], bssn);
@@ -1080,6 +1102,68 @@ extern "C" int grmhd_init_prims(grmhd_ctx* c, const double* rho, const double* p
         int st = inst_set_state(c, in, U.data(), 0);
         if (st) return st;
     }
+    return GRMHD_OK;
+}
+
+extern "C" int grmhd_xcts_init(grmhd_ctx* c, const double* rho, const double* p, const double* vr,
+                               const double* vth, const double* vph, const double* A_phi, int iters,
+                               double tol, double* psi_out, double* changes, double* stats) {
+    if (!c || !rho || !p || !vr || !vth || !vph || !A_phi || iters < 1 || iters > 10000 || !(tol >= 0.0))
+        return GRMHD_EINVAL;
+    if (!c->ft) return set_err(c, GRMHD_EUNSUPPORTED, "the XCTS solve covers the whole sphere: theta_basis = 1 only");
+    if (c->n_inst != 1) return set_err(c, GRMHD_EUNSUPPORTED, "XCTS initial data is built for one instance");
+    const Dims& d = c->d;
+    XctsOps o;
+    o.E = d.E; o.Nr = d.Nr; o.Nt = d.Nt; o.Np = d.Np;
+    const size_t nr2 = (size_t)d.Nr * d.Nr, nt2 = (size_t)d.Nt * d.Nt;
+    const std::vector<double> D = cheb_lobatto_D(d.Nr);
+    o.Dr.assign(nr2 * d.E, 0.0);
+    o.Drr.assign(nr2 * d.E, 0.0);
+    for (int e = 0; e < d.E; e++) {
+        double* Dr = &o.Dr[nr2 * e];
+        for (size_t q = 0; q < nr2; q++) Dr[q] = D[q] * c->rscale_h[e];
+        for (int i = 0; i < d.Nr; i++)
+            for (int j = 0; j < d.Nr; j++) {
+                double acc = 0.0;
+                for (int q = 0; q < d.Nr; q++) acc += Dr[(size_t)i * d.Nr + q] * Dr[(size_t)q * d.Nr + j];
+                o.Drr[nr2 * e + (size_t)i * d.Nr + j] = acc;
+            }
+    }
+    // theta: the mode's extension parity s = (-1)^m; d_theta of parity s, then of parity -s
+    std::vector<double> ev, od;
+    theta_extension_ops(fourier_D_row(2 * d.Nt), d.Nt, &ev, &od);
+    o.D1.resize(2 * nt2);
+    o.D2.assign(2 * nt2, 0.0);
+    for (size_t q = 0; q < nt2; q++) { o.D1[q] = ev[q]; o.D1[nt2 + q] = od[q]; }
+    for (int i = 0; i < d.Nt; i++)
+        for (int j = 0; j < d.Nt; j++) {
+            double a = 0.0, b = 0.0;
+            for (int q = 0; q < d.Nt; q++) {
+                a += od[(size_t)i * d.Nt + q] * ev[(size_t)q * d.Nt + j];
+                b += ev[(size_t)i * d.Nt + q] * od[(size_t)q * d.Nt + j];
+            }
+            o.D2[(size_t)i * d.Nt + j] = a;
+            o.D2[nt2 + (size_t)i * d.Nt + j] = b;
+        }
+    o.r = c->r_nodes;
+    o.th = c->th_nodes;
+    o.M = c->inst_M[0];
+    o.r_min = c->grid.r_min;
+    o.r_max = c->grid.r_max;
+    // fixed point from the puncture psi = 1 + M / (2 r)
+    std::vector<double> psi((size_t)d.P);
+    for (int e = 0; e < d.E; e++)
+        for (int i = 0; i < d.Nr; i++)
+            for (long long kl = 0; kl < d.NtNp; kl++)
+                psi[((size_t)e * d.Nr + i) * d.NtNp + kl] = 1.0 + o.M / (2.0 * c->r_nodes[(size_t)e * d.Nr + i]);
+    char msg[256] = {0};
+    int st = xcts_solve(o, rho, psi.data(), iters, tol, changes, stats, c->stream, msg, sizeof(msg));
+    if (st) return set_err(c, st, "%s", msg);
+    std::vector<double> U;
+    build_instance_state(c, 0, rho, p, vr, vth, vph, A_phi, U, psi.data());
+    st = inst_set_state(c, 0, U.data(), 0);
+    if (st) return st;
+    if (psi_out) memcpy(psi_out, psi.data(), sizeof(double) * (size_t)d.P);
     return GRMHD_OK;
 }
 

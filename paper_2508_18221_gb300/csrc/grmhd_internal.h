@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/grmhd.h"
 
 namespace gk {
@@ -127,5 +129,20 @@ cudaError_t launch_diag(const Dims& d, const PhysParams& pp, const double* U,
                         const double* prim, const double* wq, const double* divB,
                         double* out_dev, cudaStream_t s);
 cudaError_t launch_nan_check(long long n, const double* U, int* flag, cudaStream_t s);
+
+// Approximate XCTS initial data (kernels_xcts.cu): operators of the boundary-value problem
+// on one instance's grid (Fourier theta basis) and the fixed-point solve
+struct XctsOps {
+    int E, Nr, Nt, Np;
+    std::vector<double> Dr, Drr;   // [E][Nr][Nr] element radial first / second derivative
+    std::vector<double> D1, D2;    // [2][Nt][Nt] theta first / second derivative, mode parity +1, -1
+    std::vector<double> r, th;     // [E * Nr] radial nodes, [Nt] theta nodes
+    double M, r_min, r_max;
+};
+// psi_host: initial guess in, solution out (num_points values); changes (iters entries, may
+// be null): max |psi_{k+1} - psi_k|; stats (may be null): set-up ms (assembly + LU),
+// mean ms per iteration, iterations done; returns a GRMHD status, message in msg
+int xcts_solve(const XctsOps& o, const double* rho_host, double* psi_host, int iters, double tol,
+               double* changes, double* stats, cudaStream_t s, char* msg, size_t msglen);
 
 }  // namespace gk
