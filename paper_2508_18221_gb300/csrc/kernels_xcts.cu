@@ -20,7 +20,8 @@
 // dgetrf / dgetrs, opened at run time (this step runs once before the time stepping and
 // has no other dense solver here); per iteration one kernel forms the source and the
 // forward real Fourier transform in phi, and one the inverse transform with the change
-// max |psi_{k+1} - psi_k| (block maxima, then one atomic per block).
+// max |psi_{k+1} - psi_k| (block maxima, then one atomic per block).  The modes' LU calls
+// are independent and latency-bound, so they are spread over up to 8 side streams.
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
 #include <dlfcn.h>
@@ -217,11 +218,16 @@ int xcts_solve(const XctsOps& o, const double* rho_host, double* psi_host, int i
             sn[(size_t)m * o.Np + l] = std::sin(a);
         }
     double *dDr = nullptr, *dDrr = nullptr, *dD1 = nullptr, *dD2 = nullptr, *dr = nullptr, *dth = nullptr,
-           *dcs = nullptr, *dsn = nullptr, *dL = nullptr, *dB = nullptr, *drho = nullptr, *dpsi = nullptr,
-           *dws = nullptr;
+           *dcs = nullptr, *dsn = nullptr, *dL = nullptr, *dB = nullptr, *drho = nullptr, *dpsi = nullptr;
     int *dpiv = nullptr, *dinfo = nullptr;
     unsigned long long* dchg = nullptr;
-    cusolverDnHandle_t h = nullptr;
+    // the modes' factorisations and triangular solves are independent: they run on NS side
+    // streams (one cuSOLVER handle and LU workspace each), forked from and joined to s
+    const int NS = nmodes < 8 ? nmodes : 8;
+    cudaStream_t ss[8] = {};
+    cusolverDnHandle_t hs[8] = {};
+    double* ws[8] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[8] = {};
     int st = GRMHD_OK;
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
     auto fail = [&](int code, const char* what) {
@@ -260,18 +266,34 @@ int xcts_solve(const XctsOps& o, const double* rho_host, double* psi_host, int i
             k_xcts_assemble<<<(unsigned)nb, 256, 0, s>>>(x, dL);
             if (cudaGetLastError() != cudaSuccess) { fail(GRMHD_ECUDA, "assembly launch"); break; }
         }
-        if (sv.create(&h) != CUSOLVER_STATUS_SUCCESS || sv.set_stream(h, s) != CUSOLVER_STATUS_SUCCESS) {
-            fail(GRMHD_ECUDA, "cusolverDnCreate failed");
-            break;
-        }
+        if (cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)) { fail(GRMHD_ECUDA, "events"); break; }
+        for (int j = 0; j < NS && st == GRMHD_OK; j++)
+            if (cudaStreamCreateWithFlags(&ss[j], cudaStreamNonBlocking) ||
+                cudaEventCreateWithFlags(&ev_join[j], cudaEventDisableTiming) ||
+                sv.create(&hs[j]) != CUSOLVER_STATUS_SUCCESS || sv.set_stream(hs[j], ss[j]) != CUSOLVER_STATUS_SUCCESS)
+                fail(GRMHD_ECUDA, "cuSOLVER handles / side streams");
+        if (st) break;
         int lwork = 0;
-        if (sv.getrf_ws(h, n, n, dL, n, &lwork) != CUSOLVER_STATUS_SUCCESS || xalloc(&dws, (size_t)lwork + 1)) {
-            fail(GRMHD_ENOMEM, "LU workspace");
-            break;
-        }
+        if (sv.getrf_ws(hs[0], n, n, dL, n, &lwork) != CUSOLVER_STATUS_SUCCESS) { fail(GRMHD_ECUDA, "LU workspace size"); break; }
+        for (int j = 0; j < NS && st == GRMHD_OK; j++)
+            if (xalloc(&ws[j], (size_t)lwork + 1)) fail(GRMHD_ENOMEM, "LU workspace");
+        if (st) break;
+        auto fork = [&]() {
+            cudaEventRecord(ev_fork, s);
+            for (int j = 0; j < NS; j++) cudaStreamWaitEvent(ss[j], ev_fork, 0);
+        };
+        auto join = [&]() {
+            for (int j = 0; j < NS; j++) {
+                cudaEventRecord(ev_join[j], ss[j]);
+                cudaStreamWaitEvent(s, ev_join[j], 0);
+            }
+        };
+        fork();
         for (int m = 0; m < nmodes && st == GRMHD_OK; m++)
-            if (sv.getrf(h, n, n, dL + nn * m, n, dws, dpiv + (size_t)n * m, dinfo + m) != CUSOLVER_STATUS_SUCCESS)
+            if (sv.getrf(hs[m % NS], n, n, dL + nn * m, n, ws[m % NS], dpiv + (size_t)n * m, dinfo + m) !=
+                CUSOLVER_STATUS_SUCCESS)
                 fail(GRMHD_ECUDA, "dgetrf failed");
+        join();
         if (st) break;
         std::vector<int> info(nmodes);
         if (cudaMemcpyAsync(info.data(), dinfo, sizeof(int) * nmodes, cudaMemcpyDeviceToHost, s) ||
@@ -286,10 +308,12 @@ int xcts_solve(const XctsOps& o, const double* rho_host, double* psi_host, int i
             if (nb > 152LL * 16) nb = 152LL * 16;
             k_xcts_forward<<<(unsigned)nb, 256, 0, s>>>(x, drho, dpsi, dB);
             if (cudaGetLastError() != cudaSuccess) { fail(GRMHD_ECUDA, "forward transform launch"); break; }
+            fork();
             for (int m = 0; m < nmodes && st == GRMHD_OK; m++)
-                if (sv.getrs(h, CUBLAS_OP_N, n, 2, dL + nn * m, n, dpiv + (size_t)n * m, dB + (size_t)2 * n * m, n,
+                if (sv.getrs(hs[m % NS], CUBLAS_OP_N, n, 2, dL + nn * m, n, dpiv + (size_t)n * m, dB + (size_t)2 * n * m, n,
                              dinfo + m) != CUSOLVER_STATUS_SUCCESS)
                     fail(GRMHD_ECUDA, "dgetrs failed");
+            join();
             if (st) break;
             unsigned long long z = 0;
             if (cudaMemcpyAsync(dchg, &z, sizeof(z), cudaMemcpyHostToDevice, s)) { fail(GRMHD_ECUDA, "reset"); break; }
@@ -323,11 +347,17 @@ int xcts_solve(const XctsOps& o, const double* rho_host, double* psi_host, int i
         }
     } while (false);
     cudaStreamSynchronize(s);
-    if (h) sv.destroy(h);
+    for (int j = 0; j < NS; j++) {
+        if (hs[j]) sv.destroy(hs[j]);
+        if (ss[j]) cudaStreamDestroy(ss[j]);
+        if (ev_join[j]) cudaEventDestroy(ev_join[j]);
+        if (ws[j]) cudaFree(ws[j]);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e2) cudaEventDestroy(e2);
-    void* bufs[] = {dDr, dDrr, dD1, dD2, dr, dth, dcs, dsn, dL, dB, drho, dpsi, dws, dpiv, dinfo, dchg};
+    void* bufs[] = {dDr, dDrr, dD1, dD2, dr, dth, dcs, dsn, dL, dB, drho, dpsi, dpiv, dinfo, dchg};
     for (void* b : bufs)
         if (b) cudaFree(b);
     return st;
