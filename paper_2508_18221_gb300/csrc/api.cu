@@ -1,10 +1,12 @@
 // C ABI: context management, the per-stage pipeline and the graph-captured RK driver.
 //
-// One right-hand-side evaluation (one Runge-Kutta stage) is 10 launches on the
-// context's stream:
-//   prep  | deriv r, theta, phi (first derivatives of 21 BSSN fields + flux divergence)
-//   | interface mean of d_r | deriv r, theta, phi (second derivatives of 11 fields)
-//   | interface mean of d_rr | rhs (+ RK stage combination)
+// One right-hand-side evaluation (one Runge-Kutta stage) is about 12 launches on two
+// streams joined before the right-hand side:
+//   side stream: deriv r, theta, phi (first derivatives of 21 BSSN fields) | interface mean
+//                of d_r | deriv r, theta, phi (second derivatives of 11 fields) | interface
+//                mean of d_rr
+//   main stream: prep | deriv r, theta, phi (flux divergence) | (join) | rhs (+ RK stage
+//                combination)
 // A time step adds the filter (3 directional contractions + interface mean of the BSSN
 // copies).  grmhd_step records nsteps steps into one CUDA graph.
 #include <cuda_runtime.h>
@@ -29,6 +31,10 @@ struct grmhd_ctx {
     PhysParams pp;
     cudaStream_t stream;
     bool own_stream;
+    // side stream of a stage: the BSSN derivative chain runs there while the primitive
+    // recovery and the flux divergence run on `stream` (fork / join events)
+    cudaStream_t s2;
+    cudaEvent_t ev_fork, ev_join;
     // device buffers
     double* U[3];            // U[0] = state, U[1], U[2] = stage buffers
     double* acc;             // RK4 accumulator (allocated for integrator = 1)
@@ -254,6 +260,9 @@ static void free_ctx(grmhd_ctx* c) {
         if (c->tc_t[k]) cudaFree(c->tc_t[k]);
     }
     if (c->fjobs) cudaFree(c->fjobs);
+    if (c->s2) cudaStreamDestroy(c->s2);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -320,6 +329,12 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         cudaError_t e = cudaStreamCreate(&c->stream);
         if (e != cudaSuccess) { free_ctx(c); return GRMHD_ECUDA; }
         c->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&c->s2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        free_ctx(c);
+        return GRMHD_ECUDA;
     }
     // physics parameters
     c->pp.M = phys->M; c->pp.a = phys->a; c->pp.gam = phys->gamma_eos;
@@ -415,9 +430,10 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
     AL(c->r_scale, E); AL(c->wq, P); AL(c->hmin, ninst); AL(c->dt, ninst); AL(c->diag, 8);
     AL(c->nfail, 1); AL(c->lam_bits, ninst); AL(c->nan_flag, 1); AL(c->tc_err, 1);
     AL(c->iface_dev, E); AL(c->elem_inst_dev, E);
-    // folding buffers of the Fourier theta basis: the largest theta job list (first
-    // derivatives: 21 fields + 8 fluxes, + psi and B^theta with GLM)
-    c->nfold = N_D1 + 8 + 2 * glm;
+    // folding buffers of the Fourier theta basis: the first-derivative list (21 fields + 8
+    // fluxes, + psi and B^theta with GLM) and, after it, the second-derivative list (22), whose
+    // contractions run on the side stream while the flux divergences run on the main one
+    c->nfold = N_D1 + 8 + 2 * glm + 2 * N_D2;
     if (c->ft) { AL(c->Y, (long long)c->nfold * P); AL(c->Z, (long long)c->nfold * P); }
 #undef AL
     if (ce != cudaSuccess) {
@@ -699,7 +715,7 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         c->fj_second = (int)fj.size();
         for (int q = 0; q < N_D2; q++)
             for (int x = 0; x < 2; x++) {
-                const long long i = 2 * q + x, so = ((long long)v2[q] * 3 + 1 + x) * P;
+                const long long i = n1 + 2 * q + x, so = ((long long)v2[q] * 3 + 1 + x) * P;
                 const int par = x == 0 ? -kThetaParity[v2[q]] : kThetaParity[v2[q]];
                 if (mixed) addf(reinterpret_cast<const float*>(c->d1) + so, Yf + i * P, par, 0);
                 else addf(c->d1 + so, c->Y + i * P, par, 0);
@@ -707,7 +723,7 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         c->fj_second_u = (int)fj.size();
         for (int q = 0; q < N_D2; q++)
             for (int x = 0; x < 2; x++) {
-                const long long i = 2 * q + x, dof = ((long long)q * 6 + 3 + x) * P;
+                const long long i = n1 + 2 * q + x, dof = ((long long)q * 6 + 3 + x) * P;
                 const int par = x == 0 ? -kThetaParity[v2[q]] : kThetaParity[v2[q]];
                 if (mixed) addf(Zf + i * P, reinterpret_cast<float*>(c->d2) + dof, par, 0);
                 else addf(c->Z + i * P, c->d2 + dof, par, 0);
@@ -796,17 +812,20 @@ static cudaError_t contract(grmhd_ctx* c, int dir, int filter, const DerivJob* j
 // the two halves along theta with the even and the odd extension operator, unfold into
 // the destinations (4 launches).  stage < 0: FP64 values (digit-slice, reflection-split or
 // dense kernel); 0 / 1: the mixed-precision tensor-core kernel on FP64 / FP32 inputs.
-static cudaError_t theta_fourier(grmhd_ctx* c, int filter, int stage, int fold_off, int unfold_off, int n) {
+// i0: folding-buffer field of the list's first job (lists that may run concurrently use
+// disjoint fields)
+static cudaError_t theta_fourier(grmhd_ctx* c, int filter, int stage, int fold_off, int unfold_off, int n,
+                                 int i0 = 0) {
     cudaError_t e = launch_theta_fold(c->d, c->fjobs + fold_off, n, stage == 1, c->stream);
     if (e != cudaSuccess) return e;
     for (int h = 0; h < 2; h++) {
         if (stage >= 0) {
-            e = launch_contract_tc(1, stage, c->dh, c->tcjobs + c->tc_fy[stage][h], n, c->tc_t[h],
+            e = launch_contract_tc(1, stage, c->dh, c->tcjobs + c->tc_fy[stage][h] + i0, n, c->tc_t[h],
                                    c->opts.precision == 2, c->r_scale, c->tc_err, c->stream);
         } else {
             const uint8_t* fx = filter ? c->fx_ft[h] : c->fx_dt[h];
             const double* split = filter ? c->Fts[h] : c->Dts[h];
-            const DerivJob* jb = c->jobs + c->job_fy[h];
+            const DerivJob* jb = c->jobs + c->job_fy[h] + i0;
             if (fx) e = launch_contract_fx(1, c->dh, jb, n, fx, 0, c->tc_err, c->stream);
             else if (split) e = launch_deriv_eo(1, c->dh, jb, n, split, filter ? 1 : -1, nullptr, c->stream);
             else e = launch_deriv(1, c->dh, jb, n, filter ? c->Ft2[h] : c->Dt2[h], nullptr, c->stream);
@@ -817,34 +836,29 @@ static cudaError_t theta_fourier(grmhd_ctx* c, int filter, int stage, int fold_o
     return launch_theta_unfold(c->d, c->fjobs + unfold_off, n, stage >= 0, c->stream);
 }
 
-static int enqueue_first_derivs(grmhd_ctx* c, int b) {
-    if (c->opts.precision > 0) {
-        const int tf32 = c->opts.precision == 2;
-        for (int dir = 0; dir < 3; dir++) {
-            if (dir == 1 && c->ft)
-                CK(theta_fourier(c, 0, 0, c->fj_first[b], c->fj_first_u[b], c->job_first_n));
-            else
-                CK(launch_contract_tc(dir, 0, c->d, c->tcjobs + c->tc_first[b][dir], c->job_first_n, c->tc_img[dir], tf32,
-                                      c->r_scale, c->tc_err, c->stream));
-            c->launches_tmp++;
-        }
-        CK(launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d1), 3 * c->d.P, N_D1 + c->pp.glm, c->stream));
-        c->launches_tmp++;
-        if (c->pp.glm) {
-            CK(launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->divB), c->d.P, 1, c->stream));
-            if (c->d.E > 1) c->launches_tmp++;
-        }
-        return GRMHD_OK;
-    }
+// First derivatives from buffer b.  part 0: the BSSN fields (+ psi) and their interface
+// means; part 1: the flux divergence (+ the field divergence with GLM), which needs the
+// fluxes of k_prep.
+static int enqueue_first_derivs(grmhd_ctx* c, int b, int part) {
+    const int nB = N_D1 + c->pp.glm, off = part == 0 ? 0 : nB, n = part == 0 ? nB : c->job_first_n - nB;
+    const int mixed = c->opts.precision > 0, tf32 = c->opts.precision == 2;
     for (int dir = 0; dir < 3; dir++) {
-        if (dir == 1 && c->ft) CK(theta_fourier(c, 0, -1, c->fj_first[b], c->fj_first_u[b], c->job_first_n));
-        else CK(contract(c, dir, 0, c->jobs + c->job_first[b][dir], c->job_first_n));
+        if (dir == 1 && c->ft)
+            CK(theta_fourier(c, 0, mixed ? 0 : -1, c->fj_first[b] + off, c->fj_first_u[b] + off, n, off));
+        else if (mixed)
+            CK(launch_contract_tc(dir, 0, c->d, c->tcjobs + c->tc_first[b][dir] + off, n, c->tc_img[dir], tf32,
+                                  c->r_scale, c->tc_err, c->stream));
+        else
+            CK(contract(c, dir, 0, c->jobs + c->job_first[b][dir] + off, n));
         c->launches_tmp++;
     }
-    CK(launch_iface_avg(c->d, c->d1, 3 * c->d.P, N_D1 + c->pp.glm, c->stream));
-    c->launches_tmp++;
-    if (c->pp.glm) {
-        CK(launch_iface_avg(c->d, c->divB, c->d.P, 1, c->stream));
+    if (part == 0) {
+        if (mixed) CK(launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d1), 3 * c->d.P, nB, c->stream));
+        else CK(launch_iface_avg(c->d, c->d1, 3 * c->d.P, nB, c->stream));
+        c->launches_tmp++;
+    } else if (c->pp.glm) {
+        if (mixed) CK(launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->divB), c->d.P, 1, c->stream));
+        else CK(launch_iface_avg(c->d, c->divB, c->d.P, 1, c->stream));
         if (c->d.E > 1) c->launches_tmp++;
     }
     return GRMHD_OK;
@@ -856,7 +870,7 @@ static int enqueue_second_derivs(grmhd_ctx* c) {
         const int n[3] = {3 * N_D2, 2 * N_D2, N_D2};
         for (int dir = 0; dir < 3; dir++) {
             if (dir == 1 && c->ft)
-                CK(theta_fourier(c, 0, 1, c->fj_second, c->fj_second_u, n[dir]));
+                CK(theta_fourier(c, 0, 1, c->fj_second, c->fj_second_u, n[dir], c->job_first_n));
             else
                 CK(launch_contract_tc(dir, 1, c->d, c->tcjobs + c->tc_second[dir], n[dir], c->tc_img[dir], tf32,
                                       c->r_scale, c->tc_err, c->stream));
@@ -868,7 +882,8 @@ static int enqueue_second_derivs(grmhd_ctx* c) {
         return GRMHD_OK;
     }
     for (int dir = 0; dir < 3; dir++) {
-        if (dir == 1 && c->ft) CK(theta_fourier(c, 0, -1, c->fj_second, c->fj_second_u, c->job_second_n[dir]));
+        if (dir == 1 && c->ft)
+            CK(theta_fourier(c, 0, -1, c->fj_second, c->fj_second_u, c->job_second_n[dir], c->job_first_n));
         else CK(contract(c, dir, 0, c->jobs + c->job_second[dir], c->job_second_n[dir]));
         c->launches_tmp++;
     }
@@ -880,15 +895,34 @@ static int enqueue_second_derivs(grmhd_ctx* c) {
 
 // one RHS evaluation on state buffer b (Us); output per RKCoef; pp selects the halves of
 // a split step (evolve_metric / evolve_fluid)
+// the calls between construction and destruction enqueue on stream s
+struct OnStream {
+    grmhd_ctx* c;
+    cudaStream_t saved;
+    OnStream(grmhd_ctx* c_, cudaStream_t s) : c(c_), saved(c_->stream) { c->stream = s; }
+    ~OnStream() { c->stream = saved; }
+};
+
 static int enqueue_stage(grmhd_ctx* c, int b, RKCoef co, double* out, const PhysParams& pp) {
+    // Two independent chains until the right-hand side: the BSSN derivatives (first
+    // derivatives of the metric fields, interface means, second derivatives; they read only
+    // the state) on the side stream, the primitive recovery and the flux divergence on the
+    // main stream.  They load different units (tensor / integer pipes against the FP64 pipe).
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->s2, c->ev_fork, 0));
+    int st;
+    {
+        OnStream on(c, c->s2);
+        st = enqueue_first_derivs(c, b, 0);
+        if (!st && pp.evolve_metric) st = enqueue_second_derivs(c);
+        if (!st) CK(cudaEventRecord(c->ev_join, c->s2));
+    }
+    if (st) return st;
     CK(launch_prep(c->d, pp, c->U[b], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream));
     c->launches_tmp++;
-    int st = enqueue_first_derivs(c, b);
+    st = enqueue_first_derivs(c, b, 1);
     if (st) return st;
-    if (pp.evolve_metric) {
-        st = enqueue_second_derivs(c);
-        if (st) return st;
-    }
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     CK(launch_rhs(c->d, pp, c->U[0], c->U[b], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
                   c->divF, c->divB, c->opts.precision > 0, c->r_scale, c->dt, co, out, c->acc, c->stream));
     c->launches_tmp++;
@@ -1370,7 +1404,7 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
                 int dir = k - 5;
                 const int nj[3] = {3 * N_D2, 2 * N_D2, N_D2};
                 if (dir == 1 && c->ft) {
-                    e = theta_fourier(c, 0, mixed ? 1 : -1, c->fj_second, c->fj_second_u, nj[dir]);
+                    e = theta_fourier(c, 0, mixed ? 1 : -1, c->fj_second, c->fj_second_u, nj[dir], c->job_first_n);
                     fl[k] = (mixed ? tc_flops(c, dir) : contraction_flops(c, dir, 0)) * nj[dir];
                     by[k] = (double)P * nj[dir] * (mixed ? 8.0 : 16.0);
                 } else if (mixed) {
