@@ -54,16 +54,49 @@ WORKLOADS = {
 DT_SCALE = {"c2f": 1e-3}
 
 
+def rank_batch(n, rank):
+    """The rank's own batch: n independent instances drawn from the batch generator with
+    seeds disjoint from every other rank's (rank 0 has the single-GPU batch).  Per-GPU work
+    stays fixed as ranks are added (weak scaling); the ranks exchange nothing but the
+    timing."""
+    from workloads import batch_configs
+    from workloads.synth import BATCH_BASE_SEED
+    return batch_configs(n, base_seed=BATCH_BASE_SEED + n * rank)
+
+
+def combine(ms_local, units_local, world):
+    """Whole-job figures from every rank's timed region: the slowest rank's time and the
+    units (point-updates) of all ranks; returns (ms_max, units_total, value per second).
+    Uses the initialised default process group when world > 1."""
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        dev = "cuda" if tdist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+        u = torch.tensor([float(units_local)], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        tdist.all_reduce(u, op=tdist.ReduceOp.SUM)
+        ms_max, units = float(t.item()), float(u.item())
+    else:
+        ms_max, units = float(ms_local), float(units_local)
+    return ms_max, units, units / (ms_max * 1e-3)
+
+
 def run_batch(args):
     """Batched workload: instances grouped by shape, each group one element-concatenated
-    grid; value = aggregate point-updates/s, also instance-steps/s."""
+    grid; value = aggregate point-updates/s, also instance-steps/s.  With N ranks every rank
+    advances its own 256-instance batch (disjoint seeds; no collective on the data path)."""
     import torch
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
     import paper_2508_18221_gb300 as pkg
-    from workloads import batch_configs, primitive_profiles
-    cfgs = batch_configs(256)
+    from workloads import primitive_profiles
+    cfgs = rank_batch(256, rank)
     desc, nsteps = WORKLOADS["c4"]
     stream = torch.cuda.Stream()
     batch = pkg.Batch([pkg.make_structs(c, precision=args.precision) for c in cfgs], stream.cuda_stream)
@@ -94,25 +127,36 @@ def run_batch(args):
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
+    if dist_on:
+        tdist.barrier()
+    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             one(evs[k])
         torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    value = npts * RHS_PER_STEP * nsteps * args.steps / (ms * 1e-3)
+    if dist_on:
+        tdist.barrier()
+    ms_local = sum(a.elapsed_time(b) for a, b in evs)
+    ms, units, value = combine(ms_local, npts * RHS_PER_STEP * nsteps * args.steps, world)
+    n_inst = len(cfgs) * world
     line = {"metric": "batched " + metric_name(args.precision), "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE[args.precision],
             "data": "synthetic (seeded Bondi-like profiles, splitmix64 noise)",
-            "config": {"workload": desc, "precision": args.precision, "instances": len(cfgs),
-                       "nodes": npts, "groups": batch.num_groups(),
-                       "instance_steps_per_s": len(cfgs) * nsteps * args.steps / (ms * 1e-3)},
+            "config": {"workload": desc, "precision": args.precision, "instances": n_inst,
+                       "nodes": int(round(units / (RHS_PER_STEP * nsteps * args.steps))),
+                       "groups_rank0": batch.num_groups(),
+                       "parallelism": f"{world} rank(s), 256 independent instances each",
+                       "instance_steps_per_s": n_inst * nsteps * args.steps / (ms * 1e-3)},
             "gpu_launches": batch.launch_count() * nsteps * args.steps,
             "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     batch.close()
+    if dist_on:
+        tdist.destroy_process_group()
 
 
 def metric_name(precision):
@@ -385,12 +429,7 @@ def run_gpu(args):
     if dist_on:
         tdist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist_on:
-        tdist.all_reduce(ms_t, op=tdist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    units = P * RHS_PER_STEP * nsteps * args.steps * world
-    value = units / (ms_max * 1e-3)
+    ms_max, units, value = combine(ms, P * RHS_PER_STEP * nsteps * args.steps, world)
 
     # end to end through the C ABI with host buffers (pinned)
     host_in = torch.empty(pkg.NV * P, dtype=torch.float64).pin_memory()

@@ -183,7 +183,10 @@ def horizon_radius(M: float, a: float) -> float:
     return M + math.sqrt(M * M - a * a)
 
 
-def batch_configs(n: int = 256, base_seed: int = 1004 * 10 ** 4):
+BATCH_BASE_SEED = 1004 * 10 ** 4
+
+
+def batch_configs(n: int = 256, base_seed: int = BATCH_BASE_SEED):
     """Uneven batch of independent instances: spin a ~ U[0, 0.99], element count
     U{2..8}, order N in {8,12,16,24,32} (N_r = N_theta = N), N_phi in {16,32,64},
     r in [0.9 r_h(a), 50], Bondi-like power-law matter with rho0 ~ U[5e-3, 2e-2]."""
