@@ -34,6 +34,8 @@ DTYPE = {0: "f64", 1: "f64 state + bf16x3/f32 derivatives", 2: "f64 state + tf32
 WORKLOADS = {
     "c2": ("c2: a=0.9, 8 radial elements r in [1.5,100], N_r=24 N_theta=32 N_phi=64, "
            "100 SSP-RK3 steps (CFL 0.3) per bench step in one CUDA graph", 100),
+    "c1": ("c1: a=0.5, 2 radial elements r in [1.8,20], N_r=N_theta=12 N_phi=16 (4,608 nodes, "
+           "latency-bound), 100 SSP-RK3 steps (CFL 0.3) per bench step in one CUDA graph", 100),
     "c2f": ("c2f: c2's instance on the paper's Fourier theta basis (N_theta=32 uniform "
             "pole-free nodes over [0, pi], double-Fourier parity extension), a=0.9, 8 radial "
             "elements r in [1.5,100], N_r=24 N_phi=64, 100 SSP-RK3 steps per bench "
@@ -449,6 +451,21 @@ def run_gpu(args):
     # live per-kernel timing (CUDA events on the library's stream): every RHS class runs
     # RHS_PER_STEP times per step, every filter class once.  The roofline is reported for
     # the kernel with the largest time per step.
+    # bare right-hand side through the C ABI (no graph, device buffers): one stage's launches
+    rhs_out = torch.empty_like(U0)
+    ctx.set_state(U0, True)
+    for _ in range(3):
+        ctx.rhs(rhs_out, True)
+    torch.cuda.synchronize()
+    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_rhs = 20
+    e_a.record(stream)
+    for _ in range(n_rhs):
+        ctx.rhs(rhs_out, True)
+    e_b.record(stream)
+    torch.cuda.synchronize()
+    rhs_call = P * n_rhs * world / (e_a.elapsed_time(e_b) * 1e-3)
+
     ctx.set_state(U0, True)
     kt_full = ctx.kernel_times(reps=5)
     roof = roofline(kt_full, P, args.precision, _kernel_names(cfg, args.precision))
@@ -476,6 +493,9 @@ def run_gpu(args):
                         "d2h_bytes_per_step": pkg.NV * P * 8},
                 "gpu_launches": launches_per_step * args.steps,
                 "clocks": clk.summary(),
+                "rhs_call": {"value": rhs_call, "unit": UNIT,
+                             "what": "grmhd_rhs on device buffers, no graph, 20 calls"},
+                "us_per_rk_step": ms_max / args.steps / nsteps * 1e3,
                 "final_diag": {"mass": stats[0], "c2p_floor_points": stats[3]}}
         print(json.dumps(line), flush=True)
     ctx.close()

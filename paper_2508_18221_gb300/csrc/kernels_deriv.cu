@@ -134,6 +134,7 @@ __global__ void k_theta_fold(Dims d, const FoldJob* __restrict__ jobs) {
     T* __restrict__ dst = static_cast<T*>(jb.dst);
     const int h = d.Np / 2;
     const long long half = d.P / 2;
+#pragma unroll 4
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < half;
          t += (long long)gridDim.x * blockDim.x) {
         const long long row = t / h;
@@ -152,6 +153,7 @@ __global__ void k_theta_unfold(Dims d, const FoldJob* __restrict__ jobs) {
     T* __restrict__ dst = static_cast<T*>(jb.dst);
     const int h = d.Np / 2;
     const long long half = d.P / 2;
+#pragma unroll 4
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < half;
          t += (long long)gridDim.x * blockDim.x) {
         const T z0 = src[t], z1 = src[half + t];
@@ -168,8 +170,10 @@ __global__ void k_theta_unfold(Dims d, const FoldJob* __restrict__ jobs) {
     }
 }
 
+// about four elements per thread (the loops above are unrolled by four: their loads are
+// independent, so four are in flight per thread)
 static dim3 fold_grid(const Dims& d, int njobs) {
-    long long nb = (d.P / 2 + 255) / 256;
+    long long nb = (d.P / 2 + 1023) / 1024;
     if (nb > 152LL * 16) nb = 152LL * 16;
     return dim3((unsigned)nb, (unsigned)njobs);
 }
