@@ -177,3 +177,77 @@ def test_fourier_theta_invalid_range(pkg):  # noqa: F811
     grid, phys, opts = pkg.make_structs(cfg)
     with pytest.raises(pkg.GrmhdError, match="-1"):
         pkg.Context(grid, phys, opts, torch.cuda.current_stream().cuda_stream)
+
+
+def test_fourier_theta_batch_equals_single_instances(pkg):  # noqa: F811
+    """Fourier theta instances in a batch (two shape groups, next to a Chebyshev-theta
+    instance, which forms its own group) evolve bit for bit as alone."""
+    import torch
+    cfgs = [_fcfg(a=0.3, n_elem=2, r_min=1.9, r_max=12.0, n_r=8, n_theta=8, n_phi=8),
+            _fcfg(a=0.8, n_elem=3, r_min=1.5, r_max=30.0, n_r=8, n_theta=8, n_phi=8),
+            _fcfg(a=0.6, n_elem=1, r_min=1.7, r_max=8.0, n_r=9, n_theta=6, n_phi=4),
+            config("c1", a=0.5, n_elem=2, n_r=8, n_theta=8, n_phi=8)]
+    structs = [pkg.make_structs(c) for c in cfgs]
+    batch = pkg.Batch(structs)
+    assert batch.num_groups() == 3
+    states, dts = [], []
+    for i, c in enumerate(cfgs):
+        g, p, U = so.workload_state(c)
+        batch.set_state(i, U.reshape(-1).copy(), False)
+        states.append(U)
+        dts.append(5e-4 * (1 + 0.1 * i))
+    batch.step(dts, 2)
+    for i in range(len(cfgs)):
+        got = np.empty(states[i].size)
+        batch.get_state(i, got, False)
+        grid, phys, opts = structs[i]
+        ctx = pkg.Context(grid, phys, opts, torch.cuda.current_stream().cuda_stream)
+        ctx.set_state(torch.from_numpy(states[i].reshape(-1).copy()).cuda(), True)
+        ctx.step(dts[i], 2)
+        ref = np.empty(states[i].size)
+        ctx.get_state(ref, False)
+        ctx.close()
+        np.testing.assert_array_equal(got, ref)
+    batch.close()
+
+
+def test_fourier_theta_glm_mixed_rhs(pkg):  # noqa: F811
+    """GLM cleaning with split-BF16 x3 contractions on the Fourier theta basis: the mixed
+    bar 2e-6."""
+    tp.TENSOR_OF[so.I_PSI] = [so.I_PSI]
+    cfg = _fcfg(n_elem=2, n_r=8, n_theta=10, n_phi=8)
+    g, p, U = _state(cfg, glm=1)
+    U[so.I_PSI] = 1e-4 * np.cos(g.T) * np.cos(g.P) * (g.R / g.R.max())
+    ctx = tp._ctx(pkg, cfg, glm=1, precision=1)
+    R = tp._gpu_rhs(pkg, ctx, U)
+    tp.assert_parity(R, so.rhs(U, g, p), "fourier theta glm mixed rhs", tol=2e-6, U=U, g=g,
+                     groups=((0, 24), (24, 32), (32, 33)))
+    ctx.close()
+
+
+def test_fourier_theta_split_coupling_rk4(pkg):  # noqa: F811
+    """The paper's split loop with RK4 on the Fourier theta basis, two steps."""
+    import torch
+    cfg = _fcfg(n_elem=2, n_r=8, n_theta=10, n_phi=8)
+    g, p, U = _state(cfg, integrator=1, coupling=1)
+    ctx = tp._ctx(pkg, cfg, integrator=1, coupling=1)
+    ctx.set_state(torch.from_numpy(U.reshape(-1).copy()).cuda(), True)
+    dt = 5e-4
+    ctx.step(dt, 2)
+    got = np.empty(U.size)
+    ctx.get_state(got, False)
+    ref = so.rk_step(so.rk_step(U, dt, g, p), dt, g, p)
+    tp.assert_parity(got.reshape(U.shape), ref, "fourier theta split rk4", U=U)
+    ctx.close()
+
+
+@pytest.mark.slow
+def test_fourier_theta_rhs_parity_full_size(pkg):  # noqa: F811
+    """The benchmarked Fourier theta instance (393,216 nodes) in the benchmark's launch
+    configuration: every node of one RHS evaluation against the oracle."""
+    cfg = config("c2f")
+    g, p, U = _state(cfg)
+    ctx = tp._ctx(pkg, cfg)
+    R = tp._gpu_rhs(pkg, ctx, U)
+    tp.assert_parity(R, so.rhs(U, g, p), "fourier theta rhs c2f full size", U=U, g=g)
+    ctx.close()
