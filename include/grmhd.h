@@ -275,6 +275,13 @@ int grmhd_xcts_init(grmhd_ctx* ctx, const double* rho, const double* p, const do
  * operators (radial: per element, one-sided at element ends).  Device pointers. */
 int grmhd_debug_deriv(grmhd_ctx* ctx, const double* in, double* out, int nfields, int dir);
 
+/* Test hook of the device-side wait limits: one digit-slice contraction whose tiles are
+ * withheld, so that every bounded wait of the kernel runs out (about 0.5 s); the CTAs leave,
+ * free their tensor memory and flag the failure, and the call returns GRMHD_ETIMEOUT with the
+ * context still usable (GRMHD_OK would mean the limit did not act; GRMHD_EUNSUPPORTED
+ * without digit-slice operators).  Nothing faults or hangs. */
+int grmhd_debug_wait_timeout(grmhd_ctx* ctx);
+
 /* Test hook: the theta derivative (filter = 0) or the theta filter (filter = 1) of
  * `nfields` canonical fields (device pointers, nfields * num_points doubles each), field f
  * taken with parity[f] = +1 or -1 (host array) under theta_basis 1 (ignored under the

@@ -77,6 +77,7 @@ SIGNATURES = {
     "grmhd_xcts_init": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int, C.c_double, _P, _P, _P]),
     "grmhd_debug_deriv": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
     "grmhd_debug_theta": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(C.c_int), C.c_int]),
+    "grmhd_debug_wait_timeout": (C.c_int, [_P]),
     "grmhd_cfl_dt_noalloc": (C.c_int, [_P, C.c_longlong, C.c_double, C.c_double, _P, _P]),
     "grmhd_strerror": (C.c_char_p, [C.c_int]),
     "grmhd_last_error": (C.c_char_p, [_P]),
@@ -230,6 +231,10 @@ class Context:
 
     def debug_deriv(self, src, dst, nfields: int, direction: int):
         self._chk(self.lib.grmhd_debug_deriv(self.h, _ptr(src), _ptr(dst), nfields, direction))
+
+    def debug_wait_timeout(self):
+        """status of grmhd_debug_wait_timeout (GRMHD_ETIMEOUT expected)"""
+        return int(self.lib.grmhd_debug_wait_timeout(self.h))
 
     def debug_theta(self, src, dst, parities, filter: bool = False):
         """theta derivative (or theta filter) of len(parities) fields, field f with the

@@ -1475,6 +1475,26 @@ extern "C" int grmhd_debug_deriv(grmhd_ctx* c, const double* in, double* out, in
     return GRMHD_OK;
 }
 
+extern "C" int grmhd_debug_wait_timeout(grmhd_ctx* c) {
+    if (!c) return GRMHD_EINVAL;
+    int dir = -1;
+    for (int k = 0; k < 3 && dir < 0; k++)
+        if (c->fx_d[k]) dir = k;
+    if (dir < 0) return set_err(c, GRMHD_EUNSUPPORTED, "no digit-slice contraction in this context (contraction = 1)");
+    DerivJob jb;
+    jb.src = c->U[0]; jb.dst = c->scratch; jb.accumulate = 0; jb.pad = 0;
+    CK(cudaMemcpyAsync(c->jobs + c->job_dbg, &jb, sizeof(jb), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream));
+    CK(launch_contract_fx(dir, c->d, c->jobs + c->job_dbg, 1, c->fx_d[dir], dir == 0 ? c->fx_estride : 0, c->tc_err,
+                          c->stream, 1));
+    int te = 0;
+    CK(cudaMemcpyAsync(&te, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (!te) return GRMHD_OK;
+    CK(cudaMemset(c->tc_err, 0, sizeof(int)));
+    return set_err(c, GRMHD_ETIMEOUT, "a tensor-core contraction wait timed out (requested stall)");
+}
+
 extern "C" int grmhd_debug_theta(grmhd_ctx* c, const double* in, double* out, int nfields, const int* parity,
                                  int filter) {
     if (!c || !in || !out || !parity || nfields < 1 || (filter != 0 && filter != 1)) return GRMHD_EINVAL;

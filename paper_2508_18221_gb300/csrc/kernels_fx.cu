@@ -202,6 +202,7 @@ struct FxParams {
     long long ntiles;        // 128-line tiles of one field
     uint32_t stg_bytes;
     int* err;
+    int stall;               // test of the wait limits: the staging warp issues no copies
 };
 
 template <int DIR>
@@ -378,8 +379,9 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
             FxTile tl;
             int pass, job;
             fx_item<DIR>(fp, d, it, &tl, &pass, &job);
-            fx_stage<DIR>(d, tl, N, fp.jobs[job].src, reinterpret_cast<double*>(sm + b * fp.stg_bytes),
-                          &bars->stg_full[b], lane);
+            if (!fp.stall)
+                fx_stage<DIR>(d, tl, N, fp.jobs[job].src, reinterpret_cast<double*>(sm + b * fp.stg_bytes),
+                              &bars->stg_full[b], lane);
         }
     } else if (warp == 9) {
         // ---------------------------------------------------------------- MMA issue
@@ -694,7 +696,7 @@ cudaError_t fx_init() {
 }
 
 cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int njobs, const uint8_t* img,
-                               long long img_estride, int* err, cudaStream_t s) {
+                               long long img_estride, int* err, cudaStream_t s, int stall) {
     if (njobs <= 0) return cudaSuccess;
     const int N = dir == 0 ? d.Nr : (dir == 1 ? d.Nt : d.Np);
     if (!fx_supported(dir, N)) return cudaErrorNotSupported;
@@ -719,6 +721,7 @@ cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int
     fp.njobs = njobs;
     fp.stg_bytes = fx_stg_bytes(dir, N);
     fp.err = err;
+    fp.stall = stall;
     if (dir == 0) fp.ntiles = (long long)d.E * ((d.NtNp + 127) / 128);
     else if (dir == 1) fp.ntiles = ((long long)d.E * d.Nr * d.Np + 127) / 128;
     else fp.ntiles = (d.P / N + 127) / 128;
