@@ -73,9 +73,9 @@ def _run(pkg, ctx, u, d):
 
 
 def _report(name, value):
-    """measured errors go to gpurun_out/fx_accuracy.json when that folder exists"""
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if not os.path.isdir(out):
+    """measured errors go to fx_accuracy.json in the folder GRMHD_REPORT_DIR names, when set"""
+    out = os.environ.get("GRMHD_REPORT_DIR")
+    if not out or not os.path.isdir(out):
         return
     fn = os.path.join(out, "fx_accuracy.json")
     data = json.load(open(fn)) if os.path.exists(fn) else {}

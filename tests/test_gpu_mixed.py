@@ -128,8 +128,8 @@ def test_precision_variant_report(pkg, capsys):
                 trt.append(float(max(trunc[v] * np.abs(ref[n][v]).max() for v in t) / mx) if mx > 0 else 0.0)
             report[f"p{prec}_n{n}"] = {"l2": l2, "linf": linf, "l2_tensor": l2t, "trunc_tensor": trt}
         ctx.close()
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(out):
+    out = os.environ.get("GRMHD_REPORT_DIR")      # optional folder for the report
+    if out and os.path.isdir(out):
         with open(os.path.join(out, "precision_report_c3.json"), "w") as fh:
             json.dump(report, fh)
     with capsys.disabled():
