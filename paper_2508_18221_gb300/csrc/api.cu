@@ -1549,7 +1549,7 @@ extern "C" const char* grmhd_strerror(int s) {
         case GRMHD_ECUDA: return "CUDA runtime error";
         case GRMHD_ENAN: return "non-finite value in the evolved state";
         case GRMHD_ETIMEOUT: return "device-side wait timed out";
-        case GRMHD_EUNSUPPORTED: return "option not supported by this build";
+        case GRMHD_EUNSUPPORTED: return "option not supported by this library";
         default: return "unknown status";
     }
 }
