@@ -290,8 +290,9 @@ def run_reference(args):
 # (2 x DFMA + DADD + DMUL, smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on.sum)
 # on the 393,216-node workload; the kernels recompute nothing, so this is their algorithmic
 # FP64 work.  The primitive-recovery count is taken inside the time stepping (Newton
-# started from the previous stage's primitives).
-FP64_FLOPS_PER_NODE = {"k_rhs<double>": 2618.0, "k_prep": 1031.0}
+# started from the previous stage's primitives); k_prep<float> (mixed modes) forms the
+# fluxes and T^{mu nu} in FP32, so only its metric and primitive recovery count.
+FP64_FLOPS_PER_NODE = {"k_rhs<double>": 2618.0, "k_prep<double>": 1031.0, "k_prep<float>": 692.0}
 # Nominal FP64 peak of GB300 from its unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop
 # x 2.07 GHz (a probe of dependent DFMA chains on all SMs measured 1.198 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -303,7 +304,8 @@ RHS32_BYTES_PER_NODE = 8 * (32 + 32 + 10) + 4 * (63 + 66 + 8) + 8 * 32
 def _kernel_names(cfg, precision):
     """class of grmhd_kernel_times -> kernel (template instance) that runs it."""
     ns = (cfg.n_r, cfg.n_theta, cfg.n_phi)
-    names = {"prep": "k_prep", "iface_d1": "k_iface_avg", "iface_d2": "k_iface_avg",
+    names = {"prep": "k_prep<double>" if precision == 0 else "k_prep<float>",
+             "iface_d1": "k_iface_avg", "iface_d2": "k_iface_avg",
              "rhs": "k_rhs<double>" if precision == 0 else "k_rhs<float>"}
     for d, dn in enumerate(("r", "theta", "phi")):
         fx = 2 <= ns[d] <= 128 and (d != 2 or ns[d] % 2 == 0)
@@ -374,7 +376,7 @@ def roofline(kt_full, P, precision, names):
 # three stages of a step); absent = not captured since the kernel last changed.
 # k_rhs<double> moves ~2.7 KB per node, about twice its algorithmic bytes: register spills
 # (it is FP64-bound, the bytes are not).
-TRAFFIC = {"k_rhs<double>": 1.08e9, "k_prep": 1.38e8, "k_rhs<float>": 5.95e8}
+TRAFFIC = {"k_rhs<double>": 1.08e9, "k_prep<double>": 1.38e8, "k_prep<float>": 1.39e8, "k_rhs<float>": 5.95e8}
 
 
 def run_gpu(args):

@@ -926,7 +926,8 @@ static int enqueue_stage(grmhd_ctx* c, int b, RKCoef co, double* out, const Phys
         if (!st) CK(cudaEventRecord(c->ev_join, c->s2));
     }
     if (st) return st;
-    CK(launch_prep(c->d, pp, c->U[b], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream));
+    CK(launch_prep(c->d, pp, c->U[b], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream,
+                   c->opts.precision > 0));
     c->launches_tmp++;
     st = enqueue_first_derivs(c, b, 1);
     if (st) return st;
@@ -1396,7 +1397,8 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
         CK(cudaEventRecord(e0, c->stream));
         for (int r = 0; r < reps; r++) {
             cudaError_t e = cudaSuccess;
-            if (k == 0) e = launch_prep(c->d, c->pp, c->U[1], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream);
+            if (k == 0) e = launch_prep(c->d, c->pp, c->U[1], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream,
+                                        mixed);
             else if (k >= 1 && k <= 3) {
                 int dir = k - 1;
                 if (dir == 1 && c->ft) {

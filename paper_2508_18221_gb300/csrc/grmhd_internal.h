@@ -85,7 +85,7 @@ cudaError_t eo_init();
 cudaError_t tc_init();
 cudaError_t launch_prep(const Dims& d, const PhysParams& pp, const double* U, double* prim,
                         double* flux, double* tmn, double* lam, unsigned long long* nfail,
-                        cudaStream_t s);
+                        cudaStream_t s, int fp32_algebra = 0);
 struct RKCoef { double a, b, c, w; int acc_mode; };  // out = a U0 + b Us + c dt L (+acc)
 // d1, d2, divF are double (FP64 mode) or float (deriv_fp32 = 1, mixed modes)
 cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, const double* Us,

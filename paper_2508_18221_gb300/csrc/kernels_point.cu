@@ -186,6 +186,7 @@ __device__ int con2prim_point(double D, const double S_d[3], double tau, const d
 }
 
 // --------------------------------------------------------------------------- k_prep
+template <typename R>
 __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const double* __restrict__ U,
                                               double* __restrict__ prim, double* __restrict__ flux,
                                               double* __restrict__ tmn, double* __restrict__ lam,
@@ -233,56 +234,78 @@ __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const doubl
         prim[5 * P + p] = pr;
         prim[6 * P + p] = W;
 
-        // ---- four-vectors
-        double v_d[3];
-        for (int i = 0; i < 3; i++) v_d[i] = g[i][0] * v[0] + g[i][1] * v[1] + g[i][2] * v[2];
-        double ia = 1.0 / alpha;
-        double u0 = W * ia;
-        double uu[3];
-        for (int i = 0; i < 3; i++) uu[i] = W * (v[i] - beta[i] * ia);
-        double b0 = W * (v_d[0] * B_u[0] + v_d[1] * B_u[1] + v_d[2] * B_u[2]) * ia;
-        double iW = 1.0 / W;
-        double bu[3];
-        for (int i = 0; i < 3; i++) bu[i] = (B_u[i] + alpha * b0 * uu[i]) * iW;
-        double beta_d[3];
+        // ---- four-vectors, fluxes and T^{mu nu} in R: FP64, or FP32 in the mixed modes
+        // (their consumers, the tensor-core contractions and the FP32 right-hand side, keep
+        // about 24 bits); the primitive recovery above stays FP64
+        const R alphaR = (R)alpha, sqgR = (R)sqg, WR = (R)W;
+        R gR[3][3], betaR[3], vR[3], BR[3];
+        for (int i = 0; i < 3; i++) {
+            betaR[i] = (R)beta[i];
+            vR[i] = (R)v[i];
+            BR[i] = (R)B_u[i];
+            for (int j = 0; j < 3; j++) gR[i][j] = (R)g[i][j];
+        }
+        R v_d[3];
+        for (int i = 0; i < 3; i++) v_d[i] = gR[i][0] * vR[0] + gR[i][1] * vR[1] + gR[i][2] * vR[2];
+        R ia = R(1.0) / alphaR;
+        R u0 = WR * ia;
+        R uu[3];
+        for (int i = 0; i < 3; i++) uu[i] = WR * (vR[i] - betaR[i] * ia);
+        R b0 = WR * (v_d[0] * BR[0] + v_d[1] * BR[1] + v_d[2] * BR[2]) * ia;
+        R iW = R(1.0) / WR;
+        R bu[3];
+        for (int i = 0; i < 3; i++) bu[i] = (BR[i] + alphaR * b0 * uu[i]) * iW;
+        R beta_d[3];
         for (int i = 0; i < 3; i++)
-            beta_d[i] = g[i][0] * beta[0] + g[i][1] * beta[1] + g[i][2] * beta[2];
-        double bb_ = beta_d[0] * beta[0] + beta_d[1] * beta[1] + beta_d[2] * beta[2];
-        double g00 = -alpha * alpha + bb_;
-        double bd0 = g00 * b0 + beta_d[0] * bu[0] + beta_d[1] * bu[1] + beta_d[2] * bu[2];
-        double bd[3];
+            beta_d[i] = gR[i][0] * betaR[0] + gR[i][1] * betaR[1] + gR[i][2] * betaR[2];
+        R bb_ = beta_d[0] * betaR[0] + beta_d[1] * betaR[1] + beta_d[2] * betaR[2];
+        R g00 = -alphaR * alphaR + bb_;
+        R bd0 = g00 * b0 + beta_d[0] * bu[0] + beta_d[1] * bu[1] + beta_d[2] * bu[2];
+        R bd[3];
         for (int i = 0; i < 3; i++)
-            bd[i] = beta_d[i] * b0 + g[i][0] * bu[0] + g[i][1] * bu[1] + g[i][2] * bu[2];
-        double b2 = b0 * bd0 + bu[0] * bd[0] + bu[1] * bd[1] + bu[2] * bd[2];
-        double pstar = pr + 0.5 * b2;
-        double rhohs = rho * (1.0 + eps) + pr + b2;   // rho h*
+            bd[i] = beta_d[i] * b0 + gR[i][0] * bu[0] + gR[i][1] * bu[1] + gR[i][2] * bu[2];
+        R b2 = b0 * bd0 + bu[0] * bd[0] + bu[1] * bd[1] + bu[2] * bd[2];
+        R pstar = (R)pr + R(0.5) * b2;
+        R rhohs = (R)rho * (R(1.0) + (R)eps) + (R)pr + b2;   // rho h*
         // conserved variables from the primitives (undensitized)
-        double Dp = rho * W;
-        double Sp[3];
-        for (int j = 0; j < 3; j++) Sp[j] = rhohs * W * W * v_d[j] - alpha * b0 * bd[j];
-        double taup = rhohs * W * W - pstar - alpha * alpha * b0 * b0 - Dp;
+        R Dp = (R)rho * WR;
+        R Sp[3];
+        for (int j = 0; j < 3; j++) Sp[j] = rhohs * WR * WR * v_d[j] - alphaR * b0 * bd[j];
+        // tau = rho h* W^2 - p* - alpha^2 b0^2 - D without its cancellation: with
+        // W^2 - 1 = W^2 v^2 and W - 1 = W^2 v^2 / (W + 1),
+        // tau = rho W (eps W + W^2 v^2 / (W + 1)) + p W^2 v^2 + b^2 (W^2 - 1/2) - alpha^2 b0^2
+        // (tau ~ 1e-3 D for a cold gas: the direct form loses 3 digits, all of FP32's margin)
+        // (FP32 only; FP64 keeps the direct form, which the oracle also uses)
+        R taup;
+        if constexpr (sizeof(R) == 4) {
+            const R Wv2 = WR * WR * (v_d[0] * vR[0] + v_d[1] * vR[1] + v_d[2] * vR[2]);
+            taup = (R)rho * WR * ((R)eps * WR + Wv2 / (WR + R(1.0))) + (R)pr * Wv2 + b2 * (WR * WR - R(0.5)) -
+                   alphaR * alphaR * b0 * b0;
+        } else {
+            taup = rhohs * WR * WR - pstar - alphaR * alphaR * b0 * b0 - Dp;
+        }
         // ---- densitized fluxes [dir][var]
-        double vt[3];
-        for (int i = 0; i < 3; i++) vt[i] = alpha * v[i] - beta[i];
+        R vt[3];
+        for (int i = 0; i < 3; i++) vt[i] = alphaR * vR[i] - betaR[i];
         for (int i = 0; i < 3; i++) {
             double* F = flux + (long long)(i * 8) * P + p;
-            F[0 * P] = sqg * (Dp * vt[i]);
+            F[0 * P] = sqgR * (Dp * vt[i]);
             for (int j = 0; j < 3; j++)
-                F[(1 + j) * P] = sqg * (Sp[j] * vt[i] + (i == j ? alpha * pstar : 0.0) -
-                                        alpha * bd[j] * B_u[i] * iW);
-            F[4 * P] = sqg * (taup * vt[i] + alpha * pstar * v[i] -
-                              alpha * alpha * b0 * B_u[i] * iW);
-            for (int k = 0; k < 3; k++) F[(5 + k) * P] = sqg * (vt[i] * B_u[k] - vt[k] * B_u[i]);
+                F[(1 + j) * P] = sqgR * (Sp[j] * vt[i] + (i == j ? alphaR * pstar : R(0.0)) -
+                                         alphaR * bd[j] * BR[i] * iW);
+            F[4 * P] = sqgR * (taup * vt[i] + alphaR * pstar * vR[i] -
+                               alphaR * alphaR * b0 * BR[i] * iW);
+            for (int k = 0; k < 3; k++) F[(5 + k) * P] = sqgR * (vt[i] * BR[k] - vt[k] * BR[i]);
         }
         // ---- T^{mu nu}
-        double ia2 = ia * ia;
-        double gu[4][4];
+        R ia2 = ia * ia;
+        R gu[4][4];
         gu[0][0] = -ia2;
-        for (int i = 0; i < 3; i++) gu[0][i + 1] = gu[i + 1][0] = beta[i] * ia2;
+        for (int i = 0; i < 3; i++) gu[0][i + 1] = gu[i + 1][0] = betaR[i] * ia2;
         for (int i = 0; i < 3; i++)
-            for (int j = 0; j < 3; j++) gu[i + 1][j + 1] = gi[i][j] - beta[i] * beta[j] * ia2;
-        double u4[4] = {u0, uu[0], uu[1], uu[2]};
-        double b4[4] = {b0, bu[0], bu[1], bu[2]};
+            for (int j = 0; j < 3; j++) gu[i + 1][j + 1] = (R)gi[i][j] - betaR[i] * betaR[j] * ia2;
+        R u4[4] = {u0, uu[0], uu[1], uu[2]};
+        R b4[4] = {b0, bu[0], bu[1], bu[2]};
         int n = 0;
         for (int m = 0; m < 4; m++)
             for (int k = m; k < 4; k++, n++)
@@ -716,10 +739,11 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
 // --------------------------------------------------------------------------- launchers
 cudaError_t launch_prep(const Dims& d, const PhysParams& pp, const double* U, double* prim,
                         double* flux, double* tmn, double* lam, unsigned long long* nfail,
-                        cudaStream_t s) {
+                        cudaStream_t s, int fp32_algebra) {
     int bs = 128;
     long long nb = (d.P + bs - 1) / bs;
-    k_prep<<<(unsigned)nb, bs, 0, s>>>(d, pp, U, prim, flux, tmn, lam, nfail);
+    if (fp32_algebra) k_prep<float><<<(unsigned)nb, bs, 0, s>>>(d, pp, U, prim, flux, tmn, lam, nfail);
+    else k_prep<double><<<(unsigned)nb, bs, 0, s>>>(d, pp, U, prim, flux, tmn, lam, nfail);
     return cudaGetLastError();
 }
 
