@@ -67,3 +67,35 @@ def test_resume_after_destroy(pkg):  # noqa: F811
     ctx.get_state(got, False)
     ctx.close()
     tp.assert_parity(got.reshape(U.shape), ref.reshape(U.shape), "resumed run", tol=1e-11, U=U)
+
+
+def test_unphysical_states_are_floored_not_trapped(pkg):  # noqa: F811
+    """Conserved states with no admissible inversion (tau lowered below the internal
+    energy at a few nodes) injected on the host: the primitive recovery floors eps there,
+    counts the nodes, agrees with the oracle's floored primitives, and a time step stays
+    finite (no trap, no NaN)."""
+    import torch
+    cfg = config("c1", n_elem=2, n_r=8, n_theta=8, n_phi=8)
+    g, p, U = so.workload_state(cfg)
+    bad = U.copy()
+    rng = np.random.default_rng(3)
+    nodes = [tuple(int(rng.integers(0, n)) for n in g.shape) for _ in range(6)]
+    prim0 = so.primitives(U, p)
+    for nd in nodes:
+        D = bad[(so.I_D,) + nd]
+        bad[(so.I_TAU,) + nd] -= 2.0 * prim0["eps"][nd] * D + 0.1 * D
+    ref = so.primitives(bad, p)
+    ctx = tp._ctx(pkg, cfg)
+    ctx.set_state(torch.from_numpy(bad.reshape(-1).copy()).cuda(), True)
+    out = torch.empty(7 * U[0].size, dtype=torch.float64, device="cuda")
+    nf = ctx.con2prim(out, True)
+    P = out.cpu().numpy().reshape((7,) + U.shape[1:])
+    assert nf == int(np.sum(~ref["ok"])) and nf >= len(set(nodes)) - 1
+    assert np.all(np.isfinite(P))
+    np.testing.assert_allclose(P[4], ref["eps"], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(P[0], ref["rho"], rtol=1e-12)
+    ctx.step(1e-4, 1)
+    after = np.empty(U.size)
+    ctx.get_state(after, False)
+    assert np.all(np.isfinite(after))
+    ctx.close()
