@@ -49,27 +49,8 @@ def bssn_rhs(f, d1, d2, matter, gauge=0, eta=2.0):
     gtinv = inv3(gt)
     e4m = np.exp(-4.0 * phi)
     Chr = christoffel3(gt, dgt)                               # Gammatilde^k_ij [k,i,j]
-    Chr_low = np.einsum("...il,...ljk->...ijk", gt, Chr)      # Gammatilde_ijk
-    Gt_d = np.einsum("...jk,...ijk->...i", gtinv, Chr)        # computed Gammatilde^i
     divb = np.einsum("...kk->...", dbeta)
-
-    # conformal Ricci tensor
-    Rt = (-0.5 * np.einsum("...lm,...lmij->...ij", gtinv, ddgt)
-          + 0.5 * (np.einsum("...ki,...jk->...ij", gt, dGt)
-                   + np.einsum("...kj,...ik->...ij", gt, dGt))
-          + 0.5 * (np.einsum("...k,...ijk->...ij", Gt_d, Chr_low)
-                   + np.einsum("...k,...jik->...ij", Gt_d, Chr_low))
-          + np.einsum("...lm,...kli,...jkm->...ij", gtinv, Chr, Chr_low)
-          + np.einsum("...lm,...klj,...ikm->...ij", gtinv, Chr, Chr_low)
-          + np.einsum("...lm,...kim,...klj->...ij", gtinv, Chr, Chr_low))
-    # conformal-factor part
-    DDphi = ddphi - np.einsum("...kij,...k->...ij", Chr, dphi)
-    lap_phi = np.einsum("...lm,...lm->...", gtinv, DDphi)
-    dphi2 = np.einsum("...lm,...l,...m->...", gtinv, dphi, dphi)
-    Rphi = (-2.0 * DDphi - 2.0 * gt * lap_phi[..., None, None]
-            + 4.0 * np.einsum("...i,...j->...ij", dphi, dphi)
-            - 4.0 * gt * dphi2[..., None, None])
-    Ric = Rt + Rphi
+    Ric = ricci_bssn(f, d1, d2)
 
     # physical second covariant derivative of the lapse
     eye = np.eye(3)
@@ -125,6 +106,47 @@ def bssn_rhs(f, d1, d2, matter, gauge=0, eta=2.0):
         out["beta"] = np.zeros_like(beta)
         out["B"] = np.zeros_like(B)
     return out
+
+
+def ricci_bssn(f, d1, d2):
+    """Physical Ricci tensor R_ij = Rtilde_ij + R^phi_ij in BSSN variables (evolved
+    Gammatilde^k in the derivative term, computed Gammatilde^k in the Gammatilde^k
+    Gammatilde_(ij)k term)."""
+    gt, Gt = f["gt"], f["Gt"]
+    dgt, dphi, dGt = d1["gt"], d1["phi"], d1["Gt"]
+    ddgt, ddphi = d2["gt"], d2["phi"]
+    gtinv = inv3(gt)
+    Chr = christoffel3(gt, dgt)                               # Gammatilde^k_ij [k,i,j]
+    Chr_low = np.einsum("...il,...ljk->...ijk", gt, Chr)      # Gammatilde_ijk
+    Gt_d = np.einsum("...jk,...ijk->...i", gtinv, Chr)        # computed Gammatilde^i
+    # conformal Ricci tensor
+    Rt = (-0.5 * np.einsum("...lm,...lmij->...ij", gtinv, ddgt)
+          + 0.5 * (np.einsum("...ki,...jk->...ij", gt, dGt)
+                   + np.einsum("...kj,...ik->...ij", gt, dGt))
+          + 0.5 * (np.einsum("...k,...ijk->...ij", Gt_d, Chr_low)
+                   + np.einsum("...k,...jik->...ij", Gt_d, Chr_low))
+          + np.einsum("...lm,...kli,...jkm->...ij", gtinv, Chr, Chr_low)
+          + np.einsum("...lm,...klj,...ikm->...ij", gtinv, Chr, Chr_low)
+          + np.einsum("...lm,...kim,...klj->...ij", gtinv, Chr, Chr_low))
+    # conformal-factor part
+    DDphi = ddphi - np.einsum("...kij,...k->...ij", Chr, dphi)
+    lap_phi = np.einsum("...lm,...lm->...", gtinv, DDphi)
+    dphi2 = np.einsum("...lm,...l,...m->...", gtinv, dphi, dphi)
+    Rphi = (-2.0 * DDphi - 2.0 * gt * lap_phi[..., None, None]
+            + 4.0 * np.einsum("...i,...j->...ij", dphi, dphi)
+            - 4.0 * gt * dphi2[..., None, None])
+    return Rt + Rphi
+
+
+def hamiltonian(f, d1, d2, rho):
+    """Hamiltonian constraint H = R + K^2 - K_ij K^ij - 16 pi rho in BSSN variables:
+    R = e^{-4 phi} gammatilde^ij R_ij, K_ij K^ij = Atilde_ij Atilde^ij + K^2 / 3, so
+    H = R + (2/3) K^2 - Atilde_ij Atilde^ij - 16 pi rho (rho the Eulerian energy density)."""
+    gtinv = inv3(f["gt"])
+    R = np.exp(-4.0 * f["phi"]) * np.einsum("...ij,...ij->...", gtinv, ricci_bssn(f, d1, d2))
+    At_uu = np.einsum("...ik,...jl,...kl->...ij", gtinv, gtinv, f["At"])
+    AA = np.einsum("...ij,...ij->...", f["At"], At_uu)
+    return R + 2.0 / 3.0 * f["K"] ** 2 - AA - 2.0 * EIGHT_PI * rho
 
 
 def ricci_physical(gam, dgam, ddgam):

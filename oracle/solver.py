@@ -516,7 +516,8 @@ def quadrature_weights(g: Grid):
 
 
 def diagnostics(U, g: Grid, p: Params):
-    """[rest mass, entropy, max |d_i B~^i|, c2p failures, Hamiltonian-constraint RMS].
+    """[rest mass, entropy, max |d_i B~^i|, c2p failures, max |H|, quadrature RMS of H] with
+    H the Hamiltonian constraint.
     Entropy follows the paper's discrete functional E = sum rho s sqrt(gamma) dV with
     s = ln(p / rho^Gamma)/(Gamma-1) and dV the quadrature weight (reading: the paper's
     "cell volume" on spectral nodes).  Parity unpinned for the entropy (the paper
@@ -529,7 +530,23 @@ def diagnostics(U, g: Grid, p: Params):
     s = np.log(prim["p"] / prim["rho"] ** p.gamma_eos) / (p.gamma_eos - 1.0)
     ent = np.sum(w * prim["rho"] * s * sqg)
     divB = g.d_r(U[I_B]) + g.d_t(U[I_B + 1], THETA_PAR[I_B + 1]) + g.d_p(U[I_B + 2])
-    return np.array([mass, ent, np.max(np.abs(divB)), float(np.sum(~prim["ok"]))])
+    H = hamiltonian_constraint(U, g, p, prim)
+    return np.array([mass, ent, np.max(np.abs(divB)), float(np.sum(~prim["ok"])),
+                     np.max(np.abs(H)), np.sqrt(np.sum(w * H * H) / np.sum(w))])
+
+
+def hamiltonian_constraint(U, g: Grid, p: Params, prim=None):
+    """Hamiltonian constraint at every node (the right-hand side's derivatives: radial first
+    derivatives interface-averaged, second derivatives as the compositions of the RHS),
+    with the Eulerian energy density of the matter."""
+    prim = prim if prim is not None else primitives(U, p)
+    f = unpack_bssn(U)
+    gam, _ = metric_from_bssn(f)
+    T = va.stress_energy(prim["rho"], prim["v"], prim["eps"], prim["B"], f["alpha"], f["beta"],
+                         gam, p.gamma_eos)
+    rho_adm = va.matter_3p1(T, f["alpha"], f["beta"], gam)[0]
+    d1, d2 = _derivs(g, U)
+    return bs.hamiltonian(f, _d1_fields(d1), _d2_fields(d2), rho_adm)
 
 
 # ----------------------------------------------------------------- initial data
