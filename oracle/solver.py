@@ -532,7 +532,14 @@ def diagnostics(U, g: Grid, p: Params):
     divB = g.d_r(U[I_B]) + g.d_t(U[I_B + 1], THETA_PAR[I_B + 1]) + g.d_p(U[I_B + 2])
     H = hamiltonian_constraint(U, g, p, prim)
     return np.array([mass, ent, np.max(np.abs(divB)), float(np.sum(~prim["ok"])),
-                     np.max(np.abs(H)), np.sqrt(np.sum(w * H * H) / np.sum(w))])
+                     np.max(np.abs(H)), weighted_rms(H, w)])
+
+
+def weighted_rms(f, w):
+    """Quadrature root mean square sqrt(sum w f^2 / sum w) over every node; w may be
+    broadcast over phi (quadrature_weights), so its sum is taken at f's full shape."""
+    wf = np.broadcast_to(w, f.shape)
+    return np.sqrt(np.sum(wf * f * f) / np.sum(wf))
 
 
 def hamiltonian_constraint(U, g: Grid, p: Params, prim=None):

@@ -78,3 +78,27 @@ def test_diagnostics_report_H():
     g, p, U = so.workload_state(cfg)
     d = so.diagnostics(U, g, p)
     assert d.shape == (6,) and np.isfinite(d).all() and d[4] >= d[5] > 0
+
+
+def test_weighted_rms_is_a_mean_over_every_node():
+    """The RMS of a constant field is its magnitude, a field that is c on one radial element
+    and 0 on the other has RMS c sqrt(V_e / V) with V_e the element's quadrature volume, and
+    no RMS exceeds the maximum (positive weights) -- with the weights broadcast over phi, a
+    sum of w alone would miss the factor N_phi."""
+    cfg = config("c1", n_elem=2, n_r=8, n_theta=8, n_phi=16)
+    g, p, U = so.workload_state(cfg)
+    w = so.quadrature_weights(g)
+    assert np.all(w > 0)
+    shape = U.shape[1:]
+    np.testing.assert_allclose(so.weighted_rms(np.full(shape, -3.0), w), 3.0, rtol=1e-14)
+    f = np.zeros(shape)
+    f[1] = 2.0
+    wf = np.broadcast_to(w, shape)
+    np.testing.assert_allclose(so.weighted_rms(f, w), 2.0 * np.sqrt(wf[1].sum() / wf.sum()),
+                               rtol=1e-14)
+    H = so.hamiltonian_constraint(U, g, p)
+    for e in range(2):
+        assert so.weighted_rms(H[e], w[e]) <= np.abs(H[e]).max() * (1 + 1e-14)
+    d = so.diagnostics(U, g, p)
+    np.testing.assert_allclose(d[4], np.abs(H).max(), rtol=1e-14)
+    np.testing.assert_allclose(d[5], so.weighted_rms(H, w), rtol=1e-14)
