@@ -191,7 +191,10 @@ int grmhd_cfl_dt(grmhd_ctx* ctx, double* dt);
 /* Diagnostics (out[GRMHD_NDIAG]): 0 rest mass sum w D~, 1 entropy sum w rho s sqrt(gamma)
  * with s = ln(p/rho^Gamma)/(Gamma-1) (Methods, "The Entropy Stability and
  * Convergence", quadrature weights as the cell volume), 2 max |d_i(sqrt(gamma) B^i)|,
- * 3 floor/failed points of the last recovery, 4 dt of the last step, 5-7 reserved. */
+ * 3 floor/failed points of the last recovery, 4 dt of the last step, 5 max |H| and 6 the
+ * quadrature RMS of the Hamiltonian constraint H = R + (2/3) K^2 - Atilde_ij Atilde^ij -
+ * 16 pi rho (rho the Eulerian energy density; the right-hand side's derivatives; FP32
+ * algebra in the mixed modes), 7 reserved.  Costs one right-hand-side evaluation. */
 int grmhd_diag(grmhd_ctx* ctx, double out[GRMHD_NDIAG]);
 
 /* Kernel launches issued by the last grmhd_step / grmhd_rhs call (per step / per call). */

@@ -55,6 +55,8 @@ struct grmhd_ctx {
     double* divF;
     double* scratch;         // nv * P
     double* divB;            // d_i (sqrt(gamma) B^i) (GLM only)
+    double* ham;             // Hamiltonian constraint per node (diagnostics)
+    double* ham_out;         // non-null while a diagnostic stage is enqueued: k_rhs writes H there
     int nv;                  // evolved variables: GRMHD_NV, + 1 (psi) with GLM
     double* Dr;              // Nr x Nr reference CGL matrix on [-1, 1]
     double* Dt;              // Nt x Nt Gauss matrix scaled to [theta_min, theta_max]
@@ -238,7 +240,7 @@ static void free_ctx(grmhd_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     double** bufs[] = {&c->U[0], &c->U[1], &c->U[2], &c->acc, &c->prim, &c->flux, &c->tmn, &c->lam,
                        &c->d1, &c->d2, &c->divF, &c->scratch, &c->Dr, &c->Dt, &c->Dp, &c->Fr,
-                       &c->Ft, &c->Fp, &c->r_scale, &c->wq, &c->hmin, &c->dt, &c->diag, &c->divB};
+                       &c->Ft, &c->Fp, &c->r_scale, &c->wq, &c->hmin, &c->dt, &c->diag, &c->divB, &c->ham};
     for (double** b : bufs)
         if (*b) cudaFree(*b);
     for (int k = 0; k < 3; k++) {
@@ -432,6 +434,7 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
     if (glm) AL(c->divB, P);
     AL(c->d2, N_D2 * 6 * P);
     AL(c->divF, 8 * P);
+    AL(c->ham, P);
     AL(c->scratch, nv * P);
     AL(c->Dr, Nr * Nr); AL(c->Dt, Nt * Nt); AL(c->Dp, Np);
     AL(c->Fr, Nr * Nr); AL(c->Ft, Nt * Nt); AL(c->Fp, Np);
@@ -933,7 +936,8 @@ static int enqueue_stage(grmhd_ctx* c, int b, RKCoef co, double* out, const Phys
     if (st) return st;
     CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     CK(launch_rhs(c->d, pp, c->U[0], c->U[b], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
-                  c->divF, c->divB, c->opts.precision > 0, c->r_scale, c->dt, co, out, c->acc, c->stream));
+                  c->divF, c->divB, c->opts.precision > 0, c->r_scale, c->dt, co, out, c->acc, c->stream,
+                  c->ham_out));
     c->launches_tmp++;
     return GRMHD_OK;
 }
@@ -1312,6 +1316,21 @@ extern "C" int grmhd_step(grmhd_ctx* c, double dt, int nsteps, double* dt_used) 
 extern "C" int grmhd_diag(grmhd_ctx* c, double out[GRMHD_NDIAG]) {
     NvtxRange nvtx_range("grmhd_diag");
     if (!c || !out) return GRMHD_EINVAL;
+    // Hamiltonian constraint: one right-hand-side evaluation of the current state with the
+    // metric part always on (its result, written to scratch, is discarded); k_rhs writes H
+    // per node from the Ricci tensor it forms anyway
+    {
+        PhysParams ph = c->pp;
+        ph.evolve_metric = 1;
+        ph.evolve_fluid = 1;
+        const RKCoef co = {0, 0, 0, 0, -1};
+        c->ham_out = c->ham;
+        const long long keep = c->launches_tmp;
+        const int st = enqueue_stage(c, 0, co, c->scratch, ph);
+        c->ham_out = nullptr;
+        c->launches_tmp = keep;
+        if (st) return st;
+    }
     CK(cudaMemsetAsync(c->nfail, 0, sizeof(unsigned long long), c->stream));
     CK(launch_prep(c->d, c->pp, c->U[0], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream));
     // divergence of the densitized field into scratch
@@ -1333,7 +1352,7 @@ extern "C" int grmhd_diag(grmhd_ctx* c, double out[GRMHD_NDIAG]) {
         }
     }
     CK(cudaMemsetAsync(c->diag, 0, sizeof(double) * 8, c->stream));
-    CK(launch_diag(c->d, c->pp, c->U[0], c->prim, c->wq, c->scratch, c->diag, c->stream));
+    CK(launch_diag(c->d, c->pp, c->U[0], c->prim, c->wq, c->scratch, c->diag, c->stream, c->ham));
     double h[8];
     unsigned long long nf = 0;
     double dtv = 0.0;
@@ -1347,6 +1366,8 @@ extern "C" int grmhd_diag(grmhd_ctx* c, double out[GRMHD_NDIAG]) {
     out[2] = h[2];
     out[3] = (double)nf;
     out[4] = dtv;
+    out[5] = h[5];                                    // max |H|
+    out[6] = h[7] > 0.0 ? std::sqrt(h[6] / h[7]) : 0.0;  // quadrature RMS of H
     return GRMHD_OK;
 }
 

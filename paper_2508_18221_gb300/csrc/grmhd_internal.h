@@ -87,12 +87,14 @@ cudaError_t launch_prep(const Dims& d, const PhysParams& pp, const double* U, do
                         double* flux, double* tmn, double* lam, unsigned long long* nfail,
                         cudaStream_t s, int fp32_algebra = 0);
 struct RKCoef { double a, b, c, w; int acc_mode; };  // out = a U0 + b Us + c dt L (+acc)
-// d1, d2, divF are double (FP64 mode) or float (deriv_fp32 = 1, mixed modes)
+// d1, d2, divF are double (FP64 mode) or float (deriv_fp32 = 1, mixed modes); ham != null
+// also writes the Hamiltonian constraint per node (diagnostics)
 cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, const double* Us,
                        const double* prim, const double* flux, const double* tmn,
                        const double* lam, const void* d1, const void* d2,
                        const void* divF, const void* divB, int deriv_fp32, const double* r_scale_dev,
-                       const double* dt_dev, RKCoef co, double* out, double* acc, cudaStream_t s);
+                       const double* dt_dev, RKCoef co, double* out, double* acc, cudaStream_t s,
+                       double* ham = nullptr);
 // tensor-core contraction (kernels_tc.cu); op_img in the kernel's shared-memory layout
 cudaError_t launch_contract_tc(int dir, int in_fp32, const Dims& d, const TcJob* jobs, int njobs,
                                const uint8_t* op_img, int tf32, const double* r_scale, int* err,
@@ -129,7 +131,7 @@ cudaError_t launch_cfl(const Dims& d, int n_inst, const double* U, const double*
                        double* dt_dev, unsigned long long* lam_bits, cudaStream_t s);
 cudaError_t launch_diag(const Dims& d, const PhysParams& pp, const double* U,
                         const double* prim, const double* wq, const double* divB,
-                        double* out_dev, cudaStream_t s);
+                        double* out_dev, cudaStream_t s, const double* ham = nullptr);
 cudaError_t launch_nan_check(long long n, const double* U, int* flag, cudaStream_t s);
 
 // Approximate XCTS initial data (kernels_xcts.cu): operators of the boundary-value problem

@@ -246,10 +246,10 @@ cudaError_t launch_cfl(const Dims& d, int n_inst, const double* U, const double*
 // out[0] += w D~, out[1] += w rho s sqrt(gamma), out[2] = max |divB| (bits)
 __global__ void k_diag(Dims d, PhysParams pp, const double* __restrict__ U,
                        const double* __restrict__ prim, const double* __restrict__ wq,
-                       const double* __restrict__ divB, double* out) {
+                       const double* __restrict__ divB, const double* __restrict__ ham, double* out) {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long P = d.P;
-    double m = 0.0, s = 0.0, db = 0.0;
+    double m = 0.0, s = 0.0, db = 0.0, hm = 0.0, h2 = 0.0, ws = 0.0;
     if (p < P) {
         double e4 = exp(4.0 * U[V_PHI * P + p]);
         const int sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
@@ -263,25 +263,39 @@ __global__ void k_diag(Dims d, PhysParams pp, const double* __restrict__ U,
         m = wq[p] * U[V_D * P + p];
         s = wq[p] * rho * (log(pr / pow(rho, pp.gam)) / (pp.gam - 1.0)) * sqrt(det);
         db = fabs(divB[p]);
+        if (ham) {
+            hm = fabs(ham[p]);
+            h2 = wq[p] * ham[p] * ham[p];
+            ws = wq[p];
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         m += __shfl_xor_sync(0xffffffffu, m, o);
         s += __shfl_xor_sync(0xffffffffu, s, o);
         db = fmax(db, __shfl_xor_sync(0xffffffffu, db, o));
+        hm = fmax(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+        h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+        ws += __shfl_xor_sync(0xffffffffu, ws, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&out[0], m);
         atomicAdd(&out[1], s);
         atomicMax(reinterpret_cast<unsigned long long*>(&out[2]),
                   (unsigned long long)__double_as_longlong(db));
+        if (ham) {
+            atomicMax(reinterpret_cast<unsigned long long*>(&out[5]),
+                      (unsigned long long)__double_as_longlong(hm));
+            atomicAdd(&out[6], h2);
+            atomicAdd(&out[7], ws);
+        }
     }
 }
 
 cudaError_t launch_diag(const Dims& d, const PhysParams& pp, const double* U,
                         const double* prim, const double* wq, const double* divB,
-                        double* out_dev, cudaStream_t s) {
+                        double* out_dev, cudaStream_t s, const double* ham) {
     int bs = 256;
-    k_diag<<<(unsigned)((d.P + bs - 1) / bs), bs, 0, s>>>(d, pp, U, prim, wq, divB, out_dev);
+    k_diag<<<(unsigned)((d.P + bs - 1) / bs), bs, 0, s>>>(d, pp, U, prim, wq, divB, ham, out_dev);
     return cudaGetLastError();
 }
 

@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const doubl
 // The FP32-algebra instance is capped at 170 registers (3 blocks per SM): its spills cost
 // less than the latency its extra warps hide (measured 0.23 -> 0.18 ms on 393k nodes); the
 // FP64 instance is FP64-pipe bound and keeps 255.
-template <typename DT, typename R>
+template <typename DT, typename R, bool HAM>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, PhysParams pp, const double* __restrict__ U0,
                                              const double* __restrict__ Us,
                                              const double* __restrict__ prim,
@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
                                              const DT* __restrict__ divB,
                                              const double* __restrict__ r_scale,
                                              const double* __restrict__ dt_dev, RKCoef co,
-                                             double* __restrict__ out, double* __restrict__ acc) {
+                                             double* __restrict__ out, double* __restrict__ acc,
+                                             double* __restrict__ ham) {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long P = d.P;
     if (p >= P) return;
@@ -657,6 +658,13 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
                 }
             rhs[V_PHI] = -alpha * K * sixth + (beta[0] * dphi[0] + beta[1] * dphi[1] + beta[2] * dphi[2]) +
                          divb * sixth;
+            // diagnostics only: the Hamiltonian constraint R + (2/3) K^2 - Atilde.Atilde - 16 pi rho,
+            // with R = gamma^ij R_ij = (e^{-4 phi} trX + trDDal) / alpha + 8 pi S (trX, trDDal
+            // as above: the same Ricci tensor, no extra derivative)
+            // (a separate instance, HAM = true, so that the stepping kernel carries none of it)
+            if constexpr (HAM)
+                ham[p] = (double)((e4mr * trX + trDDal) / alpha + R(8.0) * PI * Str + two3 * K * K - AA -
+                                  R(16.0) * PI * rho_m);
             rhs[V_K] = -trDDal + alpha * (AA + K * K3) + R(4.0) * PI * alpha * (rho_m + Str) +
                        (beta[0] * dK[0] + beta[1] * dK[1] + beta[2] * dK[2]);
             // Gammatilde
@@ -751,17 +759,20 @@ cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, co
                        const double* prim, const double* flux, const double* tmn,
                        const double* lam, const void* d1, const void* d2,
                        const void* divF, const void* divB, int deriv_fp32, const double* r_scale_dev,
-                       const double* dt_dev, RKCoef co, double* out, double* acc, cudaStream_t s) {
+                       const double* dt_dev, RKCoef co, double* out, double* acc, cudaStream_t s,
+                       double* ham) {
     int bs = 128;
     long long nb = (d.P + bs - 1) / bs;
-    if (deriv_fp32)
-        k_rhs<float, float><<<(unsigned)nb, bs, 0, s>>>(d, pp, U0, Us, prim, flux, tmn, lam, (const float*)d1,
-                                                 (const float*)d2, (const float*)divF, (const float*)divB,
-                                                 r_scale_dev, dt_dev, co, out, acc);
-    else
-        k_rhs<double, double><<<(unsigned)nb, bs, 0, s>>>(d, pp, U0, Us, prim, flux, tmn, lam, (const double*)d1,
-                                                  (const double*)d2, (const double*)divF, (const double*)divB,
-                                                  r_scale_dev, dt_dev, co, out, acc);
+#define RHS_ARGS(T) d, pp, U0, Us, prim, flux, tmn, lam, (const T*)d1, (const T*)d2, (const T*)divF, \
+                    (const T*)divB, r_scale_dev, dt_dev, co, out, acc, ham
+    if (deriv_fp32) {
+        if (ham) k_rhs<float, float, true><<<(unsigned)nb, bs, 0, s>>>(RHS_ARGS(float));
+        else k_rhs<float, float, false><<<(unsigned)nb, bs, 0, s>>>(RHS_ARGS(float));
+    } else {
+        if (ham) k_rhs<double, double, true><<<(unsigned)nb, bs, 0, s>>>(RHS_ARGS(double));
+        else k_rhs<double, double, false><<<(unsigned)nb, bs, 0, s>>>(RHS_ARGS(double));
+    }
+#undef RHS_ARGS
     return cudaGetLastError();
 }
 

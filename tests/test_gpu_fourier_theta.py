@@ -168,6 +168,9 @@ def test_fourier_theta_init_cfl_diag(pkg):  # noqa: F811
     ref = so.diagnostics(U, g, p)
     np.testing.assert_allclose(dg[0], ref[0], rtol=1e-13)
     np.testing.assert_allclose(dg[1], ref[1], rtol=1e-12)
+    assert ref[4] > 0
+    np.testing.assert_allclose(dg[5], ref[4], rtol=1e-9)
+    np.testing.assert_allclose(dg[6], ref[5], rtol=1e-9)
     ctx.close()
 
 

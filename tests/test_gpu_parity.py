@@ -230,6 +230,18 @@ def test_cfl_and_diagnostics(pkg):
     np.testing.assert_allclose(dg[0], ref[0], rtol=1e-13)
     np.testing.assert_allclose(dg[1], ref[1], rtol=1e-12)
     assert dg[2] <= 1e-12 * np.abs(U[so.I_B:so.I_B + 3]).max() * 100
+    # Hamiltonian constraint: max |H| and its quadrature RMS (a residual of O(1) cancelling
+    # curvature terms: the RHS bar relative to the largest term, here max |H| itself)
+    assert ref[4] > 0
+    np.testing.assert_allclose(dg[5], ref[4], rtol=1e-9)
+    np.testing.assert_allclose(dg[6], ref[5], rtol=1e-9)
+    # the diagnostic leaves the state untouched
+    after = np.empty(U.size)
+    ctx.get_state(after, False)
+    np.testing.assert_array_equal(after, U.reshape(-1))
+    dg2 = ctx.diag()
+    # (sums by atomic adds: equal up to their order)
+    np.testing.assert_allclose(np.asarray(dg2)[[0, 1, 2, 5, 6]], np.asarray(dg)[[0, 1, 2, 5, 6]], rtol=1e-13)
     ctx.close()
 
 
