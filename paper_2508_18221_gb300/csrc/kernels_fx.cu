@@ -253,7 +253,10 @@ __device__ __forceinline__ void fx_stage(const Dims& d, const FxTile& tl, int N,
 //              exponents, then the seven digit slices of each 16-wide K chunk into a
 //              two-stage ring of A buffers;
 //   warps 4-7  epilogue: thread m reads TMEM lane m (warp w serves lane quadrant w & 3),
-//              combines the five accumulators and stores the FP64 results;
+//              combines the five accumulators and stores the FP64 results, 8 columns
+//              at a time; TMEM goes back to the MMA warp once the last block is in
+//              registers, before its arithmetic (the epilogue's latency, not its
+//              instruction count, sets the rate at which items pass through TMEM);
 //   warp 8     stages the FP64 tiles in shared memory (bulk copies);
 //   warp 9     one thread loads the operator digits and issues the MMAs.
 // A work item is (field, 128-line tile, column pass); the CTA walks items blockIdx.x,
@@ -540,11 +543,11 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
             FxTile tl;
             int pass, job;
             fx_item<DIR>(fp, d, it, &tl, &pass, &job);
+            const DerivJob jb = fp.jobs[job];  // loaded before the waits
             const int t = k & 1;
             if (!bwait(&bars->el_ready[t], (uint32_t)((k >> 1) & 1), abort_flag)) break;
             if (!bwait(&bars->acc_full, (uint32_t)(k & 1), abort_flag)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const DerivJob jb = fp.jobs[job];
             const bool valid = m < tl.nlines;
             long long base, stride;
             if (DIR == 0) {
@@ -575,6 +578,17 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
                 }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 const int c0 = pass * Npp + cb;  // output column of r[.][0]
+                int X[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) X[j] = EL + sF[t * 128 + c0 + j] - 2096;
+                if (cb + 8 >= Npp) {
+                    // every accumulator column has been read, and the row exponents too:
+                    // hand TMEM (and this set of sEL, sF) back before the last block's
+                    // arithmetic, so that the next item's MMAs start under it
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    __syncwarp();
+                    if (lane == 0) barrive(&bars->acc_empty[t]);
+                }
                 if (valid) {
                     double v[8];
 #pragma unroll
@@ -582,7 +596,7 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
                         const long long R = combine(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]),
                                                     __uint_as_float(r[2][j]), __uint_as_float(r[3][j]),
                                                     __uint_as_float(r[4][j]), wide);
-                        v[j] = scale_int(R, EL + sF[t * 128 + c0 + j] - 2096);
+                        v[j] = scale_int(R, X[j]);
                     }
                     if (line_bad)
 #pragma unroll
@@ -599,9 +613,6 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
                     }
                 }
             }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncwarp();
-            if (lane == 0) barrive(&bars->acc_empty[t]);
         }
     }
 
