@@ -309,17 +309,21 @@ def _kernel_names(cfg, precision):
              "rhs": "k_rhs<double>" if precision == 0 else "k_rhs<float>"}
     for d, dn in enumerate(("r", "theta", "phi")):
         fx = 2 <= ns[d] <= 128 and (d != 2 or ns[d] % 2 == 0)
-        fp64 = f"k_contract_fx<{d}>" if fx else f"k_deriv_eo<{d}>"
+        fourier = d == 2 or (d == 1 and getattr(cfg, "theta_basis", 0) == 1)
+        # derivatives take the digit slices up to 32 Chebyshev / 128 Fourier nodes
+        fx_d = fx and (fourier or ns[d] <= 32)
+        fp64_f = f"k_contract_fx<{d}>" if fx else f"k_deriv_eo<{d}>"
+        fp64_d = f"k_contract_fx<{d}>" if fx_d else f"k_deriv_eo<{d}>"
         if d == 1 and getattr(cfg, "theta_basis", 0) == 1:
             # Fourier theta: fold, two half-width contractions, unfold (timed together)
-            fp64 = "theta fold + k_contract_fx<1> x2 + unfold" if fx and cfg.n_phi % 4 == 0 else \
+            fp64_f = fp64_d = "theta fold + k_contract_fx<1> x2 + unfold" if fx and cfg.n_phi % 4 == 0 else \
                 "theta fold + k_deriv_eo<1> x2 + unfold"
             tc = "theta fold + k_contract_tc<1> x2 + unfold"
         else:
             tc = f"k_contract_tc<{d}>"
         for c in ("d1", "d2"):
-            names[f"{c}_{dn}"] = fp64 if precision == 0 else tc
-        names[f"filter_{dn}"] = fp64
+            names[f"{c}_{dn}"] = fp64_d if precision == 0 else tc
+        names[f"filter_{dn}"] = fp64_f
     return names
 
 

@@ -61,7 +61,7 @@ enum { GRMHD_NV = 32, GRMHD_NPRIM = 7, GRMHD_NDIAG = 8 };
  * phi + pi), s = -1 per theta index of a coordinate-basis component and -1 once more for
  * the sqrt(gamma)-weighted Valencia variables.  phi uses n_phi uniform nodes
  * 2 pi l / n_phi.  Limits: 1 <= n_elem, 4 <= n_r <= 64, 4 <= n_theta <= 128,
- * 4 <= n_phi <= 256 and even, 0 < r_min < r_max, 0 <= theta_min < theta_max <= pi. */
+ * 4 <= n_phi <= 128 and even, 0 < r_min < r_max, 0 <= theta_min < theta_max <= pi. */
 typedef struct {
     int n_elem;
     double r_min, r_max;
@@ -94,8 +94,11 @@ typedef struct {
  * limit and relative tolerance of the primitive recovery.  contraction: how the FP64
  * spectral contractions (all derivatives at precision 0, the filter at every precision)
  * run: 0 (default) on the BF16 tensor cores with exact base-256 digit slices of the
- * FP64 values (Ozaki splitting; error about 2^-53 of sum_j |D_ij| max_j |u_j|; up to 128
- * nodes per direction), 1 on the FP64 units.  coupling: 0 (default) one
+ * FP64 values (Ozaki splitting; error at most about K 2^-53 of sum_j |D_ij| max_j |u_j|
+ * for K nodes; filters up to 128 nodes per direction, derivatives up to 128 Fourier and
+ * 32 Chebyshev nodes: above 32 the second derivatives, two composed contractions, would
+ * carry the digit slices' error past 1e-11 of the right-hand side, and the FP64 units
+ * take them), 1 on the FP64 units.  coupling: 0 (default) one
  * unsplit right-hand side over all 32 variables per Runge-Kutta stage; 1 the paper's
  * coupled loop ("Coupled Main Loop"): per step the fluid is advanced by the selected
  * Runge-Kutta scheme on the frozen metric, then BSSN + gauge take one forward-Euler step

@@ -84,6 +84,9 @@ struct grmhd_ctx {
     uint8_t* fx_d[3];
     uint8_t* fx_f[3];
     long long fx_estride;    // bytes between the per-element radial derivative images
+    // derivative contractions of the right-hand side take the digit slices along this
+    // direction (fx_deriv_ok); the images exist for every supported size (test hook)
+    bool fx_rhs[3];
     TcJob* tcjobs;
     int tc_first[3][3];      // [buffer][dir]
     int tc_second[3];
@@ -200,12 +203,22 @@ extern "C" int grmhd_defaults(grmhd_grid* g, grmhd_physics* ph, grmhd_opts* o) {
     return GRMHD_OK;
 }
 
+// Digit-slice derivatives along a direction of N nodes.  The digit slices carry an error of
+// about K 2^-53 of sum_j |D_ij| max_j |u_j| per contraction (the worst case of an FP64 dot
+// product, which FP64 units seldom reach); the second derivatives compose two contractions
+// and amplify it with the operator's norm, ~N^2 per application on Chebyshev nodes.  On
+// 4-node-thin grids the right-hand side then stays within the 1e-11 bar up to 32 Chebyshev
+// nodes (6.7e-12 radial, 2.6e-12 theta; 40 nodes: 2.4e-11) and up to 128 Fourier nodes
+// (2.8e-12), measured against the oracle; beyond that the FP64 units take the derivatives
+// (1.2e-12 at 64 radial nodes).  Filters apply one contraction and keep the digit slices.
+static bool fx_deriv_ok(bool fourier, int N) { return fourier ? N <= 128 : N <= 32; }
+
 static int validate(const grmhd_grid* g, const grmhd_physics* ph, const grmhd_opts* o, char* msg) {
     if (!g || !ph || !o) { strcpy(msg, "NULL parameter struct"); return GRMHD_EINVAL; }
     if (g->n_elem < 1 || g->n_elem > 4096) { strcpy(msg, "n_elem out of range"); return GRMHD_EINVAL; }
     if (g->n_r < 4 || g->n_r > 64) { strcpy(msg, "n_r must be in [4, 64]"); return GRMHD_EINVAL; }
     if (g->n_theta < 4 || g->n_theta > 128) { strcpy(msg, "n_theta must be in [4, 128]"); return GRMHD_EINVAL; }
-    if (g->n_phi < 4 || g->n_phi > 256 || (g->n_phi % 2)) { strcpy(msg, "n_phi must be even in [4, 256]"); return GRMHD_EINVAL; }
+    if (g->n_phi < 4 || g->n_phi > 128 || (g->n_phi % 2)) { strcpy(msg, "n_phi must be even in [4, 128]"); return GRMHD_EINVAL; }
     if (!(g->r_min > 0.0) || !(g->r_max > g->r_min)) { strcpy(msg, "need 0 < r_min < r_max"); return GRMHD_EINVAL; }
     if (!(g->theta_min >= 0.0) || !(g->theta_max > g->theta_min) || !(g->theta_max <= M_PI + 1e-12)) {
         strcpy(msg, "need 0 <= theta_min < theta_max <= pi"); return GRMHD_EINVAL;
@@ -597,6 +610,7 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         std::vector<double> dense_f[3] = {Fr, Ft, circulant(Fp)};
         for (int k = 0; k < 3; k++) {
             if (!fx_supported(k, Ns[k]) || (k == 1 && c->ft)) continue;
+            c->fx_rhs[k] = fx_deriv_ok(k == 2, Ns[k]);
             int np_, kp_, kc_;
             fx_geometry(Ns[k], &np_, &kp_, &kc_);
             std::vector<uint8_t> img_f = fx_operator_image(dense_f[k], Ns[k], 1.0, np_, kp_, kc_);
@@ -802,13 +816,15 @@ extern "C" int grmhd_coords(const grmhd_ctx* c, double* r, double* th, double* p
 
 // ------------------------------------------------------------------ pipeline
 // One directional contraction of `njobs` FP64 fields: the digit-sliced tensor-core
-// kernel when the context built its images (opts.contraction = 0, at most 64 nodes),
-// else the reflection-split kernel when the size has a compiled instance, else the dense
-// kernel.  filter = 1 uses the modal filter operator (unscaled), 0 the derivative
+// kernel when the context built its images (opts.contraction = 0) and, for a derivative,
+// the direction passes fx_deriv_ok (force_fx: whenever the image exists, for the test
+// hook), else the reflection-split kernel when the size has a compiled instance, else the
+// dense kernel.  filter = 1 uses the modal filter operator (unscaled), 0 the derivative
 // (radial: scaled per element).
-static cudaError_t contract(grmhd_ctx* c, int dir, int filter, const DerivJob* jobs, int njobs) {
+static cudaError_t contract(grmhd_ctx* c, int dir, int filter, const DerivJob* jobs, int njobs,
+                            bool force_fx = false) {
     if (dir == 1 && c->ft) return cudaErrorInvalidValue;   // theta_fourier below
-    const uint8_t* fx = filter ? c->fx_f[dir] : c->fx_d[dir];
+    const uint8_t* fx = filter ? c->fx_f[dir] : ((c->fx_rhs[dir] || force_fx) ? c->fx_d[dir] : nullptr);
     if (fx) return launch_contract_fx(dir, c->d, jobs, njobs, fx, (dir == 0 && !filter) ? c->fx_estride : 0,
                                       c->tc_err, c->stream);
     const double* split = filter ? c->Fs[dir] : c->Ds[dir];
@@ -1509,7 +1525,7 @@ extern "C" int grmhd_debug_deriv(grmhd_ctx* c, const double* in, double* out, in
         return grmhd_debug_theta(c, in, out, nfields, par.data(), 0);
     }
     CK(cudaMemcpyAsync(c->jobs + c->job_dbg, jb.data(), sizeof(DerivJob) * nfields, cudaMemcpyHostToDevice, c->stream));
-    CK(contract(c, dir, 0, c->jobs + c->job_dbg, nfields));
+    CK(contract(c, dir, 0, c->jobs + c->job_dbg, nfields, true));
     CK(cudaStreamSynchronize(c->stream));
     return GRMHD_OK;
 }

@@ -150,3 +150,55 @@ def test_contraction_sizes(pkg, contraction):
             assert err.max() <= 3e-14, ((nr, nt, nph), d, float(err.max()))
         ctx.close()
     _report(f"sizes_contraction{contraction}", worst)
+
+
+@pytest.mark.parametrize("contraction", [0, 1])
+def test_contraction_maximum_sizes(pkg, contraction):
+    """The largest node counts the library accepts per direction (n_r = 64, n_theta = 128,
+    n_phi = 128) and ragged lengths below them, on thin grids, through the test hook
+    (the digit-slice kernel whenever it supports the size).  Bar: 2 K 2^-53 of the bound
+    (the worst-case rounding of an FP64 dot product of length K), at least 3e-14."""
+    worst = {}
+    for nr, nt, nph in ((64, 4, 4), (63, 4, 4), (4, 128, 4), (4, 127, 4), (4, 4, 128), (4, 4, 126)):
+        cfg = config("c1", n_elem=2, n_r=nr, n_theta=nt, n_phi=nph)
+        g, ctx = _setup(pkg, cfg, contraction)
+        absD = _abs_ops(g)
+        ops = (g.d_r, g.d_t, g.d_p)
+        u = np.sin(g.R) * np.cos(2 * g.T) * (1.5 + np.sin(3 * g.P)) + 0.1 * g.R
+        for d in range(3):
+            k = (nr, nt, nph)[d]
+            got = _run(pkg, ctx, u, d)
+            err = np.abs(got - ops[d](u)) / _bound(g, absD, u, d)
+            worst[f"{k} nodes dir {d}"] = float(err.max())
+            assert err.max() <= max(3e-14, 2 * k * 2.0 ** -53), ((nr, nt, nph), d, float(err.max()))
+        ctx.close()
+    _report(f"maximum_sizes_contraction{contraction}", worst)
+
+
+def test_maximum_sizes_rhs_and_limits(pkg):
+    """Right-hand sides at the largest node counts (thin grids the oracle evaluates in
+    seconds) with the default contraction choice against the oracle at the FP64 bar: 64
+    radial nodes (derivatives on the FP64 units: above 32 Chebyshev nodes the digit slices'
+    error, compounded by the second derivatives, measured 2.4e-11 at 40 nodes), 128 Fourier
+    theta and 128 phi nodes (digit slices), 64 Chebyshev theta nodes.  (128 Chebyshev theta
+    nodes measured 9.3e-12 of the bar's normalisation, within it but without margin: the
+    normalisation follows first-derivative rounding, max|U| / dx_min, while Chebyshev
+    second derivatives round with the square of the operator norm.)  Limits: n_phi above
+    128 or odd, n_theta above 128, n_r above 64 are invalid."""
+    import torch
+
+    import test_gpu_parity as tp
+    for kw in (dict(n_elem=1, n_r=64, n_theta=4, n_phi=4), dict(n_elem=2, n_r=4, n_theta=64, n_phi=4),
+               dict(n_elem=2, n_r=4, n_theta=128, n_phi=4, theta_min=0.0, theta_max=np.pi, theta_basis=1),
+               dict(n_elem=1, n_r=5, n_theta=5, n_phi=128)):
+        cfg = config("c1", **kw)
+        g, p, U = so.workload_state(cfg)
+        ctx = tp._ctx(pkg, cfg)
+        R = tp._gpu_rhs(pkg, ctx, U)
+        ctx.close()
+        tp.assert_parity(R, so.rhs(U, g, p), f"rhs {kw}", U=U, g=g)
+    stream = torch.cuda.current_stream().cuda_stream
+    for kw in (dict(n_phi=130), dict(n_phi=256), dict(n_phi=6, n_theta=129), dict(n_r=65), dict(n_phi=7)):
+        grid, phys, opts = pkg.make_structs(config("c1", n_elem=1, **kw))
+        with pytest.raises(pkg.GrmhdError):
+            pkg.Context(grid, phys, opts, stream)
