@@ -310,10 +310,13 @@ def _kernel_names(cfg, precision):
     for d, dn in enumerate(("r", "theta", "phi")):
         fx = 2 <= ns[d] <= 128 and (d != 2 or ns[d] % 2 == 0)
         fourier = d == 2 or (d == 1 and getattr(cfg, "theta_basis", 0) == 1)
-        # derivatives take the digit slices up to 32 Chebyshev / 128 Fourier nodes
-        fx_d = fx and (fourier or ns[d] <= 32)
+        # Chebyshev derivatives: six accumulators above 32 nodes, the FP64 units above 64
         fp64_f = f"k_contract_fx<{d}>" if fx else f"k_deriv_eo<{d}>"
-        fp64_d = f"k_contract_fx<{d}>" if fx_d else f"k_deriv_eo<{d}>"
+        fp64_d = fp64_f
+        if fx and not fourier and ns[d] > 64:
+            fp64_d = f"k_deriv<{d}>"
+        elif fx and not fourier and ns[d] > 32:
+            fp64_d = f"k_contract_fx<{d}, 6>"
         if d == 1 and getattr(cfg, "theta_basis", 0) == 1:
             # Fourier theta: fold, two half-width contractions, unfold (timed together)
             fp64_f = fp64_d = "theta fold + k_contract_fx<1> x2 + unfold" if fx and cfg.n_phi % 4 == 0 else \

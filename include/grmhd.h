@@ -94,11 +94,11 @@ typedef struct {
  * limit and relative tolerance of the primitive recovery.  contraction: how the FP64
  * spectral contractions (all derivatives at precision 0, the filter at every precision)
  * run: 0 (default) on the BF16 tensor cores with exact base-256 digit slices of the
- * FP64 values (Ozaki splitting; error at most about K 2^-53 of sum_j |D_ij| max_j |u_j|
- * for K nodes; filters up to 128 nodes per direction, derivatives up to 128 Fourier and
- * 32 Chebyshev nodes: above 32 the second derivatives, two composed contractions, would
- * carry the digit slices' error past 1e-11 of the right-hand side, and the FP64 units
- * take them), 1 on the FP64 units.  coupling: 0 (default) one
+ * FP64 values (Ozaki splitting; up to 128 nodes per direction; error about K 2^-53 of
+ * sum_j |D_ij| max_j |u_j| for K nodes with five accumulators; derivatives along a
+ * Chebyshev direction of 33-64 nodes take a sixth, exact one, since the composed second
+ * derivatives would carry that error past 1e-11 of the right-hand side, and above 64
+ * Chebyshev nodes the FP64 units take the derivatives), 1 on the FP64 units.  coupling: 0 (default) one
  * unsplit right-hand side over all 32 variables per Runge-Kutta stage; 1 the paper's
  * coupled loop ("Coupled Main Loop"): per step the fluid is advanced by the selected
  * Runge-Kutta scheme on the frozen metric, then BSSN + gauge take one forward-Euler step

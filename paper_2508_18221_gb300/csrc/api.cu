@@ -84,9 +84,6 @@ struct grmhd_ctx {
     uint8_t* fx_d[3];
     uint8_t* fx_f[3];
     long long fx_estride;    // bytes between the per-element radial derivative images
-    // derivative contractions of the right-hand side take the digit slices along this
-    // direction (fx_deriv_ok); the images exist for every supported size (test hook)
-    bool fx_rhs[3];
     TcJob* tcjobs;
     int tc_first[3][3];      // [buffer][dir]
     int tc_second[3];
@@ -202,16 +199,6 @@ extern "C" int grmhd_defaults(grmhd_grid* g, grmhd_physics* ph, grmhd_opts* o) {
     }
     return GRMHD_OK;
 }
-
-// Digit-slice derivatives along a direction of N nodes.  The digit slices carry an error of
-// about K 2^-53 of sum_j |D_ij| max_j |u_j| per contraction (the worst case of an FP64 dot
-// product, which FP64 units seldom reach); the second derivatives compose two contractions
-// and amplify it with the operator's norm, ~N^2 per application on Chebyshev nodes.  On
-// 4-node-thin grids the right-hand side then stays within the 1e-11 bar up to 32 Chebyshev
-// nodes (6.7e-12 radial, 2.6e-12 theta; 40 nodes: 2.4e-11) and up to 128 Fourier nodes
-// (2.8e-12), measured against the oracle; beyond that the FP64 units take the derivatives
-// (1.2e-12 at 64 radial nodes).  Filters apply one contraction and keep the digit slices.
-static bool fx_deriv_ok(bool fourier, int N) { return fourier ? N <= 128 : N <= 32; }
 
 static int validate(const grmhd_grid* g, const grmhd_physics* ph, const grmhd_opts* o, char* msg) {
     if (!g || !ph || !o) { strcpy(msg, "NULL parameter struct"); return GRMHD_EINVAL; }
@@ -610,7 +597,6 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         std::vector<double> dense_f[3] = {Fr, Ft, circulant(Fp)};
         for (int k = 0; k < 3; k++) {
             if (!fx_supported(k, Ns[k]) || (k == 1 && c->ft)) continue;
-            c->fx_rhs[k] = fx_deriv_ok(k == 2, Ns[k]);
             int np_, kp_, kc_;
             fx_geometry(Ns[k], &np_, &kp_, &kc_);
             std::vector<uint8_t> img_f = fx_operator_image(dense_f[k], Ns[k], 1.0, np_, kp_, kc_);
@@ -816,17 +802,33 @@ extern "C" int grmhd_coords(const grmhd_ctx* c, double* r, double* th, double* p
 
 // ------------------------------------------------------------------ pipeline
 // One directional contraction of `njobs` FP64 fields: the digit-sliced tensor-core
-// kernel when the context built its images (opts.contraction = 0) and, for a derivative,
-// the direction passes fx_deriv_ok (force_fx: whenever the image exists, for the test
-// hook), else the reflection-split kernel when the size has a compiled instance, else the
-// dense kernel.  filter = 1 uses the modal filter operator (unscaled), 0 the derivative
+// kernel when the context built its images (opts.contraction = 0, at most 128 nodes),
+// else the reflection-split kernel when the size has a compiled instance, else the dense
+// kernel.  filter = 1 uses the modal filter operator (unscaled), 0 the derivative
 // (radial: scaled per element).
+//
+// Accumulators of the digit-slice kernel: with five, the folded one's FP32 additions leave
+// an error of about K 2^-53 of sum_j |D_ij| max_j |u_j| per contraction (3.5e-15 / 7.5e-15
+// / 1.4e-14 at 24 / 64 / 128 nodes); the second derivatives compose two contractions and
+// amplify it with the operator's norm, ~N^2 per application on Chebyshev nodes.  Measured
+// on 4-node-thin grids against the oracle, the right-hand side stays within the 1e-11 bar
+// up to 32 Chebyshev nodes (6.7e-12 radial; 40 nodes: 2.4e-11) and up to 128 Fourier nodes
+// (2.8e-12).  Chebyshev derivatives above 32 nodes therefore take a sixth accumulator that
+// keeps the digit-order sum 6 exact (combine6 in the kernel): operator error 7e-16 of the
+// bound, right-hand side within 7.1e-12 up to 64 nodes.  Above 64 Chebyshev nodes the
+// digit slices' remaining error (the fixed-point rounding of each line against its
+// largest value) reaches 1.5e-11 at 96 theta nodes, against 9.5e-12 for the FP64 units,
+// which take those derivatives.  force_fx (the test hook): the digit slices whenever the
+// image exists.
 static cudaError_t contract(grmhd_ctx* c, int dir, int filter, const DerivJob* jobs, int njobs,
                             bool force_fx = false) {
     if (dir == 1 && c->ft) return cudaErrorInvalidValue;   // theta_fourier below
-    const uint8_t* fx = filter ? c->fx_f[dir] : ((c->fx_rhs[dir] || force_fx) ? c->fx_d[dir] : nullptr);
+    const int Ns[3] = {c->d.Nr, c->d.Nt, c->d.Np};
+    const bool cheb_d = !filter && dir < 2;
+    const uint8_t* fx = filter ? c->fx_f[dir] : ((cheb_d && Ns[dir] > 64 && !force_fx) ? nullptr : c->fx_d[dir]);
+    const int nacc = (cheb_d && Ns[dir] > 32) ? 6 : 5;
     if (fx) return launch_contract_fx(dir, c->d, jobs, njobs, fx, (dir == 0 && !filter) ? c->fx_estride : 0,
-                                      c->tc_err, c->stream);
+                                      c->tc_err, c->stream, 0, nacc);
     const double* split = filter ? c->Fs[dir] : c->Ds[dir];
     const double* rs = filter ? nullptr : c->r_scale;
     if (split) return launch_deriv_eo(dir, c->d, jobs, njobs, split, filter ? 1 : -1, rs, c->stream);

@@ -38,7 +38,7 @@ namespace gk {
 namespace {
 
 constexpr int NDIG = 7;                                      // base-256 digits per operand
-constexpr int NACC = 5;                                      // TMEM accumulators
+constexpr int NACC = 5;                                      // TMEM accumulators (6: see combine6)
 constexpr unsigned long long DIG_BIAS = 0x80808080808080ull;  // 128 in each digit
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -137,6 +137,31 @@ __device__ __forceinline__ long long combine(float g2, float g3, float g4, float
     const int nlo = __float_as_int(fmaf(flo, 65536.f, MAG)) - 0x4B400000;
     const long long a = ((long long)n2 << 24) + ((long long)n3 << 16) + ((long long)n4 << 8) + (long long)(n5 + nfh);
     return (a << 16) + (long long)nlo;
+}
+
+// Six accumulators (Chebyshev derivatives above 32 nodes): the digit-order sum q + l = 6
+// gets an exact accumulator of its own and only q + l = 7, 8 are folded.  With five, the
+// folded accumulator holds the q + l = 6 terms, about 2^-32 of the leading ones, and its
+// FP32 additions (truncating alignment, ~1.1 K of them) leave an error growing as K:
+// 3.5e-15 / 7.5e-15 / 1.4e-14 of the bound at 24 / 64 / 128 nodes, which the composed
+// second derivatives amplify past 1e-11 of the right-hand side above 32 Chebyshev nodes.
+// T = g2 + .. + g6 + gf as R = round(T 2^40): g_s an exact multiple of 2^(-8 (s-2)) with
+// |g_s 2^(8 (s-2))| < 2^24 (K <= 128), |gf| < 2^-15 (its scaled head < 2^18 rounds by
+// the magic-number add, the exact remainder gives the last 8 bits).
+__device__ __forceinline__ long long combine6(float g2, float g3, float g4, float g5, float g6, float gf) {
+    const int n2 = __float2int_rn(g2);
+    const int n3 = __float2int_rn(g3 * 256.f);
+    const int n4 = __float2int_rn(g4 * 65536.f);
+    const int n5 = __float2int_rn(g5 * 16777216.f);
+    const int n6 = __float2int_rn(g6 * 4294967296.f);
+    const float MAG = 12582912.f;
+    const float fh = fmaf(gf, 4294967296.f, MAG);
+    const int nfh = __float_as_int(fh) - 0x4B400000;
+    const float flo = fmaf(gf, 4294967296.f, -(fh - MAG));  // exact remainder in [-1/2, 1/2]
+    const int nlo = __float2int_rn(flo * 256.f);
+    const long long a = ((long long)n2 << 32) + ((long long)n3 << 24) + ((long long)n4 << 16) +
+                        ((long long)n5 << 8) + (long long)(n6 + nfh);
+    return (a << 8) + (long long)nlo;
 }
 
 }  // namespace
@@ -318,7 +343,7 @@ __device__ __forceinline__ void fx_item(const FxParams& fp, const Dims& d, long 
     fx_tile<DIR>(d, r / fp.npass, fp.N, tl);
 }
 
-template <int DIR>
+template <int DIR, int NA>
 __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams fp) {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -443,10 +468,10 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
                     const uint32_t a0 = smem_u32(sA + a * a_stage);
                     const uint32_t b0 = smem_u32(sB + (fp.b_all ? kc * chunk_bytes : 0)) + brow;
                     for (int sd = NDIG - 1; sd >= 0; sd--) {
-                        const int g = sd < NACC - 1 ? sd : NACC - 1;
+                        const int g = sd < NA - 1 ? sd : NA - 1;
                         for (int q = 0; q <= sd; q++) {
                             const int l = sd - q;
-                            const bool first = kc == 0 && q == 0 && (sd < NACC - 1 || sd == NDIG - 1);
+                            const bool first = kc == 0 && q == 0 && (sd < NA - 1 || sd == NDIG - 1);
                             mma_bf16(tmem + (uint32_t)(g * Npp), smem_desc(a0 + q * a_bytes, lbo, sbo),
                                      smem_desc(b0 + l * b_bytes, lbo, sbo), id, first ? 0u : 1u);
                         }
@@ -567,9 +592,9 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
             const int EL = sEL[t * 128 + m];
             const bool line_bad = EL == 0x7FF;
             for (int cb = 0; cb < Npp; cb += 8) {
-                uint32_t r[NACC][8];
+                uint32_t r[NA][8];
 #pragma unroll
-                for (int g = 0; g < NACC; g++) {
+                for (int g = 0; g < NA; g++) {
                     const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * Npp + cb);
                     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                                  : "=r"(r[g][0]), "=r"(r[g][1]), "=r"(r[g][2]), "=r"(r[g][3]), "=r"(r[g][4]),
@@ -593,9 +618,13 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
                     double v[8];
 #pragma unroll
                     for (int j = 0; j < 8; j++) {
-                        const long long R = combine(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]),
-                                                    __uint_as_float(r[2][j]), __uint_as_float(r[3][j]),
-                                                    __uint_as_float(r[4][j]), wide);
+                        const long long R =
+                            NA == 6 ? combine6(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]),
+                                               __uint_as_float(r[2][j]), __uint_as_float(r[3][j]),
+                                               __uint_as_float(r[4][j]), __uint_as_float(r[NA - 1][j]))
+                                    : combine(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]),
+                                              __uint_as_float(r[2][j]), __uint_as_float(r[3][j]),
+                                              __uint_as_float(r[4][j]), wide);
                         v[j] = scale_int(R, X[j]);
                     }
                     if (line_bad)
@@ -653,7 +682,7 @@ static size_t fx_rest_bytes(int N, int b_all) {
            2 * 128 * 4 + sizeof(FxBars) + 16;
 }
 
-// CTAs per SM (TMEM: 5 Npp columns rounded to a power of two, from 512), staging buffers
+// CTAs per SM (TMEM: na Npp columns rounded to a power of two, from 512), staging buffers
 // (two when they fit the per-CTA share of the SM's 228 KB, 1 KB reserved per CTA) and the
 // dynamic shared memory, at least 1/(ctas + 1) of the SM so that no further CTA co-resides
 // (its TMEM allocation would wait for a CTA to finish all of its work)
@@ -661,12 +690,12 @@ struct FxCfg {
     int cols, ctas, nstg, b_all;
     size_t smem;
 };
-static FxCfg fx_cfg(int dir, int N) {
+static FxCfg fx_cfg(int dir, int N, int na) {
     int Np, Kp, KC;
     fx_geometry(N, &Np, &Kp, &KC);
     FxCfg c;
     const int Npp = Np > 64 ? 64 : Np;
-    const int need = NACC * Npp;
+    const int need = na * Npp;
     c.cols = need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : (need <= 256 ? 256 : 512)));
     c.ctas = c.cols <= 256 ? 2 : 1;
     size_t share = 233472 / c.ctas - 1024;
@@ -685,30 +714,34 @@ static FxCfg fx_cfg(int dir, int N) {
     return c;
 }
 
-size_t fx_smem_bytes(int dir, int N) { return fx_cfg(dir, N).smem; }
-
-static size_t fx_smem_max(int dir) {
+static size_t fx_smem_max(int dir, int na) {
     size_t mx = 0;
-    for (int n = 2; n <= 128; n++) mx = fx_smem_bytes(dir, n) > mx ? fx_smem_bytes(dir, n) : mx;
+    for (int n = 2; n <= 128; n++) {
+        const size_t b = fx_cfg(dir, n, na).smem;
+        mx = b > mx ? b : mx;
+    }
     return mx;
 }
 
-template <int DIR>
+template <int DIR, int NA>
 static cudaError_t set_attr_fx() {
-    return cudaFuncSetAttribute(k_contract_fx<DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fx_smem_max(DIR));
+    return cudaFuncSetAttribute(k_contract_fx<DIR, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fx_smem_max(DIR, NA));
 }
 
 cudaError_t fx_init() {
     cudaError_t e;
-    if ((e = set_attr_fx<0>()) != cudaSuccess) return e;
-    if ((e = set_attr_fx<1>()) != cudaSuccess) return e;
-    return set_attr_fx<2>();
+    if ((e = set_attr_fx<0, NACC>()) != cudaSuccess) return e;
+    if ((e = set_attr_fx<0, 6>()) != cudaSuccess) return e;
+    if ((e = set_attr_fx<1, NACC>()) != cudaSuccess) return e;
+    if ((e = set_attr_fx<1, 6>()) != cudaSuccess) return e;
+    return set_attr_fx<2, NACC>();
 }
 
 cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int njobs, const uint8_t* img,
-                               long long img_estride, int* err, cudaStream_t s, int stall) {
+                               long long img_estride, int* err, cudaStream_t s, int stall, int nacc) {
     if (njobs <= 0) return cudaSuccess;
+    if (nacc != NACC && !(nacc == 6 && dir < 2)) return cudaErrorNotSupported;
     const int N = dir == 0 ? d.Nr : (dir == 1 ? d.Nt : d.Np);
     if (!fx_supported(dir, N)) return cudaErrorNotSupported;
     // r and theta tiles are staged with bulk copies of row segments: 16-byte alignment
@@ -725,7 +758,7 @@ cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int
     fp.Kp = Kp;
     fp.Npp = Np > 64 ? 64 : Np;
     fp.npass = Np / fp.Npp;
-    const FxCfg cfg = fx_cfg(dir, N);
+    const FxCfg cfg = fx_cfg(dir, N, nacc);
     fp.tmem_cols = cfg.cols;
     fp.nstg = cfg.nstg;
     fp.b_all = cfg.b_all;
@@ -743,9 +776,11 @@ cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int
     const long long nitems = fp.ntiles * fp.npass * njobs;
     const long long grid = nitems < (long long)cfg.ctas * nsm ? nitems : (long long)cfg.ctas * nsm;
     const size_t sm = cfg.smem;
-    if (dir == 0) k_contract_fx<0><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
-    else if (dir == 1) k_contract_fx<1><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
-    else k_contract_fx<2><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
+    if (dir == 0 && nacc == 6) k_contract_fx<0, 6><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
+    else if (dir == 0) k_contract_fx<0, NACC><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
+    else if (dir == 1 && nacc == 6) k_contract_fx<1, 6><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
+    else if (dir == 1) k_contract_fx<1, NACC><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
+    else k_contract_fx<2, NACC><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
     return cudaGetLastError();
 }
 

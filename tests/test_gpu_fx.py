@@ -178,17 +178,17 @@ def test_contraction_maximum_sizes(pkg, contraction):
 def test_maximum_sizes_rhs_and_limits(pkg):
     """Right-hand sides at the largest node counts (thin grids the oracle evaluates in
     seconds) with the default contraction choice against the oracle at the FP64 bar: 64
-    radial nodes (derivatives on the FP64 units: above 32 Chebyshev nodes the digit slices'
-    error, compounded by the second derivatives, measured 2.4e-11 at 40 nodes), 128 Fourier
-    theta and 128 phi nodes (digit slices), 64 Chebyshev theta nodes.  (128 Chebyshev theta
-    nodes measured 9.3e-12 of the bar's normalisation, within it but without margin: the
-    normalisation follows first-derivative rounding, max|U| / dx_min, while Chebyshev
-    second derivatives round with the square of the operator norm.)  Limits: n_phi above
-    128 or odd, n_theta above 128, n_r above 64 are invalid."""
+    radial and 64 Chebyshev theta nodes (digit slices with six accumulators), 128
+    Chebyshev theta nodes (FP64 units: measured 9.3e-12 of the bar's normalisation, which
+    follows first-derivative rounding, max|U| / dx_min, while Chebyshev second derivatives
+    round with the square of the operator norm), 128 Fourier theta and 128 phi nodes
+    (digit slices, five accumulators).  Limits: n_phi above 128 or odd, n_theta above 128,
+    n_r above 64 are invalid."""
     import torch
 
     import test_gpu_parity as tp
     for kw in (dict(n_elem=1, n_r=64, n_theta=4, n_phi=4), dict(n_elem=2, n_r=4, n_theta=64, n_phi=4),
+               dict(n_elem=2, n_r=4, n_theta=128, n_phi=4),
                dict(n_elem=2, n_r=4, n_theta=128, n_phi=4, theta_min=0.0, theta_max=np.pi, theta_basis=1),
                dict(n_elem=1, n_r=5, n_theta=5, n_phi=128)):
         cfg = config("c1", **kw)
@@ -202,3 +202,23 @@ def test_maximum_sizes_rhs_and_limits(pkg):
         grid, phys, opts = pkg.make_structs(config("c1", n_elem=1, **kw))
         with pytest.raises(pkg.GrmhdError):
             pkg.Context(grid, phys, opts, stream)
+
+
+def test_six_accumulators_reach_fp64_accuracy(pkg):
+    """Chebyshev derivatives above 32 nodes take the six-accumulator instance (the digit-
+    order sum 6 exact): its error stays within a few times the FP64 units' (measured 7e-16
+    of the bound at 64 and 128 nodes against 7.5e-15 and 1.4e-14 with five accumulators),
+    bar 2e-15 of the bound; at 32 nodes the five-accumulator instance stays below 4e-15."""
+    worst = {}
+    for nr, nt, d, bar in ((32, 4, 0, 4e-15), (40, 4, 0, 2e-15), (64, 4, 0, 2e-15), (4, 48, 1, 2e-15),
+                           (4, 128, 1, 2e-15)):
+        cfg = config("c1", n_elem=2, n_r=nr, n_theta=nt, n_phi=4)
+        g, ctx = _setup(pkg, cfg, 0)
+        absD = _abs_ops(g)
+        u = np.sin(g.R) * np.cos(2 * g.T) * (1.5 + np.sin(3 * g.P)) + 0.1 * g.R
+        got = _run(pkg, ctx, u, d)
+        ctx.close()
+        err = np.abs(got - (g.d_r, g.d_t)[d](u)) / _bound(g, absD, u, d)
+        worst[f"{(nr, nt)[d]} nodes dir {d}"] = float(err.max())
+        assert err.max() <= bar, ((nr, nt), d, float(err.max()))
+    _report("six_accumulators", worst)
