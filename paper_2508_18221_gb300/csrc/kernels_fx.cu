@@ -13,12 +13,15 @@
 //     a fifth.  The tensor core adds terms of different magnitude with a truncating
 //     alignment, so only the fifth accumulator rounds, about 2^-23 of its own size (2^-40
 //     below the leading term) per addition (measured: folding from q + l = 5 on instead
-//     costs 1e-12 of the bound below);
+//     costs 1e-12 of the bound below).  Over the ~1.1 K additions of a K-long line that
+//     leaves about K 2^-53 of the bound; the NA = 6 instance gives q + l = 6 an exact
+//     accumulator too (7e-16 of the bound at K = 64 and 128), for derivatives that are
+//     composed into second derivatives on Chebyshev nodes;
 //   * the epilogue adds the five accumulators as a 64-bit integer and builds the IEEE
 //     double with integer instructions (no FP64 arithmetic: GB300 runs FP64 at ~2 fused
 //     operations per SM clock, integer and FP32 work at 64-128).
-// Error: below 2e-14 of sum_j |D_ij| max_j |u_j| (tested), a few times the worst-case
-// bound of an FP64 dot product of these lengths.  A line holding Inf or NaN yields NaN
+// Error: below 2e-14 of sum_j |D_ij| max_j |u_j| with five accumulators (tested), about the
+// worst-case bound of an FP64 dot product of these lengths; about 1e-15 with six.  A line holding Inf or NaN yields NaN
 // outputs; values below 2^-1022 (subnormals) enter as zero.
 //
 // Work item: 128 lines (tile) of one field (job) x K <= 128, one pass of at most 64 output
