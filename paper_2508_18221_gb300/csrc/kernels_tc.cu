@@ -56,6 +56,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
     return done != 0;
 }
 
+// FP64 -> FP32, rounded to nearest even, with integer instructions: the same result as
+// __double2float_rn, which GB300 runs on its FP64 pipe (at ~1/64 of the integer rate; the
+// conversions of the line tile kept that pipe 24-26 % busy).  Zero, values outside FP32's
+// normal range, Inf and NaN take the hardware conversion.
+__device__ __forceinline__ float d2f_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const uint32_t s = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+    if (e >= 1 && e <= 254) {
+        const uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);      // leading 23 mantissa bits
+        const uint32_t rest = lo & 0x1FFFFFFFu, half = 0x10000000u;  // the 29 dropped bits
+        // a carry out of the mantissa steps the exponent (to Inf above the largest float)
+        return __uint_as_float((s | ((uint32_t)e << 23) | m) + ((rest > half || (rest == half && (m & 1u))) ? 1u : 0u));
+    }
+    return (b << 1) == 0 ? __uint_as_float(s) : __double2float_rn(x);
+}
+__device__ __forceinline__ float to_f32(double x) { return d2f_rn(x); }
+__device__ __forceinline__ float to_f32(float x) { return x; }
+
 __device__ __forceinline__ void mma_issue(int tf32, uint32_t tmem, uint64_t da, uint64_t db, uint32_t id,
                                           uint32_t acc) {
     if (tf32)
@@ -124,7 +144,7 @@ __global__ void __launch_bounds__(128) k_contract_tc(Dims d, const TcJob* __rest
     const int K = N;
     constexpr int LD = 8;
     for (int base_idx = 0; base_idx < 128 * Kp; base_idx += 128 * LD) {
-        float v[LD];
+        TIn raw[LD];
 #pragma unroll
         for (int u = 0; u < LD; u++) {
             const int idx = base_idx + u * 128 + tid;
@@ -132,15 +152,16 @@ __global__ void __launch_bounds__(128) k_contract_tc(Dims d, const TcJob* __rest
             if (DIR == 2) { m = idx / Kp; k = idx % Kp; }   // consecutive threads along a line
             else { k = idx / 128; m = idx % 128; }          // consecutive threads across lines
             const long long t = t0 + m;
-            v[u] = 0.f;
+            raw[u] = TIn(0);
             if (k < K && t < nlines) {
                 long long base;
                 if (DIR == 0) { long long e = t / d.NtNp; base = e * d.elem + (t - e * d.NtNp); }
                 else if (DIR == 1) { long long eil = t / d.Np; base = eil * d.NtNp + (t - eil * d.Np); }
                 else base = t * N;
-                v[u] = (float)static_cast<const TIn*>(job.src)[base + (long long)k * stride];
+                raw[u] = static_cast<const TIn*>(job.src)[base + (long long)k * stride];
             }
         }
+        // all LD loads are issued before the first conversion
 #pragma unroll
         for (int u = 0; u < LD; u++) {
             const int idx = base_idx + u * 128 + tid;
@@ -148,13 +169,14 @@ __global__ void __launch_bounds__(128) k_contract_tc(Dims d, const TcJob* __rest
             if (DIR == 2) { m = idx / Kp; k = idx % Kp; }
             else { k = idx / 128; m = idx % 128; }
             const uint32_t off = core_off(m, k, kcores, es);
+            const float v = to_f32(raw[u]);
             if (tf32) {
                 uint32_t w;
-                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w) : "f"(v[u]));
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w) : "f"(v));
                 *reinterpret_cast<uint32_t*>(sA + off) = w;
             } else {
-                __nv_bfloat16 x1 = __float2bfloat16_rn(v[u]);
-                float r1 = v[u] - __bfloat162float(x1);
+                __nv_bfloat16 x1 = __float2bfloat16_rn(v);
+                float r1 = v - __bfloat162float(x1);
                 __nv_bfloat16 x2 = __float2bfloat16_rn(r1);
                 __nv_bfloat16 x3 = __float2bfloat16_rn(r1 - __bfloat162float(x2));
                 *reinterpret_cast<__nv_bfloat16*>(sA + off) = x1;
@@ -202,15 +224,18 @@ __global__ void __launch_bounds__(128) k_contract_tc(Dims d, const TcJob* __rest
     if (!ok && (tid & 31) == 0) atomicExch(err, 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
     // epilogue: warp w owns lines 32w..32w+31 (TMEM lanes), 8 output columns at a time
+    // (the radial Jacobian multiplies in FP32: one rounding more than forming the product in
+    // FP64 before the cast, at most 2^-24 relative, where the FP64 product kept the FP64
+    // pipe 63-76 % busy in the radial instances)
     const int m = warp * 32 + (tid & 31);
     const long long t = t0 + m;
     long long base = 0;
-    double scale = 1.0;
+    float scale = 1.0f;
     if (t < nlines) {
         if (DIR == 0) {
             long long e = t / d.NtNp;
             base = e * d.elem + (t - e * d.NtNp);
-            if (r_scale) scale = r_scale[e];
+            if (r_scale) scale = d2f_rn(r_scale[e]);
         } else if (DIR == 1) { long long eil = t / d.Np; base = eil * d.NtNp + (t - eil * d.Np); }
         else base = t * N;
     }
@@ -227,7 +252,7 @@ __global__ void __launch_bounds__(128) k_contract_tc(Dims d, const TcJob* __rest
                 // a line's 8 outputs are contiguous: two 16-byte stores
                 float o[8];
 #pragma unroll
-                for (int j = 0; j < 8; j++) o[j] = (float)(scale * (double)__uint_as_float(r[j]));
+                for (int j = 0; j < 8; j++) o[j] = __fmul_rn(scale, __uint_as_float(r[j]));
                 float4* p4 = reinterpret_cast<float4*>(job.dst + base + cb);
                 float4 lo = make_float4(o[0], o[1], o[2], o[3]), hi = make_float4(o[4], o[5], o[6], o[7]);
                 if (job.accumulate) {
@@ -242,7 +267,7 @@ __global__ void __launch_bounds__(128) k_contract_tc(Dims d, const TcJob* __rest
                 for (int j = 0; j < 8; j++) {
                     int i = cb + j;
                     if (i < N) {
-                        float o = (float)(scale * (double)__uint_as_float(r[j]));
+                        float o = __fmul_rn(scale, __uint_as_float(r[j]));
                         float* p = job.dst + base + (long long)i * stride;
                         if (job.accumulate) *p += o;
                         else *p = o;
