@@ -11,6 +11,7 @@
 // consecutive threads of a warp touch consecutive doubles of every field.
 #include <math.h>
 
+#include "fp_convert.cuh"
 #include "grmhd_internal.h"
 
 namespace gk {
@@ -237,13 +238,13 @@ __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const doubl
         // ---- four-vectors, fluxes and T^{mu nu} in R: FP64, or FP32 in the mixed modes
         // (their consumers, the tensor-core contractions and the FP32 right-hand side, keep
         // about 24 bits); the primitive recovery above stays FP64
-        const R alphaR = (R)alpha, sqgR = (R)sqg, WR = (R)W;
+        const R alphaR = narrow<R>(alpha), sqgR = narrow<R>(sqg), WR = narrow<R>(W);
         R gR[3][3], betaR[3], vR[3], BR[3];
         for (int i = 0; i < 3; i++) {
-            betaR[i] = (R)beta[i];
-            vR[i] = (R)v[i];
-            BR[i] = (R)B_u[i];
-            for (int j = 0; j < 3; j++) gR[i][j] = (R)g[i][j];
+            betaR[i] = narrow<R>(beta[i]);
+            vR[i] = narrow<R>(v[i]);
+            BR[i] = narrow<R>(B_u[i]);
+            for (int j = 0; j < 3; j++) gR[i][j] = narrow<R>(g[i][j]);
         }
         R v_d[3];
         for (int i = 0; i < 3; i++) v_d[i] = gR[i][0] * vR[0] + gR[i][1] * vR[1] + gR[i][2] * vR[2];
@@ -265,10 +266,11 @@ __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const doubl
         for (int i = 0; i < 3; i++)
             bd[i] = beta_d[i] * b0 + gR[i][0] * bu[0] + gR[i][1] * bu[1] + gR[i][2] * bu[2];
         R b2 = b0 * bd0 + bu[0] * bd[0] + bu[1] * bd[1] + bu[2] * bd[2];
-        R pstar = (R)pr + R(0.5) * b2;
-        R rhohs = (R)rho * (R(1.0) + (R)eps) + (R)pr + b2;   // rho h*
+        const R rhoR = narrow<R>(rho), epsR = narrow<R>(eps), prR = narrow<R>(pr);
+        R pstar = prR + R(0.5) * b2;
+        R rhohs = rhoR * (R(1.0) + epsR) + prR + b2;   // rho h*
         // conserved variables from the primitives (undensitized)
-        R Dp = (R)rho * WR;
+        R Dp = rhoR * WR;
         R Sp[3];
         for (int j = 0; j < 3; j++) Sp[j] = rhohs * WR * WR * v_d[j] - alphaR * b0 * bd[j];
         // tau = rho h* W^2 - p* - alpha^2 b0^2 - D without its cancellation: with
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const doubl
         R taup;
         if constexpr (sizeof(R) == 4) {
             const R Wv2 = WR * WR * (v_d[0] * vR[0] + v_d[1] * vR[1] + v_d[2] * vR[2]);
-            taup = (R)rho * WR * ((R)eps * WR + Wv2 / (WR + R(1.0))) + (R)pr * Wv2 + b2 * (WR * WR - R(0.5)) -
+            taup = rhoR * WR * (epsR * WR + Wv2 / (WR + R(1.0))) + prR * Wv2 + b2 * (WR * WR - R(0.5)) -
                    alphaR * alphaR * b0 * b0;
         } else {
             taup = rhohs * WR * WR - pstar - alphaR * alphaR * b0 * b0 - Dp;
@@ -289,13 +291,13 @@ __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const doubl
         for (int i = 0; i < 3; i++) vt[i] = alphaR * vR[i] - betaR[i];
         for (int i = 0; i < 3; i++) {
             double* F = flux + (long long)(i * 8) * P + p;
-            F[0 * P] = sqgR * (Dp * vt[i]);
+            F[0 * P] = widen(sqgR * (Dp * vt[i]));
             for (int j = 0; j < 3; j++)
-                F[(1 + j) * P] = sqgR * (Sp[j] * vt[i] + (i == j ? alphaR * pstar : R(0.0)) -
-                                         alphaR * bd[j] * BR[i] * iW);
-            F[4 * P] = sqgR * (taup * vt[i] + alphaR * pstar * vR[i] -
-                               alphaR * alphaR * b0 * BR[i] * iW);
-            for (int k = 0; k < 3; k++) F[(5 + k) * P] = sqgR * (vt[i] * BR[k] - vt[k] * BR[i]);
+                F[(1 + j) * P] = widen(sqgR * (Sp[j] * vt[i] + (i == j ? alphaR * pstar : R(0.0)) -
+                                               alphaR * bd[j] * BR[i] * iW));
+            F[4 * P] = widen(sqgR * (taup * vt[i] + alphaR * pstar * vR[i] -
+                                     alphaR * alphaR * b0 * BR[i] * iW));
+            for (int k = 0; k < 3; k++) F[(5 + k) * P] = widen(sqgR * (vt[i] * BR[k] - vt[k] * BR[i]));
         }
         // ---- T^{mu nu}
         R ia2 = ia * ia;
@@ -303,13 +305,13 @@ __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const doubl
         gu[0][0] = -ia2;
         for (int i = 0; i < 3; i++) gu[0][i + 1] = gu[i + 1][0] = betaR[i] * ia2;
         for (int i = 0; i < 3; i++)
-            for (int j = 0; j < 3; j++) gu[i + 1][j + 1] = (R)gi[i][j] - betaR[i] * betaR[j] * ia2;
+            for (int j = 0; j < 3; j++) gu[i + 1][j + 1] = narrow<R>(gi[i][j]) - betaR[i] * betaR[j] * ia2;
         R u4[4] = {u0, uu[0], uu[1], uu[2]};
         R b4[4] = {b0, bu[0], bu[1], bu[2]};
         int n = 0;
         for (int m = 0; m < 4; m++)
             for (int k = m; k < 4; k++, n++)
-                tmn[n * P + p] = rhohs * u4[m] * u4[k] + pstar * gu[m][k] - b4[m] * b4[k];
+                tmn[n * P + p] = widen(rhohs * u4[m] * u4[k] + pstar * gu[m][k] - b4[m] * b4[k]);
         lam[p] = fabs(beta[0]) + alpha * sqrt(gi[0][0]);
     }
     // warp-aggregated failure count
@@ -353,17 +355,17 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
     for (int i = 0; i < 3; i++)
         for (int j = i; j < 3; j++) {
             gt64[i][j] = gt64[j][i] = Us[(V_GT + SI(i, j)) * P + p];
-            gt[i][j] = gt[j][i] = (R)gt64[i][j];
-            At[i][j] = At[j][i] = (R)Us[(V_AT + SI(i, j)) * P + p];
+            gt[i][j] = gt[j][i] = narrow<R>(gt64[i][j]);
+            At[i][j] = At[j][i] = narrow<R>(Us[(V_AT + SI(i, j)) * P + p]);
         }
     const double phi = Us[V_PHI * P + p];
-    const R K = (R)Us[V_K * P + p];
-    const R alpha = (R)Us[V_ALPHA * P + p];
+    const R K = narrow<R>(Us[V_K * P + p]);
+    const R alpha = narrow<R>(Us[V_ALPHA * P + p]);
     R Gam[3], beta[3], Bg[3];
     for (int i = 0; i < 3; i++) {
-        Gam[i] = (R)Us[(V_GAM + i) * P + p];
-        beta[i] = (R)Us[(V_BETA + i) * P + p];
-        Bg[i] = (R)Us[(V_BG + i) * P + p];
+        Gam[i] = narrow<R>(Us[(V_GAM + i) * P + p]);
+        beta[i] = narrow<R>(Us[(V_BETA + i) * P + p]);
+        Bg[i] = narrow<R>(Us[(V_BG + i) * P + p]);
     }
     // conformal factor, physical metric, its determinant and inverse, conformal inverse:
     // FP64 in every mode; the algebra below runs in R
@@ -371,7 +373,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
     // det gamma = e^{12 phi} det gammatilde (one cofactor inverse)
     const double e4 = exp(4.0 * phi);
     const double e4m = 1.0 / e4;
-    const R e4r = (R)e4, e4mr = (R)e4m;
+    const R e4r = narrow<R>(e4), e4mr = narrow<R>(e4m);
     double g64[3][3], gi64[3][3], gti64[3][3];
     const double detgt = inv3sym(gt64, gti64);
     for (int i = 0; i < 3; i++)
@@ -380,13 +382,13 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
             gi64[i][j] = e4m * gti64[i][j];
         }
     const double detg = e4 * e4 * e4 * detgt;
-    const R sqg = (R)sqrt(detg);
+    const R sqg = narrow<R>(sqrt(detg));
     R g[3][3], gi[3][3], gti[3][3];
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) {
-            g[i][j] = (R)g64[i][j];
-            gi[i][j] = (R)gi64[i][j];
-            gti[i][j] = (R)gti64[i][j];
+            g[i][j] = narrow<R>(g64[i][j]);
+            gi[i][j] = narrow<R>(gi64[i][j]);
+            gti[i][j] = narrow<R>(gti64[i][j]);
         }
 
     // first derivatives: field f, direction dd -> d1[(f*3+dd)*P + p]
@@ -410,12 +412,12 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
 
     // ------------------------------------------------------------ Valencia
     {
-        R T00 = tmn[0 * P + p];
-        R T0i[3] = {tmn[1 * P + p], tmn[2 * P + p], tmn[3 * P + p]};
+        R T00 = narrow<R>(tmn[0 * P + p]);
+        R T0i[3] = {narrow<R>(tmn[1 * P + p]), narrow<R>(tmn[2 * P + p]), narrow<R>(tmn[3 * P + p])};
         R Tij[3][3];
-        Tij[0][0] = tmn[4 * P + p]; Tij[0][1] = Tij[1][0] = tmn[5 * P + p];
-        Tij[0][2] = Tij[2][0] = tmn[6 * P + p]; Tij[1][1] = tmn[7 * P + p];
-        Tij[1][2] = Tij[2][1] = tmn[8 * P + p]; Tij[2][2] = tmn[9 * P + p];
+        Tij[0][0] = narrow<R>(tmn[4 * P + p]); Tij[0][1] = Tij[1][0] = narrow<R>(tmn[5 * P + p]);
+        Tij[0][2] = Tij[2][0] = narrow<R>(tmn[6 * P + p]); Tij[1][1] = narrow<R>(tmn[7 * P + p]);
+        Tij[1][2] = Tij[2][1] = narrow<R>(tmn[8 * P + p]); Tij[2][2] = narrow<R>(tmn[9 * P + p]);
         R beta_d[3];
         for (int i = 0; i < 3; i++)
             beta_d[i] = g[i][0] * beta[0] + g[i][1] * beta[1] + g[i][2] * beta[2];
@@ -478,10 +480,10 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
         // divergence d_i(sqrt(gamma) B^i) / sqrt(gamma); field source -alpha sqrt(gamma)
         // gamma^ij d_j psi (d psi: d1 field N_D1)
         if (pp.glm) {
-            const R psi = (R)Us[(long long)V_PSI * P + p];
+            const R psi = narrow<R>(Us[(long long)V_PSI * P + p]);
             R dpsi[3];
             for (int k = 0; k < 3; k++) dpsi[k] = (R)d1[((long long)N_D1 * 3 + k) * P + p];
-            rhs[V_PSI] = alpha * (-(R)pp.glm_ch2 * (R)divB[p] / sqg - psi * (R)pp.glm_itau);
+            rhs[V_PSI] = alpha * (-narrow<R>(pp.glm_ch2) * (R)divB[p] / sqg - psi * narrow<R>(pp.glm_itau));
             for (int i = 0; i < 3; i++)
                 rhs[V_B + i] -= asg * (gi[i][0] * dpsi[0] + gi[i][1] * dpsi[1] + gi[i][2] * dpsi[2]);
         }
@@ -505,8 +507,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
                 double UL = Us[(V_D + v) * P + pl];
                 double UR = Us[(V_D + v) * P + pr_];
                 double Fs = 0.5 * (FL + FR) - 0.5 * lmax * (UR - UL);
-                if (side > 0) rhs[V_D + v] += (R)((FL - Fs) * fac);
-                else rhs[V_D + v] -= (R)((FR - Fs) * fac);
+                if (side > 0) rhs[V_D + v] += narrow<R>((FL - Fs) * fac);
+                else rhs[V_D + v] -= narrow<R>((FR - Fs) * fac);
             }
         }
 
@@ -663,8 +665,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
             // as above: the same Ricci tensor, no extra derivative)
             // (a separate instance, HAM = true, so that the stepping kernel carries none of it)
             if constexpr (HAM)
-                ham[p] = (double)((e4mr * trX + trDDal) / alpha + R(8.0) * PI * Str + two3 * K * K - AA -
-                                  R(16.0) * PI * rho_m);
+                ham[p] = widen((e4mr * trX + trDDal) / alpha + R(8.0) * PI * Str + two3 * K * K - AA -
+                               R(16.0) * PI * rho_m);
             rhs[V_K] = -trDDal + alpha * (AA + K * K3) + R(4.0) * PI * alpha * (rho_m + Str) +
                        (beta[0] * dK[0] + beta[1] * dK[1] + beta[2] * dK[2]);
             // Gammatilde
@@ -698,7 +700,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
                 rhs[V_ALPHA] = -R(2.0) * alpha * K + beta[0] * dal[0] + beta[1] * dal[1] + beta[2] * dal[2];
                 for (int i = 0; i < 3; i++) {
                     rhs[V_BETA + i] = R(0.75) * Bg[i];
-                    rhs[V_BG + i] = rhs[V_GAM + i] - (R)pp.eta * Bg[i];
+                    rhs[V_BG + i] = rhs[V_GAM + i] - narrow<R>(pp.eta) * Bg[i];
                 }
             } else {
                 rhs[V_ALPHA] = R(0.0);
@@ -722,12 +724,12 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
     // ------------------------------------------------------------ output
     const double dt = dt_dev ? dt_dev[d.elem_inst[elem_id]] : 0.0;
     if (co.acc_mode < 0) {
-        for (int v = 0; v < nv; v++) out[v * P + p] = (double)rhs[v];
+        for (int v = 0; v < nv; v++) out[v * P + p] = widen(rhs[v]);
         return;
     }
     for (int v = 0; v < nv; v++) {
         long long ix = v * P + p;
-        double L = (double)rhs[v];
+        double L = widen(rhs[v]);
         double o;
         if (co.acc_mode == 0) {
             // SSP-RK3 (Shu-Osher): a U0 + b (Us + dt L)

@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "fp_convert.cuh"
 #include "grmhd_internal.h"
 
 namespace gk {
@@ -56,23 +57,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
     return done != 0;
 }
 
-// FP64 -> FP32, rounded to nearest even, with integer instructions: the same result as
-// __double2float_rn, which GB300 runs on its FP64 pipe (at ~1/64 of the integer rate; the
-// conversions of the line tile kept that pipe 24-26 % busy).  Zero, values outside FP32's
-// normal range, Inf and NaN take the hardware conversion.
-__device__ __forceinline__ float d2f_rn(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
-    const uint32_t s = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
-    if (e >= 1 && e <= 254) {
-        const uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);      // leading 23 mantissa bits
-        const uint32_t rest = lo & 0x1FFFFFFFu, half = 0x10000000u;  // the 29 dropped bits
-        // a carry out of the mantissa steps the exponent (to Inf above the largest float)
-        return __uint_as_float((s | ((uint32_t)e << 23) | m) + ((rest > half || (rest == half && (m & 1u))) ? 1u : 0u));
-    }
-    return (b << 1) == 0 ? __uint_as_float(s) : __double2float_rn(x);
-}
 __device__ __forceinline__ float to_f32(double x) { return d2f_rn(x); }
 __device__ __forceinline__ float to_f32(float x) { return x; }
 
