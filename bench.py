@@ -348,20 +348,20 @@ def roofline(kt_full, P, precision, names):
     if top in FP64_FLOPS_PER_NODE and FP64_FLOPS_PER_NODE[top]:
         achieved = FP64_FLOPS_PER_NODE[top] * P * launches / t_s / 1e12
         roof.update({"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get(top),
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": _traffic(top, P),
                      "peak_source": "GB300 FP64 from unit counts and clock (of nominal)",
                      "work": f"{FP64_FLOPS_PER_NODE[top]:.0f} FP64 flop per node (ncu-counted)"})
     elif top.startswith("k_contract") or top.startswith("k_deriv"):
         if top.startswith("k_deriv_eo"):
             achieved = work[top][0] / t_s / 1e12
             roof.update({"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get(top),
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": _traffic(top, P),
                          "peak_source": "GB300 FP64 from unit counts and clock (of nominal)",
                          "work": "2 N FP64 flop per output node"})
         else:
             achieved = work[top][1] / t_s / 1e9
             roof.update({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": TRAFFIC.get(top),
+                         "frac": achieved / hbm, "traffic": _traffic(top, P),
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                          "work": "input read + output written per contracted field"})
     else:
@@ -372,18 +372,29 @@ def roofline(kt_full, P, precision, names):
         else:
             achieved = by * P * launches / t_s / 1e9
             roof.update({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": TRAFFIC.get(top),
+                         "frac": achieved / hbm, "traffic": _traffic(top, P),
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                          "work": f"{by} bytes per node"})
+    if roof.get("traffic") is not None and P != TRAFFIC_NODES:
+        roof["traffic_note"] = (f"ncu DRAM bytes of the {TRAFFIC_NODES}-node workload scaled to {P} nodes "
+                                "(per-node traffic of a pointwise kernel)")
     return roof
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of
 # the current kernel code inside the time stepping of the 393,216-node workload, mean of the
-# three stages of a step); absent = not captured since the kernel last changed.
+# three stages of a step); absent = not captured since the kernel last changed.  These
+# pointwise kernels move a fixed number of bytes per node, so another workload's launch
+# is scaled by its node count (traffic_note says so).
 # k_rhs<double> moves ~2.7 KB per node, about twice its algorithmic bytes: register spills
 # (it is FP64-bound, the bytes are not).
-TRAFFIC = {"k_rhs<double>": 1.08e9, "k_prep<double>": 1.38e8, "k_prep<float>": 1.39e8, "k_rhs<float>": 5.95e8}
+TRAFFIC_NODES = 393216
+TRAFFIC = {"k_rhs<double>": 1.08e9, "k_prep<double>": 1.38e8, "k_prep<float>": 1.39e8, "k_rhs<float>": 5.76e8}
+
+
+def _traffic(kernel, P):
+    t = TRAFFIC.get(kernel)
+    return None if t is None else t * P / TRAFFIC_NODES
 
 
 def run_gpu(args):
