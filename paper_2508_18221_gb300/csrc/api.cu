@@ -95,7 +95,7 @@ struct grmhd_ctx {
     int job_filter[3][3][2]; // [buffer][dir][group] offset (8 or 24 jobs)
     int job_dbg;
     // Fourier theta basis (grid.theta_basis = 1): theta contractions fold the phi pairs
-    // (l, l + N_phi/2) into half sums / differences, contract each half with the even or
+    // (l, l + N_phi/2) into sums / differences, contract each half with the even or
     // odd extension operator, and unfold (kernels_deriv.cu)
     int ft;                  // 1: Fourier theta basis
     Dims dh;                 // one folded half: N_phi / 2 lines per (element, r, theta) row
@@ -552,9 +552,10 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
         c->dh.NtNp = (long long)Nt * (Np / 2);
         c->dh.elem = c->dh.NtNp * Nr;
         c->dh.P = P / 2;
-        theta_extension_ops(fourier_D_row(2 * Nt), Nt, &ext_d[0], &ext_d[1]);
+        // halved: the fold forms the plain sum and difference of each phi pair
+        theta_extension_ops(fourier_D_row(2 * Nt), Nt, &ext_d[0], &ext_d[1], 0.5);
         theta_extension_ops(fourier_filter_row(2 * Nt, opts->filt_alpha, opts->filt_p, opts->dealias23_theta != 0), Nt,
-                            &ext_f[0], &ext_f[1]);
+                            &ext_f[0], &ext_f[1], 0.5);
         // the digit-slice kernel stages lines with 16-byte bulk copies: the folded halves
         // need an even number of lines per row
         const bool fx_ok = opts->contraction == 0 && fx_supported(1, Nt) && (Np / 2) % 2 == 0;

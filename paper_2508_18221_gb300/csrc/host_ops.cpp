@@ -138,8 +138,10 @@ std::vector<double> quad_weights(int n, bool lobatto) {
 // Writing u = p + m, u' = p - m (p, m the half sum and half difference of the phi pair)
 // gives (C g)_i = ((A + s B) p)_i + ((A - s B) m)_i at phi and the same with -m at
 // phi + pi: the sums take A + B for s = +1 (A - B for s = -1), the differences the other.
+// scale multiplies both (exact for a power of two): 1/2 when the fold forms the plain sum
+// and difference of the pair, 1 on a line of definite parity.
 void theta_extension_ops(const std::vector<double>& c, int n, std::vector<double>* even,
-                         std::vector<double>* odd) {
+                         std::vector<double>* odd, double scale) {
     const int n2 = 2 * n;
     even->assign((size_t)n * n, 0.0);
     odd->assign((size_t)n * n, 0.0);
@@ -147,8 +149,8 @@ void theta_extension_ops(const std::vector<double>& c, int n, std::vector<double
         for (int k = 0; k < n; k++) {
             const double a = c[((i - k) % n2 + n2) % n2];
             const double b = c[(i + k + 1) % n2];
-            (*even)[(size_t)i * n + k] = a + b;
-            (*odd)[(size_t)i * n + k] = a - b;
+            (*even)[(size_t)i * n + k] = scale * (a + b);
+            (*odd)[(size_t)i * n + k] = scale * (a - b);
         }
 }
 

@@ -14,9 +14,9 @@ std::vector<double> fourier_filter_row(int n, double alpha, double p, bool deali
 std::vector<double> quad_weights(int n, bool lobatto);
 // Fourier theta basis: the n x n operators A + B (even) and A - B (odd) that act on the
 // phi-pair sums and differences of the double-Fourier extension (host_ops.cpp), for the
-// circulant row c of the 2n extended nodes (derivative or filter)
+// circulant row c of the 2n extended nodes (derivative or filter), times scale
 void theta_extension_ops(const std::vector<double>& c, int n, std::vector<double>* even,
-                         std::vector<double>* odd);
+                         std::vector<double>* odd, double scale = 1.0);
 // reflection-split packing [E | O | C | F | G] of a dense N x N operator (kernels_eo.cu);
 // kind 0 Chebyshev node set, 1 Fourier node set
 std::vector<double> split_operator(const std::vector<double>& M, int N, int kind);

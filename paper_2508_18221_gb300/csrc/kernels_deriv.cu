@@ -121,12 +121,13 @@ cudaError_t launch_iface_avg_f(const Dims& d, float* base, long long fstride, in
 // ---------------------------------------------------------------- Fourier theta folding
 // The theta derivative (or filter) of the double-Fourier extension couples the lines at
 // phi and phi + pi: out(phi) = A u(phi) + s B u(phi + pi) with the parity s of the field.
-// With the half sum p and half difference m of the pair, out(phi) = (A + s B) p + (A - s B) m
-// and out(phi + pi) = (A + s B) p - (A - s B) m, so the fold writes p and m into two
-// halves of N_phi / 2 lines per row (the half for the even operator A + B first: p when
-// s = +1, m when s = -1), each half is contracted along theta with one operator, and the
-// unfold adds and subtracts the two results.  Pure streaming: one coalesced read and write
-// per value.
+// With the sum p and difference m of the pair, out(phi) = (A + s B)/2 p + (A - s B)/2 m
+// and out(phi + pi) = (A + s B)/2 p - (A - s B)/2 m, so the fold writes p and m into two
+// halves of N_phi / 2 lines per row (the half for the even operator first: p when s = +1,
+// m when s = -1), each half is contracted along theta with one operator (the 1/2 is in the
+// operators, so the fold spends one FP64 addition per value and no multiplication: GB300's
+// FP64 pipe bounded it), and the unfold adds and subtracts the two results.  Pure
+// streaming: one coalesced read and write per value.
 template <typename T>
 __global__ void k_theta_fold(Dims d, const FoldJob* __restrict__ jobs) {
     const FoldJob jb = jobs[blockIdx.y];
@@ -140,7 +141,7 @@ __global__ void k_theta_fold(Dims d, const FoldJob* __restrict__ jobs) {
         const long long row = t / h;
         const long long i0 = row * d.Np + (t - row * h);
         const T a = src[i0], b = src[i0 + h];
-        const T p = (T)0.5 * (a + b), m = (T)0.5 * (a - b);
+        const T p = a + b, m = a - b;
         dst[t] = jb.parity > 0 ? p : m;
         dst[half + t] = jb.parity > 0 ? m : p;
     }
