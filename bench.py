@@ -292,7 +292,7 @@ def run_reference(args):
 # FP64 work.  The primitive-recovery count is taken inside the time stepping (Newton
 # started from the previous stage's primitives); k_prep<float> (mixed modes) forms the
 # fluxes and T^{mu nu} in FP32, so only its metric and primitive recovery count.
-FP64_FLOPS_PER_NODE = {"k_rhs<double>": 2618.0, "k_prep<double>": 1031.0, "k_prep<float>": 692.0}
+FP64_FLOPS_PER_NODE = {"k_rhs<double>": 2522.0, "k_prep<double>": 1050.0, "k_prep<float>": 711.0}
 # Nominal FP64 peak of GB300 from its unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop
 # x 2.07 GHz (a probe of dependent DFMA chains on all SMs measured 1.198 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -386,10 +386,10 @@ def roofline(kt_full, P, precision, names):
 # three stages of a step); absent = not captured since the kernel last changed.  These
 # pointwise kernels move a fixed number of bytes per node, so another workload's launch
 # is scaled by its node count (traffic_note says so).
-# k_rhs<double> moves ~2.7 KB per node, about twice its algorithmic bytes: register spills
+# k_rhs<double> moves ~2.8 KB per node, about twice its algorithmic bytes: register spills
 # (it is FP64-bound, the bytes are not).
 TRAFFIC_NODES = 393216
-TRAFFIC = {"k_rhs<double>": 1.08e9, "k_prep<double>": 1.38e8, "k_prep<float>": 1.39e8, "k_rhs<float>": 5.76e8}
+TRAFFIC = {"k_rhs<double>": 1.10e9, "k_prep<double>": 1.66e8, "k_prep<float>": 1.66e8, "k_rhs<float>": 6.13e8}
 
 
 def _traffic(kernel, P):

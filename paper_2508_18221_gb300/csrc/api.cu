@@ -56,6 +56,7 @@ struct grmhd_ctx {
     double* scratch;         // nv * P
     double* divB;            // d_i (sqrt(gamma) B^i) (GLM only)
     double* ham;             // Hamiltonian constraint per node (diagnostics)
+    double* met;             // 9 * P: the metric of the last k_prep (e^{4phi}, e^{-4phi}, sqrt(gamma), gammatilde^ij)
     double* ham_out;         // non-null while a diagnostic stage is enqueued: k_rhs writes H there
     int nv;                  // evolved variables: GRMHD_NV, + 1 (psi) with GLM
     double* Dr;              // Nr x Nr reference CGL matrix on [-1, 1]
@@ -240,7 +241,7 @@ static void free_ctx(grmhd_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     double** bufs[] = {&c->U[0], &c->U[1], &c->U[2], &c->acc, &c->prim, &c->flux, &c->tmn, &c->lam,
                        &c->d1, &c->d2, &c->divF, &c->scratch, &c->Dr, &c->Dt, &c->Dp, &c->Fr,
-                       &c->Ft, &c->Fp, &c->r_scale, &c->wq, &c->hmin, &c->dt, &c->diag, &c->divB, &c->ham};
+                       &c->Ft, &c->Fp, &c->r_scale, &c->wq, &c->hmin, &c->dt, &c->diag, &c->divB, &c->ham, &c->met};
     for (double** b : bufs)
         if (*b) cudaFree(*b);
     for (int k = 0; k < 3; k++) {
@@ -435,6 +436,7 @@ static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* p
     AL(c->d2, N_D2 * 6 * P);
     AL(c->divF, 8 * P);
     AL(c->ham, P);
+    AL(c->met, 9 * P);
     AL(c->scratch, nv * P);
     AL(c->Dr, Nr * Nr); AL(c->Dt, Nt * Nt); AL(c->Dp, Np);
     AL(c->Fr, Nr * Nr); AL(c->Ft, Nt * Nt); AL(c->Fp, Np);
@@ -948,13 +950,13 @@ static int enqueue_stage(grmhd_ctx* c, int b, RKCoef co, double* out, const Phys
         if (!st) CK(cudaEventRecord(c->ev_join, c->s2));
     }
     if (st) return st;
-    CK(launch_prep(c->d, pp, c->U[b], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream,
+    CK(launch_prep(c->d, pp, c->U[b], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->met, c->stream,
                    c->opts.precision > 0));
     c->launches_tmp++;
     st = enqueue_first_derivs(c, b, 1);
     if (st) return st;
     CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
-    CK(launch_rhs(c->d, pp, c->U[0], c->U[b], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
+    CK(launch_rhs(c->d, pp, c->U[0], c->U[b], c->prim, c->flux, c->tmn, c->lam, c->met, c->d1, c->d2,
                   c->divF, c->divB, c->opts.precision > 0, c->r_scale, c->dt, co, out, c->acc, c->stream,
                   c->ham_out));
     c->launches_tmp++;
@@ -1253,7 +1255,7 @@ extern "C" int grmhd_con2prim(grmhd_ctx* c, double* prim_out, int on_device, lon
     NvtxRange nvtx_range("grmhd_con2prim");
     if (!c) return GRMHD_EINVAL;
     CK(cudaMemsetAsync(c->nfail, 0, sizeof(unsigned long long), c->stream));
-    CK(launch_prep(c->d, c->pp, c->U[0], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream));
+    CK(launch_prep(c->d, c->pp, c->U[0], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->met, c->stream));
     if (prim_out) {
         int st = copy_out(c, prim_out, c->prim, (size_t)N_PRIM * c->d.P, on_device);
         if (st) return st;
@@ -1351,7 +1353,7 @@ extern "C" int grmhd_diag(grmhd_ctx* c, double out[GRMHD_NDIAG]) {
         if (st) return st;
     }
     CK(cudaMemsetAsync(c->nfail, 0, sizeof(unsigned long long), c->stream));
-    CK(launch_prep(c->d, c->pp, c->U[0], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream));
+    CK(launch_prep(c->d, c->pp, c->U[0], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->met, c->stream));
     // divergence of the densitized field into scratch
     const long long P = c->d.P;
     DerivJob jb[3];
@@ -1437,7 +1439,7 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
         CK(cudaEventRecord(e0, c->stream));
         for (int r = 0; r < reps; r++) {
             cudaError_t e = cudaSuccess;
-            if (k == 0) e = launch_prep(c->d, c->pp, c->U[1], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->stream,
+            if (k == 0) e = launch_prep(c->d, c->pp, c->U[1], c->prim, c->flux, c->tmn, c->lam, c->nfail, c->met, c->stream,
                                         mixed);
             else if (k >= 1 && k <= 3) {
                 int dir = k - 1;
@@ -1480,7 +1482,7 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
                     e = mixed ? launch_iface_avg_f(c->d, reinterpret_cast<float*>(c->d2) + x * P, 6 * P, N_D2, c->stream)
                               : launch_iface_avg(c->d, c->d2 + x * P, 6 * P, N_D2, c->stream);
             }
-            else if (k == 9) e = launch_rhs(c->d, c->pp, c->U[0], c->U[1], c->prim, c->flux, c->tmn, c->lam, c->d1, c->d2,
+            else if (k == 9) e = launch_rhs(c->d, c->pp, c->U[0], c->U[1], c->prim, c->flux, c->tmn, c->lam, c->met, c->d1, c->d2,
                                             c->divF, c->divB, c->opts.precision > 0, c->r_scale, c->dt, co, c->scratch,
                                             c->acc, c->stream);
             else {

@@ -83,15 +83,17 @@ struct FoldJob {
 cudaError_t kernels_init();
 cudaError_t eo_init();
 cudaError_t tc_init();
+// met: 9 P doubles written per node (e^{4phi}, e^{-4phi}, sqrt(gamma), gammatilde^ij in the
+// packed order rr r-theta r-phi theta-theta theta-phi phi-phi), read by launch_rhs
 cudaError_t launch_prep(const Dims& d, const PhysParams& pp, const double* U, double* prim,
-                        double* flux, double* tmn, double* lam, unsigned long long* nfail,
+                        double* flux, double* tmn, double* lam, unsigned long long* nfail, double* met,
                         cudaStream_t s, int fp32_algebra = 0);
 struct RKCoef { double a, b, c, w; int acc_mode; };  // out = a U0 + b Us + c dt L (+acc)
 // d1, d2, divF are double (FP64 mode) or float (deriv_fp32 = 1, mixed modes); ham != null
 // also writes the Hamiltonian constraint per node (diagnostics)
 cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, const double* Us,
                        const double* prim, const double* flux, const double* tmn,
-                       const double* lam, const void* d1, const void* d2,
+                       const double* lam, const double* met, const void* d1, const void* d2,
                        const void* divF, const void* divB, int deriv_fp32, const double* r_scale_dev,
                        const double* dt_dev, RKCoef co, double* out, double* acc, cudaStream_t s,
                        double* ham = nullptr);

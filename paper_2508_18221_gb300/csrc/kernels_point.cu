@@ -191,18 +191,34 @@ template <typename R>
 __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const double* __restrict__ U,
                                               double* __restrict__ prim, double* __restrict__ flux,
                                               double* __restrict__ tmn, double* __restrict__ lam,
-                                              unsigned long long* __restrict__ nfail) {
+                                              unsigned long long* __restrict__ nfail, double* __restrict__ met) {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long P = d.P;
     int bad = 0;
     if (p < P) {
-        double e4 = exp(4.0 * U[V_PHI * P + p]);
-        double g[3][3], gi[3][3];
+        // gamma = e^{4phi} gammatilde, gamma^-1 = e^{-4phi} gammatilde^-1, det gamma =
+        // e^{12phi} det gammatilde, computed as the right-hand side uses them and kept in met
+        // (e^{4phi}, e^{-4phi}, sqrt(gamma), gammatilde^ij) so that k_rhs reads them: GB300's
+        // FP64 pipe bounds both kernels, and the exponential, the cofactor inverse with its
+        // division and the square root are ~75 FP64 instructions per node
+        const double e4 = exp(4.0 * U[V_PHI * P + p]);
+        const double e4m = 1.0 / e4;
+        double gt[3][3], gti[3][3], g[3][3], gi[3][3];
         for (int i = 0; i < 3; i++)
-            for (int j = i; j < 3; j++) g[i][j] = g[j][i] = e4 * U[(V_GT + SI(i, j)) * P + p];
-        double det = inv3sym(g, gi);
-        double sqg = sqrt(det);
+            for (int j = i; j < 3; j++) gt[i][j] = gt[j][i] = U[(V_GT + SI(i, j)) * P + p];
+        const double detgt = inv3sym(gt, gti);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                g[i][j] = e4 * gt[i][j];
+                gi[i][j] = e4m * gti[i][j];
+            }
+        const double sqg = sqrt(e4 * e4 * e4 * detgt);
         double isq = 1.0 / sqg;
+        met[0 * P + p] = e4;
+        met[1 * P + p] = e4m;
+        met[2 * P + p] = sqg;
+        for (int i = 0; i < 3; i++)
+            for (int j = i; j < 3; j++) met[(3 + SI(i, j)) * P + p] = gti[i][j];
         double alpha = U[V_ALPHA * P + p];
         double beta[3] = {U[V_BETA * P + p], U[(V_BETA + 1) * P + p], U[(V_BETA + 2) * P + p]};
         double Dc = U[V_D * P + p] * isq;
@@ -333,6 +349,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
                                              const double* __restrict__ flux,
                                              const double* __restrict__ tmn,
                                              const double* __restrict__ lam,
+                                             const double* __restrict__ met,
                                              const DT* __restrict__ d1,
                                              const DT* __restrict__ d2,
                                              const DT* __restrict__ divF,
@@ -358,7 +375,6 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
             gt[i][j] = gt[j][i] = narrow<R>(gt64[i][j]);
             At[i][j] = At[j][i] = narrow<R>(Us[(V_AT + SI(i, j)) * P + p]);
         }
-    const double phi = Us[V_PHI * P + p];
     const R K = narrow<R>(Us[V_K * P + p]);
     const R alpha = narrow<R>(Us[V_ALPHA * P + p]);
     R Gam[3], beta[3], Bg[3];
@@ -368,21 +384,20 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
         Bg[i] = narrow<R>(Us[(V_BG + i) * P + p]);
     }
     // conformal factor, physical metric, its determinant and inverse, conformal inverse:
-    // FP64 in every mode; the algebra below runs in R
-    // gamma = e^{4phi} gammatilde: gamma^{-1} = e^{-4phi} gammatilde^{-1} and
-    // det gamma = e^{12 phi} det gammatilde (one cofactor inverse)
-    const double e4 = exp(4.0 * phi);
-    const double e4m = 1.0 / e4;
+    // FP64 in every mode; the algebra below runs in R.  e^{4phi}, e^{-4phi}, sqrt(gamma)
+    // and gammatilde^ij come from k_prep's met (the same formulas on the same state);
+    // gamma = e^{4phi} gammatilde, gamma^{-1} = e^{-4phi} gammatilde^{-1}
+    const double e4 = met[0 * P + p], e4m = met[1 * P + p];
     const R e4r = narrow<R>(e4), e4mr = narrow<R>(e4m);
     double g64[3][3], gi64[3][3], gti64[3][3];
-    const double detgt = inv3sym(gt64, gti64);
+    for (int i = 0; i < 3; i++)
+        for (int j = i; j < 3; j++) gti64[i][j] = gti64[j][i] = met[(3 + SI(i, j)) * P + p];
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) {
             g64[i][j] = e4 * gt64[i][j];
             gi64[i][j] = e4m * gti64[i][j];
         }
-    const double detg = e4 * e4 * e4 * detgt;
-    const R sqg = narrow<R>(sqrt(detg));
+    const R sqg = narrow<R>(met[2 * P + p]);
     R g[3][3], gi[3][3], gti[3][3];
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) {
@@ -748,24 +763,24 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_rhs(Dims d, Phy
 
 // --------------------------------------------------------------------------- launchers
 cudaError_t launch_prep(const Dims& d, const PhysParams& pp, const double* U, double* prim,
-                        double* flux, double* tmn, double* lam, unsigned long long* nfail,
+                        double* flux, double* tmn, double* lam, unsigned long long* nfail, double* met,
                         cudaStream_t s, int fp32_algebra) {
     int bs = 128;
     long long nb = (d.P + bs - 1) / bs;
-    if (fp32_algebra) k_prep<float><<<(unsigned)nb, bs, 0, s>>>(d, pp, U, prim, flux, tmn, lam, nfail);
-    else k_prep<double><<<(unsigned)nb, bs, 0, s>>>(d, pp, U, prim, flux, tmn, lam, nfail);
+    if (fp32_algebra) k_prep<float><<<(unsigned)nb, bs, 0, s>>>(d, pp, U, prim, flux, tmn, lam, nfail, met);
+    else k_prep<double><<<(unsigned)nb, bs, 0, s>>>(d, pp, U, prim, flux, tmn, lam, nfail, met);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, const double* Us,
                        const double* prim, const double* flux, const double* tmn,
-                       const double* lam, const void* d1, const void* d2,
+                       const double* lam, const double* met, const void* d1, const void* d2,
                        const void* divF, const void* divB, int deriv_fp32, const double* r_scale_dev,
                        const double* dt_dev, RKCoef co, double* out, double* acc, cudaStream_t s,
                        double* ham) {
     int bs = 128;
     long long nb = (d.P + bs - 1) / bs;
-#define RHS_ARGS(T) d, pp, U0, Us, prim, flux, tmn, lam, (const T*)d1, (const T*)d2, (const T*)divF, \
+#define RHS_ARGS(T) d, pp, U0, Us, prim, flux, tmn, lam, met, (const T*)d1, (const T*)d2, (const T*)divF, \
                     (const T*)divB, r_scale_dev, dt_dev, co, out, acc, ham
     if (deriv_fp32) {
         if (ham) k_rhs<float, float, true><<<(unsigned)nb, bs, 0, s>>>(RHS_ARGS(float));
