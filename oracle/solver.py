@@ -520,8 +520,8 @@ def diagnostics(U, g: Grid, p: Params):
     H the Hamiltonian constraint.
     Entropy follows the paper's discrete functional E = sum rho s sqrt(gamma) dV with
     s = ln(p / rho^Gamma)/(Gamma-1) and dV the quadrature weight (reading: the paper's
-    "cell volume" on spectral nodes).  Parity unpinned for the entropy (the paper
-    prints no values); reported only."""
+    "cell volume" on spectral nodes).  The paper prints no values; mass and entropy are
+    pinned by closed-form integrals on flat space."""
     w = quadrature_weights(g)
     prim = primitives(U, p)
     f = unpack_bssn(U)

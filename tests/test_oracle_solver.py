@@ -171,3 +171,46 @@ def test_split_error_is_second_order():
         diffs.append(np.max(np.abs(a - b)))
     r1, r2 = diffs[0] / diffs[1], diffs[1] / diffs[2]
     assert 3.5 < r1 < 4.5 and 3.5 < r2 < 4.5, (diffs, r1, r2)
+
+
+@pytest.mark.parametrize("theta_basis", [0, 1])
+def test_mass_and_entropy_closed_form(theta_basis):
+    """Rest mass and entropy diagnostics on flat space in spherical coordinates
+    (sqrt(gamma) = r^2 sin(theta)) against their integrals written out by hand.
+
+    rho = rho0 (1 + r/4), a uniform radial velocity v^r = 0.3 (W = 1/sqrt(1 - 0.09)),
+    p = rho^Gamma exp((Gamma - 1) s) with the specific entropy s = s0 + s1 r.  Then
+    mass = W int rho dV and entropy = int rho s dV, dV = r^2 sin(theta) dr dtheta dphi;
+    both radial integrands are polynomials the Clenshaw-Curtis rule integrates exactly,
+    and the theta factor is int sin(theta) dtheta.  A dropped sqrt(gamma), D in place of
+    rho in the entropy, a missing 1/(Gamma - 1) in s or wrong per-element weights each
+    change one of the two numbers at O(1)."""
+    if theta_basis:
+        p = so.Params(M=0.0, a=0.0, n_elem=3, r_min=2.0, r_max=6.0, n_r=8, n_theta=16,
+                      n_phi=4, theta_basis=1)
+    else:
+        p = so.Params(M=0.0, a=0.0, n_elem=3, r_min=2.0, r_max=6.0, n_r=8, n_theta=16,
+                      n_phi=4, theta_min=0.3, theta_max=2.5)
+    g = so.Grid(p)
+    rho0, s0, s1, vr, G = 1e-2, 0.7, -0.15, 0.3, p.gamma_eos
+    z = np.zeros(g.shape)
+    rho = rho0 * (1.0 + g.R / 4.0)
+    s = s0 + s1 * g.R
+    pr = rho ** G * np.exp((G - 1.0) * s)
+    U = so.initial_state(g, p, dict(rho=rho, p=pr, vr=np.full(g.shape, vr), vth=z, vph=z,
+                                    A_phi=z))
+    _, sqg = so.metric_from_bssn(so.unpack_bssn(U))
+    np.testing.assert_allclose(sqg, g.R ** 2 * np.sin(g.T), rtol=1e-13)
+    a, b = p.r_min, p.r_max
+    th0, th1 = (0.0, np.pi) if theta_basis else (p.theta_min, p.theta_max)
+    ang = 2.0 * np.pi * (np.cos(th0) - np.cos(th1))
+
+    def mom(k):                                     # int_a^b r^k dr
+        return (b ** (k + 1) - a ** (k + 1)) / (k + 1)
+    W = 1.0 / np.sqrt(1.0 - vr * vr)
+    mass = W * rho0 * (mom(2) + mom(3) / 4.0) * ang
+    ent = rho0 * (s0 * mom(2) + (s0 / 4.0 + s1) * mom(3) + s1 / 4.0 * mom(4)) * ang
+    d = so.diagnostics(U, g, p)
+    assert d[3] == 0.0
+    np.testing.assert_allclose(d[0], mass, rtol=1e-12)
+    np.testing.assert_allclose(d[1], ent, rtol=1e-11)
