@@ -292,7 +292,7 @@ def run_reference(args):
 # FP64 work.  The primitive-recovery count is taken inside the time stepping (Newton
 # started from the previous stage's primitives); k_prep<float> (mixed modes) forms the
 # fluxes and T^{mu nu} in FP32, so only its metric and primitive recovery count.
-FP64_FLOPS_PER_NODE = {"k_rhs<double>": 2522.0, "k_prep<double>": 1050.0, "k_prep<float>": 711.0}
+FP64_FLOPS_PER_NODE = {"k_rhs<double>": 2501.0, "k_prep<double>": 1050.0, "k_prep<float>": 711.0}
 # Nominal FP64 peak of GB300 from its unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop
 # x 2.07 GHz (a probe of dependent DFMA chains on all SMs measured 1.198 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
