@@ -276,11 +276,14 @@ def run_reference(args):
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Kerr-Schild torus, splitmix64 noise)",
-            "config": {"workload": "c2 sample: radial element 0 of the 8-element a=0.9 "
-                                   "24x32x64 grid, one RHS evaluation per step",
-                       "nodes": npts},
+            "config": {"workload": WORKLOADS["c2"][0], "precision": 0,
+                       "nodes": cfg.n_elem * cfg.n_r * cfg.n_theta * cfg.n_phi,
+                       "rk_steps_per_bench_step": WORKLOADS["c2"][1],
+                       "parallelism": f"replicas x{world}"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"one RHS of element 0 ({npts} nodes) per step"},
+                             "sample": f"each step one RHS evaluation of radial element 0 of "
+                                       f"the {cfg.n_elem}-element grid ({npts} nodes); numpy, "
+                                       "single-threaded elementwise"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
