@@ -61,3 +61,31 @@ def test_single_rank_combine_is_local():
     # rank 0's batch is the single-GPU batch
     from workloads import batch_configs
     assert [c.seed for c in bench.rank_batch(5, 0)] == [c.seed for c in batch_configs(5)]
+
+
+def test_reference_arm_line_matches_the_benchmark_config():
+    """`bench.py --impl reference` times the oracle on the host: one JSON line with the
+    benchmark's own metric, unit and config (the sample it times stated in cpu_baseline),
+    and an end-to-end figure with no host-device copies."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    sys.path.insert(0, root)
+    import bench
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.metric_name(0) and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["value"] > 0
+    assert d["config"]["workload"] == bench.WORKLOADS["c2"][0]
+    assert d["config"]["nodes"] == 8 * 24 * 32 * 64
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
