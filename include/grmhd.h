@@ -229,7 +229,9 @@ int grmhd_kernel_times(grmhd_ctx* ctx, int reps, double* ms_out, double* flops_o
  * group therefore advances with the launches of a single instance, and all groups of a
  * step are recorded in one CUDA graph.  Instances may differ in spin, mass, element
  * count and radial range inside a group, and in anything across groups.  grids, phys
- * and opts are arrays of n entries.  All instances share the stream given here. */
+ * and opts are arrays of n entries.  All instances share the stream given here.
+ * n < 1, a NULL array or any instance's parameters outside the ranges grmhd_create
+ * accepts give GRMHD_EINVAL before any device work. */
 int grmhd_batch_create(int n, const grmhd_grid* grids, const grmhd_physics* phys,
                        const grmhd_opts* opts, void* cuda_stream, grmhd_batch** out);
 int grmhd_batch_num_groups(const grmhd_batch* b);

@@ -1614,6 +1614,14 @@ extern "C" int grmhd_batch_create(int n, const grmhd_grid* grids, const grmhd_ph
                                   const grmhd_opts* opts, void* cuda_stream, grmhd_batch** out) {
     if (!out || n < 1 || !grids || !phys || !opts) return GRMHD_EINVAL;
     *out = nullptr;
+    // every instance's parameters are checked before any device work
+    {
+        char msg[256] = {0};
+        for (int i = 0; i < n; i++) {
+            const int st = validate(&grids[i], &phys[i], &opts[i], msg);
+            if (st != GRMHD_OK) return st;
+        }
+    }
     grmhd_batch* b = new (std::nothrow) grmhd_batch();
     if (!b) return GRMHD_ENOMEM;
     if (cuda_stream) b->stream = (cudaStream_t)cuda_stream;

@@ -52,3 +52,56 @@ def test_host_only_calls(lib):
     assert lib.grmhd_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(o), None,
                             ctypes.byref(h)) == pkg.GRMHD_EUNSUPPORTED
     assert lib.grmhd_destroy(None) == pkg.GRMHD_EINVAL
+
+
+@pytest.mark.parametrize("which,field,value", [
+    ("g", "n_elem", 0), ("g", "n_r", 3), ("g", "n_r", 65), ("g", "n_theta", 3),
+    ("g", "n_theta", 129), ("g", "n_phi", 2), ("g", "n_phi", 130), ("g", "n_phi", 17),
+    ("g", "r_min", 0.0), ("g", "r_min", -1.0), ("g", "r_max", 1.0), ("g", "theta_min", -0.1),
+    ("g", "theta_max", 3.2), ("g", "elem_map", 2), ("g", "theta_basis", 2),
+    ("p", "M", 0.0), ("p", "a", 1.0), ("p", "a", -1.0), ("p", "gamma_eos", 1.0),
+    ("p", "rho_atm", 0.0), ("p", "eps_atm", -1.0),
+    ("o", "integrator", 2), ("o", "gauge", 2), ("o", "cfl", 0.0), ("o", "c2p_maxit", 0),
+    ("o", "c2p_tol", 0.0), ("o", "filter", 64), ("o", "filter", -1), ("o", "contraction", 2),
+    ("o", "coupling", 2), ("o", "glm", 2), ("o", "dealias23_theta", 2),
+])
+def test_invalid_parameters_rejected_before_device_work(lib, which, field, value):
+    """Each parameter outside its documented range gives GRMHD_EINVAL from grmhd_create and
+    from grmhd_batch_create, before any device call (this host has no GPU)."""
+    import paper_2508_18221_gb300 as pkg
+    g, p, o = pkg.defaults()
+    if (which, field) == ("g", "r_max"):
+        g.r_min = 2.0
+    setattr({"g": g, "p": p, "o": o}[which], field, value)
+    h = ctypes.c_void_p()
+    assert lib.grmhd_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(o), None,
+                            ctypes.byref(h)) == pkg.GRMHD_EINVAL
+    assert not h.value
+    assert lib.grmhd_batch_create(1, ctypes.byref(g), ctypes.byref(p), ctypes.byref(o), None,
+                                  ctypes.byref(h)) == pkg.GRMHD_EINVAL
+
+
+def test_fourier_theta_needs_the_whole_sphere(lib):
+    import paper_2508_18221_gb300 as pkg
+    g, p, o = pkg.defaults()
+    g.theta_basis = 1
+    g.theta_min, g.theta_max = 0.1, 3.0
+    h = ctypes.c_void_p()
+    assert lib.grmhd_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(o), None,
+                            ctypes.byref(h)) == pkg.GRMHD_EINVAL
+
+
+def test_empty_and_oversized_inputs_rejected(lib):
+    """Zero instances, zero nodes and a node count above the no-allocation limit are
+    argument errors, reported before any device call."""
+    import paper_2508_18221_gb300 as pkg
+    g, p, o = pkg.defaults()
+    h = ctypes.c_void_p()
+    assert lib.grmhd_batch_create(0, ctypes.byref(g), ctypes.byref(p), ctypes.byref(o), None,
+                                  ctypes.byref(h)) == pkg.GRMHD_EINVAL
+    dt = ctypes.c_double()
+    buf = (ctypes.c_double * 1)()
+    for n in (0, -1, 16_777_217):
+        assert lib.grmhd_cfl_dt_noalloc(buf, n, 0.1, 0.3, ctypes.byref(dt), None) == pkg.GRMHD_EINVAL
+    assert lib.grmhd_cfl_dt_noalloc(buf, 10, 0.0, 0.3, ctypes.byref(dt), None) == pkg.GRMHD_EINVAL
+    assert lib.grmhd_cfl_dt_noalloc(buf, 10, 0.1, -0.3, ctypes.byref(dt), None) == pkg.GRMHD_EINVAL
