@@ -105,10 +105,15 @@ def fourier_wavenumbers(n: int) -> np.ndarray:
 
 
 def dft(u: np.ndarray, axis: int) -> np.ndarray:
-    """hat U_k = sum_n U_n exp(-2 pi i k n / N) as an explicit O(N^2) sum."""
+    """hat U_k = sum_n U_n exp(-2 pi i k n / N) as an explicit O(N^2) sum.
+
+    The phase k n / N is reduced modulo 1 in integers (k n mod N) before it is scaled by
+    2 pi: the same table entry, but the angle stays below 2 pi, so each entry is accurate
+    to the unit roundoff (with the unreduced angle, up to 2 pi N, its rounding grows in
+    proportion to N)."""
     n = u.shape[axis]
     jj = np.arange(n)
-    F = np.exp(-2j * np.pi * np.outer(jj, jj) / n)
+    F = np.exp(-2j * np.pi * (np.outer(jj, jj) % n) / n)
     um = np.moveaxis(u, axis, 0)
     U = (F @ um.reshape(n, -1)).reshape(um.shape)
     return np.moveaxis(U, 0, axis)
@@ -118,7 +123,7 @@ def idft(U: np.ndarray, axis: int) -> np.ndarray:
     """U_n = (1/N) sum_k hat U_k exp(+2 pi i k n / N)."""
     n = U.shape[axis]
     jj = np.arange(n)
-    F = np.exp(2j * np.pi * np.outer(jj, jj) / n) / n
+    F = np.exp(2j * np.pi * (np.outer(jj, jj) % n) / n) / n          # phase reduced as in dft
     Um = np.moveaxis(U, axis, 0)
     u = (F @ Um.reshape(n, -1)).reshape(Um.shape)
     return np.moveaxis(u, 0, axis)

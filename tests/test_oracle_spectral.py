@@ -112,6 +112,23 @@ def test_fourier_deriv():
     np.testing.assert_allclose(sp.fourier_deriv(nyq, 0, 2), -(n // 2) ** 2 * nyq, atol=1e-10)
 
 
+def test_fourier_deriv_rounding_at_large_n():
+    """The DFT table's phase is reduced modulo 2 pi exactly (integer k n mod N): at 64 and
+    128 nodes the derivative of a single mode keeps the accuracy of the sums (a few
+    1e-14 of its amplitude), where the unreduced angle (up to 2 pi N) would cost an order
+    of magnitude more at low modes.  Checked against numpy's FFT too."""
+    for n in (64, 128):
+        ph = sp.fourier_nodes(n)
+        for k in (1, 2, n // 4, n // 2 - 1):
+            u = np.sin(k * ph + 0.3)
+            d = sp.fourier_deriv(u, 0)
+            assert np.abs(d - k * np.cos(k * ph + 0.3)).max() <= 1e-13 * k, (n, k)
+            kk = np.fft.fftfreq(n, 1.0 / n)
+            kk[n // 2] = 0
+            ref = np.real(np.fft.ifft(1j * kk * np.fft.fft(u)))
+            assert np.abs(d - ref).max() <= 1e-13 * k, (n, k)
+
+
 def test_filters():
     # sigma(0) = 1 and sigma(k_max) = e^{-36}
     assert sp.filter_sigma(0.0, 5.0) == 1.0
