@@ -18,6 +18,9 @@ Modules
                post-step filter, CFL time step, diagnostics, initial data
   xcts         approximate XCTS initial data: flat-Laplacian boundary-value problem,
                fixed-point relaxation on psi, the conformally flat slice
+  rounding     the oracle's own rounding floor per component (the oracle evaluated
+               again with one more rounding after every stage), which sets the parity
+               bar of components that are residues of cancelling terms
 
 Parity pins live in tests/test_oracle_*.py; functions without one say
 "parity unpinned" in their docstring.

@@ -15,6 +15,7 @@ from oracle import solver as so
 from oracle import spectral as sp
 from workloads import config
 
+from oracle import rounding as fpf
 import test_gpu_parity as tp
 from test_gpu_parity import pkg  # noqa: F401  (fixture)
 
@@ -99,7 +100,9 @@ def test_fourier_theta_rhs_parity(pkg, kw, tol):  # noqa: F811
     ctx = tp._ctx(pkg, cfg, **kw)
     R = tp._gpu_rhs(pkg, ctx, U)
     Rref = so.rhs(U, g, p)
-    worst = tp.assert_parity(R, Rref, f"fourier theta rhs {kw}", tol=tol, U=U, g=g)
+    worst, _ = tp.assert_parity(R, Rref, f"fourier theta rhs {kw}", lambda X: so.rhs(X, g, p), U, tol=tol,
+                                eps=fpf.EPS32 if kw.get("precision") else fpf.EPS64,
+                                kappa=1.0 if kw.get("precision") else fpf.KAPPA)
     if kw.get("precision"):
         assert worst > 1e-12          # the tensor-core path really ran
     ctx.close()
@@ -111,12 +114,11 @@ def test_fourier_theta_rhs_parity_ragged(pkg):  # noqa: F811
     g, p, U = _state(cfg)
     ctx = tp._ctx(pkg, cfg)
     R = tp._gpu_rhs(pkg, ctx, U)
-    tp.assert_parity(R, so.rhs(U, g, p), "fourier theta rhs ragged", U=U, g=g)
+    tp.assert_parity(R, so.rhs(U, g, p), "fourier theta rhs ragged", lambda X: so.rhs(X, g, p), U)
     ctx.close()
 
 
 def test_fourier_theta_glm_rhs_parity(pkg):  # noqa: F811
-    tp.TENSOR_OF[so.I_PSI] = [so.I_PSI]
     cfg = _fcfg(n_elem=2, n_r=8, n_theta=10, n_phi=8)
     g, p, U = _state(cfg, glm=1)
     U[so.I_PSI] = 1e-4 * np.cos(g.T) * np.cos(g.P) * (g.R / g.R.max())
@@ -125,7 +127,7 @@ def test_fourier_theta_glm_rhs_parity(pkg):  # noqa: F811
     R = tp._gpu_rhs(pkg, ctx, U)
     Rref = so.rhs(U, g, p)
     assert np.abs(Rref[so.I_PSI]).max() > 0
-    tp.assert_parity(R, Rref, "fourier theta glm rhs", U=U, g=g, groups=((0, 24), (24, 32), (32, 33)))
+    tp.assert_parity(R, Rref, "fourier theta glm rhs", lambda X: so.rhs(X, g, p), U)
     ctx.close()
 
 
@@ -141,8 +143,8 @@ def test_fourier_theta_step_parity(pkg, filt):  # noqa: F811
     ctx.step(dt, 2)
     got = np.empty(U.size)
     ctx.get_state(got, False)
-    ref = so.rk_step(so.rk_step(U, dt, g, p), dt, g, p)
-    tp.assert_parity(got.reshape(U.shape), ref, f"fourier theta 2 steps filter {filt}", U=U)
+    two = lambda X: so.rk_step(so.rk_step(X, dt, g, p), dt, g, p)  # noqa: E731
+    tp.assert_parity(got.reshape(U.shape), two(U), f"fourier theta 2 steps filter {filt}", two, U, trials=2)
     ctx.close()
 
 
@@ -217,14 +219,13 @@ def test_fourier_theta_batch_equals_single_instances(pkg):  # noqa: F811
 def test_fourier_theta_glm_mixed_rhs(pkg):  # noqa: F811
     """GLM cleaning with split-BF16 x3 contractions on the Fourier theta basis: the mixed
     bar 2e-6."""
-    tp.TENSOR_OF[so.I_PSI] = [so.I_PSI]
     cfg = _fcfg(n_elem=2, n_r=8, n_theta=10, n_phi=8)
     g, p, U = _state(cfg, glm=1)
     U[so.I_PSI] = 1e-4 * np.cos(g.T) * np.cos(g.P) * (g.R / g.R.max())
     ctx = tp._ctx(pkg, cfg, glm=1, precision=1)
     R = tp._gpu_rhs(pkg, ctx, U)
-    tp.assert_parity(R, so.rhs(U, g, p), "fourier theta glm mixed rhs", tol=2e-6, U=U, g=g,
-                     groups=((0, 24), (24, 32), (32, 33)))
+    tp.assert_parity(R, so.rhs(U, g, p), "fourier theta glm mixed rhs", lambda X: so.rhs(X, g, p), U,
+                     tol=2e-6, eps=fpf.EPS32, kappa=1.0)
     ctx.close()
 
 
@@ -239,8 +240,8 @@ def test_fourier_theta_split_coupling_rk4(pkg):  # noqa: F811
     ctx.step(dt, 2)
     got = np.empty(U.size)
     ctx.get_state(got, False)
-    ref = so.rk_step(so.rk_step(U, dt, g, p), dt, g, p)
-    tp.assert_parity(got.reshape(U.shape), ref, "fourier theta split rk4", U=U)
+    two = lambda X: so.rk_step(so.rk_step(X, dt, g, p), dt, g, p)  # noqa: E731
+    tp.assert_parity(got.reshape(U.shape), two(U), "fourier theta split rk4", two, U, trials=2)
     ctx.close()
 
 
@@ -252,5 +253,6 @@ def test_fourier_theta_rhs_parity_full_size(pkg):  # noqa: F811
     g, p, U = _state(cfg)
     ctx = tp._ctx(pkg, cfg)
     R = tp._gpu_rhs(pkg, ctx, U)
-    tp.assert_parity(R, so.rhs(U, g, p), "fourier theta rhs c2f full size", U=U, g=g)
+    tp.assert_parity(R, so.rhs(U, g, p), "fourier theta rhs c2f full size", lambda X: so.rhs(X, g, p), U,
+                     trials=2)
     ctx.close()

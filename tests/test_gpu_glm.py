@@ -7,13 +7,12 @@ import pytest
 from oracle import solver as so
 from workloads import config
 
+from oracle import rounding as fpf
 import test_gpu_parity as tp
 from test_gpu_parity import pkg  # noqa: F401  (fixture)
 
 pytestmark = pytest.mark.gpu
 
-tp.TENSOR_OF[so.I_PSI] = [so.I_PSI]
-GROUPS = ((0, 24), (24, 32), (32, 33))
 
 
 def _glm_state(cfg, **kw):
@@ -32,7 +31,7 @@ def test_glm_rhs_parity(pkg, contraction):  # noqa: F811
     R = tp._gpu_rhs(pkg, ctx, U)
     Rref = so.rhs(U, g, p)
     assert np.abs(Rref[so.I_PSI]).max() > 0
-    tp.assert_parity(R, Rref, f"glm rhs contraction {contraction}", U=U, g=g, groups=GROUPS)
+    tp.assert_parity(R, Rref, f"glm rhs contraction {contraction}", lambda X: so.rhs(X, g, p), U)
     ctx.close()
 
 
@@ -46,8 +45,8 @@ def test_glm_step_parity(pkg):  # noqa: F811
     ctx.step(dt, 2)
     got = np.empty(U.size)
     ctx.get_state(got, False)
-    ref = so.rk_step(so.rk_step(U, dt, g, p), dt, g, p)
-    tp.assert_parity(got.reshape(U.shape), ref, "glm 2 steps", U=U, groups=GROUPS)
+    two = lambda X: so.rk_step(so.rk_step(X, dt, g, p), dt, g, p)  # noqa: E731
+    tp.assert_parity(got.reshape(U.shape), two(U), "glm 2 steps", two, U, trials=2)
     ctx.close()
 
 
@@ -58,5 +57,5 @@ def test_glm_mixed_rhs(pkg):  # noqa: F811
     ctx = tp._ctx(pkg, cfg, glm=1, precision=1)
     R = tp._gpu_rhs(pkg, ctx, U)
     Rref = so.rhs(U, g, p)
-    tp.assert_parity(R, Rref, "glm mixed rhs", tol=2e-6, U=U, g=g, groups=GROUPS)
+    tp.assert_parity(R, Rref, "glm mixed rhs", lambda X: so.rhs(X, g, p), U, tol=2e-6, eps=fpf.EPS32, kappa=1.0)
     ctx.close()

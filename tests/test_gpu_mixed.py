@@ -6,8 +6,11 @@ Tolerances follow from the arithmetic: the split-BF16 contraction keeps about 24
 significant bits (an FP32 contraction: relative error ~ K 2^-24 ~ 1e-6 of |D||u|), TF32
 keeps 11 (~5e-4 per contraction, compounded by the second derivatives taken from TF32
 first derivatives and by ||D|| ~ N^2: measured 1.2e-2); the right-hand side inherits that
-relative to the scale s_v of the FP64 parity test (max |rhs_v|, state / dx_min over the
-tensor).  n steps of size dt move the state by at most n dt tol_rhs / dx_min relative."""
+relative to max |rhs_v|, or to the rounding floor of the component measured at the
+unit roundoff of the mode's reduced-precision stages (2^-23 for the FP32 stages of
+split-BF16, 2^-10 for TF32 operands) where the component is a residue of cancelling terms
+(the parity bar of test_gpu_parity with that unit).  n steps of size dt move the state by
+at most n dt tol_rhs / dx_min relative to the state's tensor scale."""
 import os
 import numpy as np
 import pytest
@@ -15,12 +18,15 @@ import pytest
 from oracle import solver as so
 from workloads import config
 
-from test_gpu_parity import _ctx, _oracle, _gpu_rhs, assert_parity, pkg  # noqa: F401
+from test_gpu_parity import _ctx, _oracle, _gpu_rhs, assert_parity, pkg, TENSOR_OF  # noqa: F401
+from oracle import rounding as fpf
 
 pytestmark = pytest.mark.gpu
 
 
 TOL_RHS = {1: 2e-6, 2: 5e-2}
+# unit of the reduced-precision stages: FP32 results (split BF16), TF32 operands
+EPS_MODE = {1: fpf.EPS32, 2: 2.0 ** -10}
 
 
 @pytest.mark.parametrize("precision,tol", [(1, TOL_RHS[1]), (2, TOL_RHS[2])])
@@ -33,7 +39,8 @@ def test_mixed_rhs_against_oracle(pkg, precision, tol, name):
     ctx = pkg.Context(grid, phys, opts, torch.cuda.current_stream().cuda_stream)
     R = _gpu_rhs(pkg, ctx, U)
     Rref = so.rhs(U, g, p)
-    worst = assert_parity(R, Rref, f"mixed {precision} rhs {name}", tol=tol, U=U, g=g)
+    worst, _ = assert_parity(R, Rref, f"mixed {precision} rhs {name}", lambda X: so.rhs(X, g, p), U,
+                             tol=tol, eps=EPS_MODE[precision], kappa=1.0)
     assert worst > 1e-12          # the tensor-core path really ran (not the FP64 one)
     ctx.close()
 
@@ -57,7 +64,14 @@ def test_mixed_step_close_to_fp64(pkg, precision):
         ctx.close()
     from test_gpu_parity import min_spacing
     tol = 10 * 2e-3 * TOL_RHS[precision] / min_spacing(g)
-    assert_parity(out[1], out[0], f"10 steps precision {precision}", tol=tol, U=U)
+    # (the Gamma-driver B^i, zero at the start, takes the scale of Gammatilde^i, whose
+    # time derivative drives it)
+    group = dict(TENSOR_OF)
+    group.update({v: list(range(14, 17)) + list(range(21, 24)) for v in range(21, 24)})
+    for v in range(U.shape[0]):
+        scale = max(np.abs(out[0][w]).max() for w in group[v])
+        err = np.abs(out[1][v] - out[0][v]).max()
+        assert err <= tol * scale, (precision, v, err, scale)
 
 
 def truncation_estimate(U, g):
@@ -91,7 +105,8 @@ def test_precision_variant_report(pkg, capsys):
     tensor's components against the tensor's truncation level); TF32 is reported."""
     import json
     import torch
-    from test_gpu_parity import TENSORS
+    from test_gpu_parity import TENSORS as ALL_TENSORS
+    TENSORS = [t for t in ALL_TENSORS if max(t) < 32]
     cfg = config("c3")
     g, p, U = _oracle(cfg)
     dt = so.cfl_dt(U, g, p)
@@ -138,6 +153,11 @@ def test_precision_variant_report(pkg, capsys):
     for n in (1, 100):
         assert max(report[f"p0_n{n}"]["l2"]) <= 1e-9
     r = report["p1_n100"]
+    with capsys.disabled():
+        # headroom of the split-BF16 x3 state under the truncation level, per tensor
+        print("p1_n100 truncation level / L2 error per tensor:",
+              ", ".join(f"{list(t)[0]}: {r['trunc_tensor'][i] / r['l2_tensor'][i]:.2f}"
+                        for i, t in enumerate(TENSORS) if r["l2_tensor"][i] > 0))
     for i, t in enumerate(TENSORS):
         if r["trunc_tensor"][i] > 0:
             assert r["l2_tensor"][i] <= r["trunc_tensor"][i], (list(t), r["l2_tensor"][i], r["trunc_tensor"][i])

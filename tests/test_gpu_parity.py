@@ -4,9 +4,17 @@ Every case builds the state with the oracle's initial data (exact Kerr-Schild BS
 slice + primitive profiles of the workload generator), hands the same array to the
 C-ABI library (grmhd_set_state) and compares.
 
-Tolerance (FP64 bar 1e-11): per variable v, max|gpu_v - oracle_v| <= 1e-11 * s_v with
-s_v = max(max|oracle_v|, max|U| over v's tensor / dx_min, 1e-6 * group maximum); see
-assert_parity.
+Bar (FP64: 1e-11 relative on every component): per variable v,
+    max|gpu_v - oracle_v| <= max(1e-11, KAPPA floor_v) max|oracle_v|,
+where floor_v is the oracle's own FP64 rounding floor of that component, measured in the
+test by evaluating the oracle again with one more rounding at the unit roundoff after
+every stage of its computation (oracle/rounding.py).  For a component that is not a residue of
+cancelling terms the floor is ~1e-15 and the bar is the plain 1e-11 of max|oracle_v|; for a
+cancellation residue (the right-hand side of the metric of a stationary Kerr-Schild slice,
+the phi derivative of a nearly axisymmetric flux) rounding alone moves the oracle by more
+than 1e-11 of the residue, and the bar is KAPPA times that measured movement.  Every case
+prints, per variable, the plain ratio max|gpu_v - oracle_v| / max|oracle_v|, the floor and
+the ratio to the bar.
 """
 import os
 
@@ -15,6 +23,8 @@ import pytest
 
 from oracle import solver as so
 from workloads import config
+
+from oracle import rounding as fpf
 
 pytestmark = pytest.mark.gpu
 
@@ -49,18 +59,16 @@ def _oracle(cfg, **kw):
     return so.workload_state(cfg, **pk)
 
 
-# canonical variables grouped by the tensor they are components of; the Gamma-driver
-# B^i shares the scale of Gammatilde^i (its right-hand side contains d_t Gammatilde^i)
+# canonical variables grouped by the tensor they are components of (a component whose
+# oracle value is identically zero is compared against its tensor's scale)
 TENSORS = [range(0, 6), [6], range(7, 13), [13], range(14, 17), [17], range(18, 21),
-           range(21, 24), [24], range(25, 28), [28], range(29, 32)]
+           range(21, 24), [24], range(25, 28), [28], range(29, 32), [32]]
 TENSOR_OF = {v: list(t) for t in TENSORS for v in t}
-for _v in range(21, 24):
-    TENSOR_OF[_v] = list(range(14, 17)) + list(range(21, 24))
 
 
 def min_spacing(g):
     """Smallest node spacing min(dr, r dtheta, r sin(theta) dphi) of the grid (the CFL
-    spacing), the Delta x_min of the parity normalisation."""
+    spacing)."""
     p = g.p
     h = np.inf
     for e in range(p.n_elem):
@@ -70,31 +78,55 @@ def min_spacing(g):
     return h
 
 
-def assert_parity(got, ref, what, tol=TOL, U=None, g=None, groups=((0, 24), (24, 32))):
-    """Per-variable normwise check: max|got_v - ref_v| <= tol * s_v with
-    s_v = max(max|ref_v|, (lambda/dx_min) max|U| over v's tensor, 1e-6 * group maximum),
-    lambda = 1 (light speed) and dx_min the grid's smallest node spacing (the
-    normalisation for right-hand sides that are truncation residues of much larger
-    cancelling terms, e.g. the stationary Kerr-Schild metric, where rounding in the
-    derivative operators -- ||D|| ~ 1/dx_min -- sets the difference).  The tensor is
-    used because a component can vanish in these coordinates (gammatilde_{r theta},
-    beta^phi) while its right-hand side is built from the others; the group term covers
-    tensors that are identically zero.  Returns the worst ratio and the worst ratio
-    against the plain max|ref_v| scale."""
-    worst = 0.0
-    inv_dx = 1.0 / min_spacing(g) if g is not None else 1.0
-    for lo, hi in groups:
-        gU = max(np.abs(U[v]).max() for v in range(lo, hi)) if U is not None else 0.0
-        gR = max(np.abs(ref[v]).max() for v in range(lo, hi))
-        floor = 1e-6 * max(gU, gR)
-        for v in range(lo, hi):
-            sU = max(np.abs(U[w]).max() for w in TENSOR_OF[v]) if U is not None else 0.0
-            s = max(np.abs(ref[v]).max(), sU * inv_dx, floor)
-            err = np.abs(got[v] - ref[v]).max()
-            rel = err / s if s > 0 else err
-            worst = max(worst, rel)
-            assert rel <= tol, f"{what}: variable {v} error {err:.3e} (scale {s:.3e}) rel {rel:.3e}"
-    return worst
+def _report_line(what, rows):
+    out = os.environ.get("GRMHD_REPORT_DIR")
+    if out:
+        import json
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "parity_ratios.jsonl"), "a") as fh:
+            fh.write(json.dumps({"case": what, "vars": rows}) + "\n")
+
+
+def assert_parity(got, ref, what, fn, U, tol=TOL, eps=fpf.EPS64, trials=3, kappa=fpf.KAPPA):
+    """Per variable v: max|got_v - ref_v| <= max(tol, kappa floor_v) max|ref_v|, floor_v
+    the oracle's rounding floor of v at unit roundoff eps (fpf.floor of fn at U; fn(U) is
+    the oracle result `ref`).  The mixed-precision modes pass the unit of their FP32 stages
+    and kappa = 1 (their floor rounds every stage at that unit, the FP64 ones included).
+    A variable whose oracle value is identically zero must match to tol times its
+    tensor's largest value (exactly, when that is zero too).
+    Prints per variable the plain ratio, the floor and the ratio to the bar; returns
+    (worst plain ratio, worst ratio to the bar)."""
+    nv = ref.shape[0]
+    _, fl = fpf.floor(fn, U, trials=trials, eps=eps, ref=ref)
+    worst_plain, worst_bar, rows, bad = 0.0, 0.0, [], []
+    for v in range(nv):
+        m = float(np.abs(ref[v]).max())
+        err = float(np.abs(got[v] - ref[v]).max())
+        if not np.isfinite(err):
+            bad.append(f"variable {v}: non-finite result")
+            continue
+        if m > 0:
+            bar = max(tol, kappa * fl[v]) * m
+            plain = err / m
+        else:
+            bar = tol * max(float(np.abs(ref[w]).max()) for w in TENSOR_OF.get(v, [v]) if w < nv)
+            plain = 0.0 if err == 0 else float("inf")
+        r = err / bar if bar > 0 else (0.0 if err == 0 else float("inf"))
+        worst_plain = max(worst_plain, plain if m > 0 else 0.0)
+        worst_bar = max(worst_bar, r)
+        rows.append({"v": v, "plain": plain, "floor": float(fl[v]), "err_over_bar": r})
+        if not r <= 1.0:
+            bad.append(f"variable {v}: error {err:.3e}, max|ref| {m:.3e}, plain {plain:.3e}, "
+                       f"floor {fl[v]:.2e}, bar {bar:.3e}")
+    resid = [row["v"] for row in rows if row["floor"] * kappa > tol]
+    print(f"\n[parity] {what}: worst plain ratio {worst_plain:.2e}, worst error/bar {worst_bar:.3f}; "
+          f"variables with a floor above tol/{kappa:g} (cancellation residues): {resid}")
+    for row in rows:
+        print(f"[parity]   v{row['v']:2d} plain {row['plain']:.2e} floor {row['floor']:.1e} "
+              f"err/bar {row['err_over_bar']:.3f}")
+    _report_line(what, rows)
+    assert not bad, f"{what}: " + "; ".join(bad)
+    return worst_plain, worst_bar
 
 
 def _gpu_rhs(pkg, ctx, U):
@@ -137,7 +169,7 @@ def test_rhs_parity(pkg, name, kw):
     ctx = _ctx(pkg, cfg, **kw)
     R = _gpu_rhs(pkg, ctx, U)
     Rref = so.rhs(U, g, p)
-    assert_parity(R, Rref, f"rhs {name} {kw}", U=U, g=g)
+    assert_parity(R, Rref, f"rhs {name} {kw}", lambda X: so.rhs(X, g, p), U)
     ctx.close()
 
 
@@ -193,9 +225,10 @@ def test_step_parity(pkg, integrator, contraction, coupling):
     ctx.step(dt, 2)
     got = np.empty(U.size)
     ctx.get_state(got, False)
-    ref = so.rk_step(so.rk_step(U, dt, g, p), dt, g, p)
-    assert_parity(got.reshape(U.shape), ref,
-                  f"2 steps integrator {integrator} contraction {contraction} coupling {coupling}", U=U)
+    two = lambda X: so.rk_step(so.rk_step(X, dt, g, p), dt, g, p)  # noqa: E731
+    assert_parity(got.reshape(U.shape), two(U),
+                  f"2 steps integrator {integrator} contraction {contraction} coupling {coupling}", two, U,
+                  trials=2)
     ctx.close()
 
 
@@ -270,5 +303,5 @@ def test_rhs_parity_full_size(pkg):
     ctx = _ctx(pkg, cfg)
     R = _gpu_rhs(pkg, ctx, U)
     Rref = so.rhs(U, g, p)
-    assert_parity(R, Rref, "rhs c2 full size", U=U, g=g)
+    assert_parity(R, Rref, "rhs c2 full size", lambda X: so.rhs(X, g, p), U, trials=2)
     ctx.close()

@@ -32,8 +32,9 @@ def test_wait_limit_reports_timeout_and_context_survives(pkg):  # noqa: F811
     assert "timed out" in ctx.lib.grmhd_last_error(ctx.h).decode()
     R1 = tp._gpu_rhs(pkg, ctx, U)
     Rref = so.rhs(U, g, p)
-    tp.assert_parity(R0, Rref, "rhs before the timed-out wait", U=U, g=g)
-    tp.assert_parity(R1, Rref, "rhs after the timed-out wait", U=U, g=g)
+    fn = lambda X: so.rhs(X, g, p)  # noqa: E731
+    tp.assert_parity(R0, Rref, "rhs before the timed-out wait", fn, U)
+    tp.assert_parity(R1, Rref, "rhs after the timed-out wait", fn, U)
     ctx.close()
     # a context without digit-slice operators has nothing to stall
     ctx = tp._ctx(pkg, cfg, contraction=1)
@@ -66,7 +67,12 @@ def test_resume_after_destroy(pkg):  # noqa: F811
     got = np.empty(U.size)
     ctx.get_state(got, False)
     ctx.close()
-    tp.assert_parity(got.reshape(U.shape), ref.reshape(U.shape), "resumed run", tol=1e-11, U=U)
+    # the resumed run restarts the primitive recovery from a bracket (set_state), so it
+    # differs from the uninterrupted run by rounding: the parity bar with the oracle's
+    # floor of four steps
+    four = lambda X: so.rk_step(so.rk_step(so.rk_step(so.rk_step(X, dt, g, p), dt, g, p), dt, g, p),  # noqa: E731
+                                dt, g, p)
+    tp.assert_parity(got.reshape(U.shape), ref.reshape(U.shape), "resumed run", four, U, trials=2)
 
 
 def test_unphysical_states_are_floored_not_trapped(pkg):  # noqa: F811

@@ -47,7 +47,10 @@ def test_xcts_matches_oracle(pkg):  # noqa: F811
     np.testing.assert_allclose(ch[:3], ch_ref[:3], rtol=1e-6)
     got = np.empty(U_ref.size)
     ctx.get_state(got, False)
-    tp.assert_parity(got.reshape(U_ref.shape), U_ref, "xcts state", U=U_ref)
+    # floor of the slice: the oracle's solve again from the density rounded once more
+    tp.assert_parity(got.reshape(U_ref.shape), U_ref, "xcts state",
+                     lambda rho: xcts.xcts_state(g, p, dict(prim, rho=rho), iters=10)[0], prim["rho"],
+                     trials=2)
     ctx.close()
 
 
@@ -74,18 +77,7 @@ def test_xcts_rhs_of_the_slice(pkg):  # noqa: F811
     ctx.get_state(U, False)
     U = U.reshape((32,) + g.shape)
     R = tp._gpu_rhs(pkg, ctx, U)
-    # Atilde and K vanish on this slice, so their right-hand sides (Ricci tensor of
-    # gammatilde, second derivatives of the lapse) take the scale of the fields they are
-    # built from
-    saved = dict(tp.TENSOR_OF)
-    try:
-        for v in range(so.I_AT, so.I_AT + 6):
-            tp.TENSOR_OF[v] = list(range(0, 6)) + list(range(so.I_AT, so.I_AT + 6))
-        tp.TENSOR_OF[so.I_K] = [so.I_K, so.I_ALPHA, so.I_PHI]
-        tp.assert_parity(R, so.rhs(U, g, p), "rhs of the xcts slice", U=U, g=g)
-    finally:
-        tp.TENSOR_OF.clear()
-        tp.TENSOR_OF.update(saved)
+    tp.assert_parity(R, so.rhs(U, g, p), "rhs of the xcts slice", lambda X: so.rhs(X, g, p), U)
     ctx.close()
 
 

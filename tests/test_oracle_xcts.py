@@ -85,7 +85,11 @@ def test_fixed_point_contracts():
     g = so.Grid(p)
     prim = primitive_profiles(cfg, g.R, g.T, g.P)
     psi, ch = xcts.solve_psi(g, p, prim["rho"], iters=12)
-    ratios = np.array(ch[2:8]) / np.array(ch[1:7])
+    # contraction while the change is above the rounding floor of psi ~ 1 (a few 1e-14)
+    ch = np.array(ch)
+    k = int(np.argmax(ch < 1e-12))
+    assert k >= 6, ch
+    ratios = ch[2:k] / ch[1:k - 1]
     assert np.all(ratios < 0.1) and ch[-1] < 1e-12, ch
     assert np.all(psi > 1.0 + p.M / (2.0 * g.R) - 1e-12)   # positive density raises psi
 
