@@ -812,24 +812,26 @@ extern "C" int grmhd_coords(const grmhd_ctx* c, double* r, double* th, double* p
 //
 // Accumulators of the digit-slice kernel: with five, the folded one's FP32 additions leave
 // an error of about K 2^-53 of sum_j |D_ij| max_j |u_j| per contraction (3.5e-15 / 7.5e-15
-// / 1.4e-14 at 24 / 64 / 128 nodes); the second derivatives compose two contractions and
-// amplify it with the operator's norm, ~N^2 per application on Chebyshev nodes.  Measured
-// on 4-node-thin grids against the oracle, the right-hand side stays within the 1e-11 bar
-// up to 32 Chebyshev nodes (6.7e-12 radial; 40 nodes: 2.4e-11) and up to 128 Fourier nodes
-// (2.8e-12).  Chebyshev derivatives above 32 nodes therefore take a sixth accumulator that
-// keeps the digit-order sum 6 exact (combine6 in the kernel): operator error 7e-16 of the
-// bound, right-hand side within 7.1e-12 up to 64 nodes.  Above 64 Chebyshev nodes the
-// digit slices' remaining error (the fixed-point rounding of each line against its
-// largest value) reaches 1.5e-11 at 96 theta nodes, against 9.5e-12 for the FP64 units,
-// which take those derivatives.  force_fx (the test hook): the digit slices whenever the
-// image exists.
+// / 1.4e-14 at 24 / 64 / 128 nodes), the worst case of an FP64 dot product.  A derivative
+// whose terms cancel (the phi derivative of a flux that is constant in phi up to small
+// noise; the second derivatives, which compose two contractions and amplify the first
+// one's error by the operator norm, ~N^2 on Chebyshev nodes) carries that error into the
+// right-hand side: on the 393,216-node instance the momentum and energy equations landed
+// at 1.0-1.5e-11 of their largest value with five accumulators, against 1-3e-12 for the
+// FP64 units.  Every derivative therefore takes a sixth accumulator that keeps the
+// digit-order sum 6 exact (combine6 in the kernel): operator error 7e-16 of the bound.
+// The filter (one contraction of a smooth state, no cancellation) keeps five.  Above 64
+// Chebyshev nodes the digit slices' remaining error (the fixed-point rounding of each line
+// against its largest value) reaches 1.5e-11 at 96 theta nodes, against 9.5e-12 for the
+// FP64 units, which take those derivatives.  force_fx (the test hook): the digit slices
+// whenever the image exists.
 static cudaError_t contract(grmhd_ctx* c, int dir, int filter, const DerivJob* jobs, int njobs,
                             bool force_fx = false) {
     if (dir == 1 && c->ft) return cudaErrorInvalidValue;   // theta_fourier below
     const int Ns[3] = {c->d.Nr, c->d.Nt, c->d.Np};
     const bool cheb_d = !filter && dir < 2;
     const uint8_t* fx = filter ? c->fx_f[dir] : ((cheb_d && Ns[dir] > 64 && !force_fx) ? nullptr : c->fx_d[dir]);
-    const int nacc = (cheb_d && Ns[dir] > 32) ? 6 : 5;
+    const int nacc = filter ? 5 : 6;
     if (fx) return launch_contract_fx(dir, c->d, jobs, njobs, fx, (dir == 0 && !filter) ? c->fx_estride : 0,
                                       c->tc_err, c->stream, 0, nacc);
     const double* split = filter ? c->Fs[dir] : c->Ds[dir];
@@ -858,7 +860,7 @@ static cudaError_t theta_fourier(grmhd_ctx* c, int filter, int stage, int fold_o
             const uint8_t* fx = filter ? c->fx_ft[h] : c->fx_dt[h];
             const double* split = filter ? c->Fts[h] : c->Dts[h];
             const DerivJob* jb = c->jobs + c->job_fy[h] + i0;
-            if (fx) e = launch_contract_fx(1, c->dh, jb, n, fx, 0, c->tc_err, c->stream);
+            if (fx) e = launch_contract_fx(1, c->dh, jb, n, fx, 0, c->tc_err, c->stream, 0, filter ? 5 : 6);
             else if (split) e = launch_deriv_eo(1, c->dh, jb, n, split, filter ? 1 : -1, nullptr, c->stream);
             else e = launch_deriv(1, c->dh, jb, n, filter ? c->Ft2[h] : c->Dt2[h], nullptr, c->stream);
         }

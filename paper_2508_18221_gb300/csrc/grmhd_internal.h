@@ -109,7 +109,7 @@ bool fx_supported(int dir, int N);   // 2..128 nodes (even in phi)
 cudaError_t fx_init();
 // stall = 1 (test of the wait limits only): the tiles are never staged, so every wait of the
 // kernel runs out (about 0.5 s), the CTAs leave and *err is set.  nacc: TMEM accumulators,
-// 5, or 6 (r and theta only) for an exact accumulator of the digit-order sum 6
+// 5, or 6 for an exact accumulator of the digit-order sum 6 (every derivative; 5: filters)
 cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int njobs, const uint8_t* op_img,
                                long long img_estride, int* err, cudaStream_t s, int stall = 0, int nacc = 5);
 cudaError_t launch_deriv(int dir, const Dims& d, const DerivJob* jobs_dev, int njobs,

@@ -738,13 +738,14 @@ cudaError_t fx_init() {
     if ((e = set_attr_fx<0, 6>()) != cudaSuccess) return e;
     if ((e = set_attr_fx<1, NACC>()) != cudaSuccess) return e;
     if ((e = set_attr_fx<1, 6>()) != cudaSuccess) return e;
+    if ((e = set_attr_fx<2, 6>()) != cudaSuccess) return e;
     return set_attr_fx<2, NACC>();
 }
 
 cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int njobs, const uint8_t* img,
                                long long img_estride, int* err, cudaStream_t s, int stall, int nacc) {
     if (njobs <= 0) return cudaSuccess;
-    if (nacc != NACC && !(nacc == 6 && dir < 2)) return cudaErrorNotSupported;
+    if (nacc != NACC && nacc != 6) return cudaErrorNotSupported;
     const int N = dir == 0 ? d.Nr : (dir == 1 ? d.Nt : d.Np);
     if (!fx_supported(dir, N)) return cudaErrorNotSupported;
     // r and theta tiles are staged with bulk copies of row segments: 16-byte alignment
@@ -783,6 +784,7 @@ cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int
     else if (dir == 0) k_contract_fx<0, NACC><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
     else if (dir == 1 && nacc == 6) k_contract_fx<1, 6><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
     else if (dir == 1) k_contract_fx<1, NACC><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
+    else if (nacc == 6) k_contract_fx<2, 6><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
     else k_contract_fx<2, NACC><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
     return cudaGetLastError();
 }
