@@ -4,6 +4,7 @@
 // lambda = |beta|_gamma + max(alpha, sqrt(2 alpha)).  The reduction runs in two passes
 // (per-block maxima, then one block over the maxima) and keeps its per-block maxima in
 // the file-scope device array below instead of memory obtained from cudaMalloc.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <math.h>
@@ -23,8 +24,40 @@ __device__ __align__(256) double g_cfl_partials[kMaxBlocks];
 
 // Device address of g_cfl_partials per device ordinal, looked up on the first call made
 // with that device current.  In host code the symbol itself is only a host-side stand-in.
+// The address belongs to the device's context: a cudaDeviceReset destroys that context
+// and the next one may load the module elsewhere, so each entry also records the unique
+// id of the context it was looked up in and is looked up again when the id differs.
 double* g_partials_addr[kMaxDevices];
+unsigned long long g_partials_ctx[kMaxDevices];
 std::mutex g_setup_lock;
+
+typedef CUresult (*ctx_get_current_fn)(CUcontext*);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long*);
+ctx_get_current_fn g_ctx_get_current;
+ctx_get_id_fn g_ctx_get_id;
+bool g_driver_looked_up;
+
+// Unique id of the current context (driver entry points found through the runtime, so
+// the library does not link the driver library); 0 when the driver does not provide it.
+unsigned long long current_context_id() {
+    if (!g_driver_looked_up) {
+        g_driver_looked_up = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<ctx_get_current_fn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<ctx_get_id_fn>(f);
+    }
+    if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&c) != CUDA_SUCCESS || !c || g_ctx_get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 __global__ void __launch_bounds__(kBlock) k_cfl_partial(long long P, const double* __restrict__ U,
                                                         double* __restrict__ partials) {
@@ -81,10 +114,15 @@ extern "C" int grmhd_cfl_dt_noalloc(const double* state, long long n_points, dou
     double* partials = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_setup_lock);
-        if (!g_partials_addr[dev]) {
+        // (before the runtime's first call on this thread no context may be current: the
+        // id is then 0 and the lookup below, which makes the primary context current,
+        // runs and records the id it finds afterwards)
+        unsigned long long ctx_id = current_context_id();
+        if (!g_partials_addr[dev] || ctx_id == 0 || g_partials_ctx[dev] != ctx_id) {
             void* addr = nullptr;
             if (cudaGetSymbolAddress(&addr, g_cfl_partials) != cudaSuccess || !addr) return GRMHD_ECUDA;
             g_partials_addr[dev] = static_cast<double*>(addr);
+            g_partials_ctx[dev] = current_context_id();
         }
         partials = g_partials_addr[dev];
     }

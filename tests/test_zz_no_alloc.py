@@ -54,14 +54,21 @@ def test_cfl_noalloc_matches_context_call():
     ctx.get_state(state, True)
     dt_ref = ctx.cfl_dt()
     hmin = _hmin(r, t, cfg.n_r, cfg.n_theta, cfg.n_phi, cfg.n_elem)
+    outs = [torch.full((1,), -1.0, dtype=torch.float64, device="cuda") for _ in range(3)]
+    # a warm-up call (the first call on a device looks up the scratch array's address and
+    # may load the library's device code), then the device's free memory must not move
+    assert lib.grmhd_cfl_dt_noalloc(state.data_ptr(), ctx.n_points, hmin, cfg.cfl,
+                                    outs[2].data_ptr(), None) == pkg.GRMHD_OK
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
     dts = []
     for call in range(2):
-        out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
         st = lib.grmhd_cfl_dt_noalloc(state.data_ptr(), ctx.n_points, hmin, cfg.cfl,
-                                      out.data_ptr(), None)
+                                      outs[call].data_ptr(), None)
         assert st == pkg.GRMHD_OK, (call, st)
         torch.cuda.synchronize()
-        dts.append(float(out.item()))
+        dts.append(float(outs[call].item()))
+    assert torch.cuda.mem_get_info()[0] == free_before, "the entry point allocated device memory"
     for dt in dts:
         np.testing.assert_allclose(dt, dt_ref, rtol=1e-13)
     assert dts[0] == dts[1]
