@@ -135,9 +135,14 @@ typedef struct grmhd_batch grmhd_batch;
  * dealias on, c2p_maxit = 60, c2p_tol = 1e-15). Any pointer may be NULL. */
 int grmhd_defaults(grmhd_grid* grid, grmhd_physics* phys, grmhd_opts* opts);
 
-/* Create a context: validates the parameters (GRMHD_EINVAL), builds the operator
- * matrices on the host, allocates every device buffer (GRMHD_ENOMEM), and binds the
- * CUDA stream `cuda_stream` (a cudaStream_t, or NULL).  *out receives the handle. */
+/* Create a context for one instance of the paper's problem: a Kerr-Schild black hole of
+ * mass M and spin a (Methods, "Background Geometry: ADM Split in Kerr-Schild Coordinates"),
+ * a Gamma-law gas ("Ideal-gas EOS") and the multi-element Chebyshev x theta x Fourier grid
+ * ("Grid Discretization", "The Spectral Derivative Operators").  Validates the parameters
+ * (GRMHD_EINVAL), builds the operator matrices on the host, allocates every device buffer
+ * (GRMHD_ENOMEM), and binds the CUDA stream `cuda_stream` (a cudaStream_t, or NULL).
+ * *out receives the handle, which the caller releases with grmhd_destroy (NULL is a
+ * no-op there); on an error *out is left NULL and nothing stays allocated. */
 int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, const grmhd_opts* opts,
                  void* cuda_stream, grmhd_ctx** out);
 int grmhd_destroy(grmhd_ctx* ctx);
@@ -165,25 +170,38 @@ int grmhd_coords(const grmhd_ctx* ctx, double* r, double* theta, double* phi);
 int grmhd_init_prims(grmhd_ctx* ctx, const double* rho, const double* p, const double* vr,
                      const double* vth, const double* vph, const double* A_phi);
 
-/* Copy a full canonical state (grmhd_num_vars * num_points doubles) in / out. set_state
- * also resets the primitive guess (the next primitive recovery starts from a bracket). */
+/* Copy a full canonical state (grmhd_num_vars * num_points doubles) in / out: the evolved
+ * BSSN variables ("BSSN Evolution Equations", "Gauge Conditions", "Gamma-driver shift")
+ * and the densitized conserved variables ("Conserved variables U").  set_state also
+ * resets the primitive guess (the next primitive recovery starts from a bracket).  A NULL
+ * pointer gives GRMHD_EINVAL; a device copy that fails gives GRMHD_ECUDA. */
 int grmhd_set_state(grmhd_ctx* ctx, const double* state, int on_device);
 int grmhd_get_state(grmhd_ctx* ctx, double* state, int on_device);
 
-/* L(U) of the current state: one right-hand-side evaluation (one Runge-Kutta stage)
- * without the post-step filter, written to rhs_out (grmhd_num_vars * num_points doubles). */
+/* L(U) of the current state: one right-hand-side evaluation (one Runge-Kutta stage) of
+ * the unsplit coupled system (Methods, "Numerical Algorithm and Mathematical Formulation",
+ * "The Conserved Fluxes and Geometric Source Terms", "BSSN Evolution Equations", "Gauge
+ * Conditions") without the post-step filter, written to rhs_out (grmhd_num_vars *
+ * num_points doubles, caller-owned, canonical layout).  The state is unchanged; the
+ * primitive guess is updated by the recovery inside.  GRMHD_EINVAL for a NULL rhs_out. */
 int grmhd_rhs(grmhd_ctx* ctx, double* rhs_out, int on_device);
 
-/* Primitive recovery of the current state into prim_out (GRMHD_NPRIM * num_points
- * doubles); *n_failed (may be NULL) receives the number of points where the floor
- * eps_atm was applied or the recovery did not converge.  Updates the stored guess. */
+/* Primitive recovery (Methods, "The Primitive Variable Recovery") of the current state
+ * into prim_out (GRMHD_NPRIM * num_points doubles, caller-owned); *n_failed (may be NULL)
+ * receives the number of points where the floor eps_atm was applied or the recovery did
+ * not converge (a count, not an error status).  Updates the stored guess.  With
+ * opts.c2p_lambda > 0 the recovery is the paper's damped fixed-point iteration instead
+ * (see grmhd_opts). */
 int grmhd_con2prim(grmhd_ctx* ctx, double* prim_out, int on_device, long long* n_failed);
 
-/* Advance nsteps time steps of size dt (dt <= 0: dt from the CFL condition of the
- * current state, computed once per call).  Each step: SSP-RK3 (3 stages) or RK4 (4),
- * then the post-step filter.  The nsteps loop is captured in a CUDA graph (rebuilt
- * when nsteps or the dt mode changes).  Returns GRMHD_ENAN if the state is non-finite
- * afterwards.  *dt_used (may be NULL) receives dt. */
+/* Advance nsteps time steps of size dt (Methods, "Time Integration: The Fourth-Order
+ * Runge-Kutta", "The Stability and Complexity", "Dealiasing and Spectral Filtering",
+ * "Coupled Main Loop"; dt <= 0: dt from the CFL condition of the current state, computed
+ * once per call).  Each step: SSP-RK3 (3 stages) or RK4 (4), then the post-step filter.
+ * The nsteps loop is captured in a CUDA graph (rebuilt when nsteps or the dt mode
+ * changes).  Returns GRMHD_EINVAL for nsteps < 1, GRMHD_ENAN if the state is non-finite
+ * afterwards, GRMHD_ETIMEOUT when a bounded device wait gave up.  *dt_used (may be NULL)
+ * receives dt. */
 int grmhd_step(grmhd_ctx* ctx, double dt, int nsteps, double* dt_used);
 
 /* dt of the CFL condition for the current state (Methods, "The Stability and
@@ -221,7 +239,8 @@ int grmhd_kernel_times(grmhd_ctx* ctx, int reps, double* ms_out, double* flops_o
                        double* bytes_out, int n);
 
 /* Independent instances advanced together (the batched workload of many black-hole
- * set-ups).  Instances that share n_r, n_theta, n_phi, the theta range, gamma_eos, the
+ * set-ups; each instance is the problem of grmhd_create, advanced as grmhd_step does,
+ * Methods "Numerical Implementation of Coupled GRMHD-Einstein Evolution").  Instances that share n_r, n_theta, n_phi, the theta range, gamma_eos, the
  * floors and every option field form one group; a group is one grid whose radial
  * elements are the instances' elements in order (the right-hand side does not depend
  * on M and a, which enter only through the initial data), with interface coupling and
@@ -311,7 +330,10 @@ int grmhd_debug_theta(grmhd_ctx* ctx, const double* in, double* out, int nfields
  * device memory, which every GPU that loads the library holds until the process exits.
  * Limits: n_points <= 16,777,216 (larger inputs return GRMHD_EINVAL before any work);
  * hmin > 0, cfl > 0.  The first call on a device looks up that array's device address
- * (with the device current): make that first call before any stream capture.  All
+ * (with the device current): make that first call before any stream capture.  The
+ * address belongs to the device's context; after a cudaDeviceReset the next call finds
+ * a new context and looks the address up again, so the first call after a reset, too,
+ * belongs before any stream capture.  All
  * calls share the array and it keeps the last call's contents (every call overwrites
  * what it reads, so nothing needs clearing); calls that overlap on the GPU (several
  * streams, threads or devices' work in flight on the same device at once) race. */
