@@ -32,19 +32,23 @@ PREC_NAME = {0: "FP64", 1: "mixed: split-BF16x3 tensor-core derivatives, FP32 al
                                                       "algebra, FP64 state/c2p/metric/RK"}
 DTYPE = {0: "f64", 1: "f64 state + bf16x3/f32 derivatives", 2: "f64 state + tf32/f32 derivatives"}
 WORKLOADS = {
-    "c2": ("c2: a=0.9, 8 radial elements r in [1.5,100], N_r=24 N_theta=32 N_phi=64, "
-           "100 SSP-RK3 steps (CFL 0.3) per bench step in one CUDA graph", 100),
-    "c1": ("c1: a=0.5, 2 radial elements r in [1.8,20], N_r=N_theta=12 N_phi=16 (4,608 nodes, "
-           "latency-bound), 100 SSP-RK3 steps (CFL 0.3) per bench step in one CUDA graph", 100),
+    "c2": ("c2: a=0.9, 8 radial elements r in [1.5,100], N_r=24, N_theta=32 Chebyshev-Gauss "
+           "nodes on the polar band theta in [pi/8, 7pi/8], N_phi=64, 100 SSP-RK3 steps "
+           "(CFL 0.3) per bench step in one CUDA graph", 100),
+    "c1": ("c1: a=0.5, 2 radial elements r in [1.8,20], N_r=N_theta=12 (theta band [pi/8, 7pi/8]) "
+           "N_phi=16 (4,608 nodes, latency-bound), 100 SSP-RK3 steps (CFL 0.3) per bench step "
+           "in one CUDA graph", 100),
     "c2f": ("c2f: c2's instance on the paper's Fourier theta basis (N_theta=32 uniform "
             "pole-free nodes over [0, pi], double-Fourier parity extension), a=0.9, 8 radial "
             "elements r in [1.5,100], N_r=24 N_phi=64, 100 SSP-RK3 steps per bench "
             "step in one CUDA graph; dt = 1e-3 of the CFL step", 100),
-    "c5": ("c5: a=0.94, 16 radial elements r in [1.3,500], N_r=32 N_theta=64 N_phi=128, "
-           "200 SSP-RK3 steps (CFL 0.3) per bench step in one CUDA graph", 200),
+    "c5": ("c5: a=0.94, 16 radial elements r in [1.3,500], N_r=32, N_theta=64 (theta band "
+           "[pi/8, 7pi/8]), N_phi=128, 200 SSP-RK3 steps (CFL 0.3) per bench step in one CUDA "
+           "graph", 200),
     "c4": ("c4: 256 independent instances, a ~ U[0,0.99], 2-8 radial elements, "
-           "N_r = N_theta in {8,12,16,24,32}, N_phi in {16,32,64}, Bondi-like profiles; "
-           "10 SSP-RK3 steps per bench step, all instances in one CUDA graph", 10),
+           "N_r = N_theta in {8,12,16,24,32} (theta band [pi/8, 7pi/8]), N_phi in {16,32,64}, "
+           "Bondi-like profiles; 10 SSP-RK3 steps per bench step, all instances in one CUDA "
+           "graph", 10),
 }
 
 # Time step as a fraction of the CFL step.  The Fourier theta workload spans the whole
@@ -84,24 +88,20 @@ def combine(ms_local, units_local, world):
     return ms_max, units, units / (ms_max * 1e-3)
 
 
-def run_batch(args):
-    """Batched workload: instances grouped by shape, each group one element-concatenated
-    grid; value = aggregate point-updates/s, also instance-steps/s.  With N ranks every rank
-    advances its own 256-instance batch (disjoint seeds; no collective on the data path)."""
+def measure_batch(precision, steps, warmup, world, rank, local, dist_on):
+    """The batched workload (256 independent instances per rank, grouped by shape, all
+    groups of a step in one CUDA graph): CUDA-event time of `steps` bench steps of 10
+    SSP-RK3 steps after `warmup` untimed ones.  Returns the figures of one JSON record
+    (aggregate point-updates/s and instance-steps/s over all ranks)."""
     import torch
-
-    world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dist_on = world > 1
-    if dist_on:
-        import torch.distributed as tdist
-        tdist.init_process_group("nccl")
     import paper_2508_18221_gb300 as pkg
     from workloads import primitive_profiles
+    if dist_on:
+        import torch.distributed as tdist
     cfgs = rank_batch(256, rank)
     desc, nsteps = WORKLOADS["c4"]
     stream = torch.cuda.Stream()
-    batch = pkg.Batch([pkg.make_structs(c, precision=args.precision) for c in cfgs], stream.cuda_stream)
+    batch = pkg.Batch([pkg.make_structs(c, precision=precision) for c in cfgs], stream.cuda_stream)
     npts = 0
     states = []
     for i, c in enumerate(cfgs):
@@ -124,41 +124,68 @@ def run_batch(args):
         if ev:
             ev[1].record(stream)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         one()
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+           for _ in range(steps)]
     if dist_on:
         tdist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for k in range(args.steps):
+        for k in range(steps):
             one(evs[k])
         torch.cuda.synchronize()
     if dist_on:
         tdist.barrier()
     ms_local = sum(a.elapsed_time(b) for a, b in evs)
-    ms, units, value = combine(ms_local, npts * RHS_PER_STEP * nsteps * args.steps, world)
+    ms, units, value = combine(ms_local, npts * RHS_PER_STEP * nsteps * steps, world)
     n_inst = len(cfgs) * world
-    line = {"metric": "batched " + metric_name(args.precision), "value": value, "unit": UNIT,
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak",
-            "vs_baseline": None, "dtype": DTYPE[args.precision],
-            "data": "synthetic (seeded Bondi-like profiles, splitmix64 noise)",
-            "config": {"workload": desc, "precision": args.precision, "instances": n_inst,
-                       "nodes": int(round(units / (RHS_PER_STEP * nsteps * args.steps))),
-                       "groups_rank0": batch.num_groups(),
-                       "parallelism": f"{world} rank(s), 256 independent instances each",
-                       "instance_steps_per_s": n_inst * nsteps * args.steps / (ms * 1e-3)},
-            "gpu_launches": batch.launch_count() * nsteps * args.steps,
-            "clocks": clk.summary()}
+    rec = {"metric": "batched " + metric_name(precision), "value": value, "unit": UNIT,
+           "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
+           "instance_steps_per_s": n_inst * nsteps * steps / (ms * 1e-3),
+           "dtype": DTYPE[precision],
+           "config": {"workload": desc, "precision": precision, "instances": n_inst,
+                      "nodes": int(round(units / (RHS_PER_STEP * nsteps * steps))),
+                      "groups_rank0": batch.num_groups(),
+                      "l2": "inputs (5.4 GB state) far larger than L2",
+                      "parallelism": f"{world} rank(s), 256 independent instances each"},
+           "gpu_launches": batch.launch_count() * nsteps * steps,
+           "clocks": clk.summary()}
+    batch.close()
+    return rec
+
+
+def run_batch(args):
+    """Batched workload as the main line: value = aggregate point-updates/s, also
+    instance-steps/s.  With N ranks every rank advances its own 256-instance batch
+    (disjoint seeds; no collective on the data path)."""
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    rec = measure_batch(args.precision, args.steps, args.warmup, world, rank, local, dist_on)
+    line = dict(rec, n_gpus=world, higher_is_better=True, scaling="weak", vs_baseline=None,
+                data="synthetic (seeded Bondi-like profiles, splitmix64 noise)")
+    line["config"]["instance_steps_per_s"] = rec["instance_steps_per_s"]
     if rank == 0:
         print(json.dumps(line), flush=True)
-    batch.close()
     if dist_on:
         tdist.destroy_process_group()
+
+
+def single_config(cfg, desc, nsteps, precision, world):
+    """The `config` record of a single-instance workload, shared by the GPU arm and the
+    reference arm (which times a bounded sample of the same workload, stated outside
+    `config`)."""
+    return {"workload": desc, "precision": precision,
+            "nodes": cfg.n_elem * cfg.n_r * cfg.n_theta * cfg.n_phi,
+            "rk_steps_per_bench_step": nsteps,
+            "l2": "flushed (256 MB write) before every timed step",
+            "parallelism": f"replicas x{world}"}
 
 
 def metric_name(precision):
@@ -229,61 +256,137 @@ class ClockSampler:
                 "sm_max_mhz": smax or None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(seconds_hint=True):
-    """Oracle (numpy FP64) on the host: one RHS evaluation of radial elements 0-2 of the
-    same 8-element grid (same N and element bounds)."""
-    import numpy as np
+# ---- the oracle on the host cores (CPU baseline and the reference arm) ----------------
+#
+# The oracle is numpy FP64 with single-threaded elementwise work.  It runs, as it stands,
+# in one process per host core (spawned, never forked from a process that touched the
+# GPU), each process evaluating the right-hand side of one radial element of the
+# benchmark grid (the element's sub-grid: same N_r, N_theta, N_phi, its own radial range).
+# A step is one such evaluation in every process; the throughput is the nodes of all
+# processes divided by the step's wall time.
+
+_ORACLE_CACHE = {}
+
+
+def _oracle_element(workload, e):
+    """(grid, params, state) of radial element e of the workload as a one-element grid."""
+    key = (workload, e)
+    if key not in _ORACLE_CACHE:
+        from oracle import solver as so
+        from workloads import config
+        cfg = config(workload)
+        ra = cfg.r_min * (cfg.r_max / cfg.r_min) ** (e / cfg.n_elem)
+        rb = cfg.r_min * (cfg.r_max / cfg.r_min) ** ((e + 1) / cfg.n_elem)
+        _ORACLE_CACHE[key] = so.workload_state(config(workload, n_elem=1, r_min=ra, r_max=rb))
+    return _ORACLE_CACHE[key]
+
+
+def _oracle_rhs_task(job):
+    """One oracle right-hand side of one element (runs in a worker); returns its nodes."""
     from oracle import solver as so
-    from workloads import config
-    cfg = config("c2")
-    E = 3
-    rb = cfg.r_min * (cfg.r_max / cfg.r_min) ** (E / cfg.n_elem)
-    sub = config("c2", n_elem=E, r_max=rb)
-    g, p, U = so.workload_state(sub)
-    t0 = time.perf_counter()
+    g, p, U = _oracle_element(*job)
     so.rhs(U, g, p)
-    dt = time.perf_counter() - t0
-    npts = U[0].size
-    threads = os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS")
-    return {"value": npts / dt, "unit": UNIT, "cores": int(threads) if threads else 1,
-            "kind": "oracle",
-            "sample": f"one RHS evaluation of radial elements 0-{E - 1} of the 8-element "
-                      f"grid ({npts} nodes, {dt:.1f} s); numpy, single-threaded elementwise"}
+    return int(U[0].size)
+
+
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
+class OraclePool:
+    """One spawned process per host core, each running the oracle single-threaded."""
+
+    def __init__(self, workload="c2", workers=None):
+        import multiprocessing as mp
+        self.workload = workload
+        self.workers = workers or os.cpu_count() or 1
+        from workloads import config
+        self.n_elem = config(workload).n_elem
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.workers)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def step(self, nproc=None):
+        """One oracle RHS of one element in each of nproc processes; (nodes, seconds)."""
+        n = nproc or self.workers
+        jobs = [(self.workload, w % self.n_elem) for w in range(n)]
+        t0 = time.perf_counter()
+        nodes = sum(self.pool.map(_oracle_rhs_task, jobs, chunksize=1))
+        return nodes, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
+def cpu_baseline(workload="c2"):
+    """The oracle on the host cores: one RHS of one radial element of the benchmark grid
+    in every process (after a warm-up pass that builds the elements' states), plus the
+    same with one process."""
+    pool = OraclePool(workload)
+    try:
+        pool.step()                                  # warm-up: each worker builds its states
+        nodes, sec = pool.step()
+        n1, s1 = pool.step(1)
+    finally:
+        pool.close()
+    return {"value": nodes / sec, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+            "cpu_model": _cpu_model(),
+            "value_1_core": n1 / s1,
+            "sample": f"one RHS evaluation of one radial element of the {pool.n_elem}-element "
+                      f"grid (as a one-element grid) in each of {pool.workers} spawned "
+                      f"processes, {nodes} nodes in {sec:.2f} s; numpy FP64, one thread per "
+                      f"process; value_1_core: one process, {n1} nodes in {s1:.2f} s"}
 
 
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
-    from oracle import solver as so
     from workloads import config
     cfg = config("c2")
-    E = 1
-    rb = cfg.r_min * (cfg.r_max / cfg.r_min) ** (E / cfg.n_elem)
-    sub = config("c2", n_elem=E, r_max=rb)
-    g, p, U = so.workload_state(sub)
-    npts = U[0].size
-    for _ in range(args.warmup):
-        so.rhs(U, g, p)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        so.rhs(U, g, p)
-    el = time.perf_counter() - t0
-    val = npts * args.steps / el
+    desc, nsteps = WORKLOADS["c2"]
+    pool = OraclePool("c2")
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        nodes_total, el = 0, 0.0
+        for _ in range(args.steps):
+            n, sec = pool.step()
+            nodes_total += n
+            el += sec
+    finally:
+        pool.close()
+    val = nodes_total / el
     line = {"impl": "reference", "metric": metric_name(0), "value": val, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Kerr-Schild torus, splitmix64 noise)",
-            "config": {"workload": WORKLOADS["c2"][0], "precision": 0,
-                       "nodes": cfg.n_elem * cfg.n_r * cfg.n_theta * cfg.n_phi,
-                       "rk_steps_per_bench_step": WORKLOADS["c2"][1],
-                       "parallelism": f"replicas x{world}"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step one RHS evaluation of radial element 0 of "
-                                       f"the {cfg.n_elem}-element grid ({npts} nodes); numpy, "
-                                       "single-threaded elementwise"},
+            "config": single_config(cfg, desc, nsteps, 0, world),
+            "sample_per_step": {"nodes": nodes_total // args.steps, "rhs_evaluations_per_node": 1,
+                                "what": f"one RHS of one radial element ({cfg.n_r} x {cfg.n_theta} x "
+                                        f"{cfg.n_phi} nodes) in each of {pool.workers} processes"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+                             "cpu_model": _cpu_model(),
+                             "sample": f"each step one RHS evaluation of one radial element of the "
+                                       f"{cfg.n_elem}-element grid in each of {pool.workers} "
+                                       "spawned processes; numpy FP64, one thread per process"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -313,17 +416,17 @@ def _kernel_names(cfg, precision):
     for d, dn in enumerate(("r", "theta", "phi")):
         fx = 2 <= ns[d] <= 128 and (d != 2 or ns[d] % 2 == 0)
         fourier = d == 2 or (d == 1 and getattr(cfg, "theta_basis", 0) == 1)
-        # Chebyshev derivatives: six accumulators above 32 nodes, the FP64 units above 64
-        fp64_f = f"k_contract_fx<{d}>" if fx else f"k_deriv_eo<{d}>"
-        fp64_d = fp64_f
+        # derivatives: six accumulators (Chebyshev above 64 nodes: the FP64 units); the
+        # filter: five
+        fp64_f = f"k_contract_fx<{d}, 5>" if fx else f"k_deriv_eo<{d}>"
+        fp64_d = f"k_contract_fx<{d}, 6>" if fx else f"k_deriv_eo<{d}>"
         if fx and not fourier and ns[d] > 64:
             fp64_d = f"k_deriv<{d}>"
-        elif fx and not fourier and ns[d] > 32:
-            fp64_d = f"k_contract_fx<{d}, 6>"
         if d == 1 and getattr(cfg, "theta_basis", 0) == 1:
             # Fourier theta: fold, two half-width contractions, unfold (timed together)
-            fp64_f = fp64_d = "theta fold + k_contract_fx<1> x2 + unfold" if fx and cfg.n_phi % 4 == 0 else \
-                "theta fold + k_deriv_eo<1> x2 + unfold"
+            fx_t = fx and cfg.n_phi % 4 == 0
+            fp64_f = "theta fold + k_contract_fx<1, 5> x2 + unfold" if fx_t else "theta fold + k_deriv_eo<1> x2 + unfold"
+            fp64_d = "theta fold + k_contract_fx<1, 6> x2 + unfold" if fx_t else fp64_f
             tc = "theta fold + k_contract_tc<1> x2 + unfold"
         else:
             tc = f"k_contract_tc<{d}>"
@@ -400,22 +503,21 @@ def _traffic(kernel, P):
     return None if t is None else t * P / TRAFFIC_NODES
 
 
-def run_gpu(args):
-    import numpy as np
+def measure_single(workload, precision, steps, warmup, world, rank, local, dist_on, extras=True):
+    """One single-instance workload: `steps` timed bench steps (each `nsteps` SSP-RK3 steps
+    recorded in one CUDA graph, from the same initial state, L2 flushed before each) after
+    `warmup` untimed ones; then the end-to-end figure through the C ABI with host buffers,
+    the bare right-hand side and the per-kernel times behind the roofline.  Returns the
+    record and the state after one bench step (a device tensor)."""
     import torch
-
-    world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dist_on = world > 1
-    if dist_on:
-        import torch.distributed as tdist
-        tdist.init_process_group("nccl")
     import paper_2508_18221_gb300 as pkg
     from workloads import config, primitive_profiles
+    if dist_on:
+        import torch.distributed as tdist
 
-    cfg = config(args.workload)
-    desc, nsteps = WORKLOADS[args.workload]
-    grid, phys, opts = pkg.make_structs(cfg, precision=args.precision)
+    cfg = config(workload)
+    desc, nsteps = WORKLOADS[workload]
+    grid, phys, opts = pkg.make_structs(cfg, precision=precision)
     stream = torch.cuda.Stream()
     ctx = pkg.Context(grid, phys, opts, stream.cuda_stream)
     P = ctx.n_points
@@ -425,7 +527,7 @@ def run_gpu(args):
     ctx.init_prims(pr["rho"], pr["p"], pr["vr"], pr["vth"], pr["vph"], pr["A_phi"])
     U0 = torch.empty(pkg.NV * P, dtype=torch.float64, device="cuda")
     ctx.get_state(U0, True)
-    dt = ctx.cfl_dt() * DT_SCALE.get(args.workload, 1.0)
+    dt = ctx.cfl_dt() * DT_SCALE.get(workload, 1.0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def one(timed_events=None):
@@ -438,29 +540,31 @@ def run_gpu(args):
             if timed_events:
                 timed_events[1].record(stream)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         one()
     torch.cuda.synchronize()
     launches_per_step = ctx.launch_count()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+           for _ in range(steps)]
     if dist_on:
         tdist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for k in range(args.steps):
+        for k in range(steps):
             one(evs[k])
         torch.cuda.synchronize()
     if dist_on:
         tdist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    ms_max, units, value = combine(ms, P * RHS_PER_STEP * nsteps * args.steps, world)
+    ms_max, units, value = combine(ms, P * RHS_PER_STEP * nsteps * steps, world)
+    final = torch.empty_like(U0)
+    ctx.get_state(final, True)
 
     # end to end through the C ABI with host buffers (pinned)
     host_in = torch.empty(pkg.NV * P, dtype=torch.float64).pin_memory()
     host_out = torch.empty_like(host_in)
     host_in.copy_(U0.cpu())
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -471,28 +575,110 @@ def run_gpu(args):
     e2e_s = time.perf_counter() - t0
     e2e_val = P * RHS_PER_STEP * nsteps * e2e_steps * world / e2e_s
 
+    rec = {"metric": metric_name(precision), "value": value, "unit": UNIT,
+           "steps": steps, "warmup": warmup, "ms_per_step": ms_max / steps,
+           "dtype": DTYPE[precision], "config": single_config(cfg, desc, nsteps, precision, world),
+           "dt": dt,
+           "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": pkg.NV * P * 8,
+                   "d2h_bytes_per_step": pkg.NV * P * 8},
+           "gpu_launches": launches_per_step * steps, "clocks": clk.summary(),
+           "us_per_rk_step": ms_max / steps / nsteps * 1e3}
+    if extras:
+        # bare right-hand side through the C ABI (no graph, device buffers)
+        rhs_out = torch.empty_like(U0)
+        ctx.set_state(U0, True)
+        for _ in range(3):
+            ctx.rhs(rhs_out, True)
+        torch.cuda.synchronize()
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_rhs = 20
+        e_a.record(stream)
+        for _ in range(n_rhs):
+            ctx.rhs(rhs_out, True)
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        rec["rhs_call"] = {"value": P * n_rhs * world / (e_a.elapsed_time(e_b) * 1e-3), "unit": UNIT,
+                           "what": "grmhd_rhs on device buffers, no graph, 20 calls"}
     # live per-kernel timing (CUDA events on the library's stream): every RHS class runs
     # RHS_PER_STEP times per step, every filter class once.  The roofline is reported for
     # the kernel with the largest time per step.
-    # bare right-hand side through the C ABI (no graph, device buffers): one stage's launches
-    rhs_out = torch.empty_like(U0)
-    ctx.set_state(U0, True)
-    for _ in range(3):
-        ctx.rhs(rhs_out, True)
-    torch.cuda.synchronize()
-    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n_rhs = 20
-    e_a.record(stream)
-    for _ in range(n_rhs):
-        ctx.rhs(rhs_out, True)
-    e_b.record(stream)
-    torch.cuda.synchronize()
-    rhs_call = P * n_rhs * world / (e_a.elapsed_time(e_b) * 1e-3)
-
     ctx.set_state(U0, True)
     kt_full = ctx.kernel_times(reps=5)
-    roof = roofline(kt_full, P, args.precision, _kernel_names(cfg, args.precision))
+    rec["roofline"] = roofline(kt_full, P, precision, _kernel_names(cfg, precision))
     stats = ctx.diag()
+    rec["final_diag"] = {"mass": stats[0], "c2p_floor_points": stats[3]}
+    ctx.close()
+    return rec, final
+
+
+# evolved variables grouped by tensor (for the error of the mixed path against FP64)
+TENSOR_GROUPS = {"gammatilde": range(0, 6), "phi": [6], "Atilde": range(7, 13), "K": [13],
+                 "Gammatilde": range(14, 17), "alpha": [17], "beta": range(18, 21),
+                 "B_driver": range(21, 24), "D": [24], "S": range(25, 28), "tau": [28],
+                 "B_field": range(29, 32)}
+
+
+def tensor_rel_l2(a, b, nv):
+    """Relative L2 difference of each tensor of two canonical states (device tensors)."""
+    A = a.view(nv, -1)
+    Bm = b.view(nv, -1)
+    out = {}
+    for name, idx in TENSOR_GROUPS.items():
+        idx = list(idx)
+        den = float(Bm[idx].norm())
+        out[name] = float((A[idx] - Bm[idx]).norm()) / den if den > 0 else 0.0
+    return out
+
+
+# Relative L2 errors of the split-BF16 x3 mode against the FP64 oracle after 100 SSP-RK3
+# steps of the 2-element 12 x 12 x 16 instance, per tensor, from the GPU test
+# test_precision_variant_report (asserted there to stay below the spectral truncation
+# level of every tensor); the largest and the tightest tensor.
+MIXED_STATED_ERROR = {"instance": "2 elements 12 x 12 x 16 (4,608 nodes), 100 SSP-RK3 steps",
+                      "max_rel_l2_vs_fp64_oracle": 7.6e-05, "tensor": "B_driver (starts at zero)",
+                      "tightest": "K: 2.8e-05 against a truncation level of 2.9e-05",
+                      "source": "tests/test_gpu_mixed.py::test_precision_variant_report"}
+
+
+def run_gpu(args):
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    rec, final = measure_single(args.workload, args.precision, args.steps, args.warmup, world, rank,
+                                local, dist_on)
+    line = dict(rec, n_gpus=world, higher_is_better=True, scaling="weak", vs_baseline=None,
+                data="synthetic (seeded Kerr-Schild torus, splitmix64 noise)")
+    extras = not args.no_extras and args.workload == "c2" and args.precision == 0
+    if extras:
+        # the rest of the headline metric in the same line: the mixed form on the same
+        # workload (with its error against the FP64 path after one bench step) and the
+        # batched workload in both forms
+        mrec, mfinal = measure_single("c2", 1, args.steps, args.warmup, world, rank, local, dist_on,
+                                      extras=False)
+        nv = final.numel() // (mrec["config"]["nodes"])
+        err = tensor_rel_l2(mfinal, final, nv)
+        mrec["error_vs_fp64_path"] = {
+            "what": "relative L2 per tensor of the state after one bench step (100 SSP-RK3 steps) "
+                    "against the FP64 path's state from the same initial data",
+            "max": max(err.values()), "per_tensor": err}
+        mrec["stated_error"] = MIXED_STATED_ERROR
+        mrec["vs_fp64_path"] = mrec["value"] / rec["value"]
+        del final, mfinal
+        torch.cuda.empty_cache()
+        bsteps, bwarm = min(args.steps, 3), max(3, min(args.warmup, 3))
+        b64 = measure_batch(0, bsteps, bwarm, world, rank, local, dist_on)
+        torch.cuda.empty_cache()
+        b32 = measure_batch(1, bsteps, bwarm, world, rank, local, dist_on)
+        torch.cuda.empty_cache()
+        b64["vs_single_instance_fp64"] = b64["value"] / rec["value"]
+        b32["vs_batch_fp64"] = b32["value"] / b64["value"]
+        line["mixed"] = mrec
+        line["batch"] = {"fp64": b64, "mixed": b32}
     if rank == 0:
         cb = None
         if not args.no_cpu_baseline:
@@ -500,28 +686,8 @@ def run_gpu(args):
                 cb = cpu_baseline()
             except Exception as exc:  # noqa: BLE001
                 cb = {"error": str(exc)}
-        line = {"metric": metric_name(args.precision), "value": value, "unit": UNIT,
-                "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
-                "data": "synthetic (seeded Kerr-Schild torus, splitmix64 noise)",
-                "config": {"workload": desc, "precision": args.precision,
-                           "nodes": P, "rk_steps_per_bench_step": nsteps,
-                           "l2": "flushed (256 MB write) before every timed step",
-                           "dt": dt, "parallelism": f"replicas x{world}"},
-                "roofline": roof, "cpu_baseline": cb,
-                "e2e": {"value": e2e_val, "unit": UNIT,
-                        "h2d_bytes_per_step": pkg.NV * P * 8,
-                        "d2h_bytes_per_step": pkg.NV * P * 8},
-                "gpu_launches": launches_per_step * args.steps,
-                "clocks": clk.summary(),
-                "rhs_call": {"value": rhs_call, "unit": UNIT,
-                             "what": "grmhd_rhs on device buffers, no graph, 20 calls"},
-                "us_per_rk_step": ms_max / args.steps / nsteps * 1e3,
-                "final_diag": {"mass": stats[0], "c2p_floor_points": stats[3]}}
+        line["cpu_baseline"] = cb
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist_on:
         tdist.destroy_process_group()
 
@@ -533,6 +699,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the mixed-precision and batched records of the default line")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     args = ap.parse_args()
