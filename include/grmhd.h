@@ -12,7 +12,8 @@
  * integration ("Time Integration", SSP-RK3 by default, the printed RK4 as option).
  *
  * Conventions shared by every call
- *   - Every function returns an int status: GRMHD_OK (0) or a negative error code.
+ *   - Every function returns an int status: GRMHD_OK (0), a negative error code, or a
+ *     positive warning (the call did its work; see GRMHD_WPRECISION).
  *     No call aborts, traps or exits the process; after an error the context stays
  *     usable and grmhd_last_error() describes the cause.
  *   - Field arrays use the canonical layout double[nv][E][N_r][N_theta][N_phi] with phi
@@ -44,7 +45,13 @@ enum {
     GRMHD_ECUDA = -3,         /* a CUDA runtime call failed (message in last_error)    */
     GRMHD_ENAN = -4,          /* a non-finite value appeared in the evolved state      */
     GRMHD_ETIMEOUT = -5,      /* a bounded device-side wait gave up                    */
-    GRMHD_EUNSUPPORTED = -6   /* option value not built into this library              */
+    GRMHD_EUNSUPPORTED = -6,  /* option value not built into this library              */
+    /* positive statuses are warnings: the call did its work and its outputs are valid */
+    GRMHD_WPRECISION = 1      /* created with precision 2 (TF32 contractions), a mode
+                                 whose error exceeds the mixed-precision bar: its state's
+                                 relative L2 error reaches O(1) within 100 steps on the
+                                 2-element 12 x 12 x 16 workload; precision 1 stays below
+                                 the spectral truncation level there                   */
 };
 
 enum { GRMHD_NV = 32, GRMHD_NPRIM = 7, GRMHD_NDIAG = 8 };
@@ -90,8 +97,18 @@ typedef struct {
  * variables in r/theta/phi (default 47: all but theta for BSSN); filt_alpha, filt_p are
  * the exponential-filter constants (paper: 36, 8); dealias23_phi applies the 2/3 rule
  * in phi, dealias23_theta in theta under theta_basis 1 (|k| > 2 n_theta / 3 of the
- * extended line zeroed; default 1; the Chebyshev theta filter has no 2/3 rule).  cfl: Courant factor for dt <= 0.  c2p_maxit, c2p_tol: Newton iteration
- * limit and relative tolerance of the primitive recovery.  contraction: how the FP64
+ * extended line zeroed; default 1; the Chebyshev theta filter has no 2/3 rule).  cfl: Courant factor for dt <= 0.  c2p_maxit, c2p_tol: iteration limit
+ * and relative tolerance of the primitive recovery.  c2p_lambda: 0 (default) solves the
+ * one-variable master function in mu = 1/(h W) by safeguarded Newton (tolerance: of the
+ * step in mu); in (0, 1] it runs the paper's damped iteration instead ("The Primitive
+ * Variable Recovery"): from the stored primitives (or, after grmhd_set_state, the dust
+ * estimates v^i = gamma^ij S_j / (tau + D), eps = (tau + D)/(D W) - 1), the update
+ * v^i += lam gamma^ij dS_j / (rho h W^2), eps += lam dtau / (rho W^2), rho = D / W with
+ * lam = c2p_lambda at first and halved while the residual grows, until ||dS|| + |dtau| <
+ * c2p_tol D or c2p_maxit updates (the paper: 30-40), then one Newton update of eps.  It
+ * converges linearly: after 40 iterations from a cold start eps is within about 1e-9 of
+ * the exact root on the 2-element workload (2e-11 in the torus), so the default stays
+ * the Newton solve.  contraction: how the FP64
  * spectral contractions (all derivatives at precision 0, the filter at every precision)
  * run: 0 (default) on the BF16 tensor cores with exact base-256 digit slices of the
  * FP64 values (Ozaki splitting; up to 128 nodes per direction; error about K 2^-53 of
@@ -125,6 +142,7 @@ typedef struct {
     int glm;
     double glm_ch, glm_tau;
     int dealias23_theta;
+    double c2p_lambda;
 } grmhd_opts;
 
 typedef struct grmhd_ctx grmhd_ctx;
@@ -132,7 +150,7 @@ typedef struct grmhd_batch grmhd_batch;
 
 /* Fill the structs with the defaults listed above (M = 1, a = 0.5, Gamma = 4/3,
  * rho_atm = 1e-12, eps_atm = 1e-10, eta = 2, cfl = 0.3, filter = 47, 36, 8,
- * dealias on, c2p_maxit = 60, c2p_tol = 1e-15). Any pointer may be NULL. */
+ * dealias on, c2p_maxit = 60, c2p_tol = 1e-15, c2p_lambda = 0). Any pointer may be NULL. */
 int grmhd_defaults(grmhd_grid* grid, grmhd_physics* phys, grmhd_opts* opts);
 
 /* Create a context for one instance of the paper's problem: a Kerr-Schild black hole of
@@ -142,7 +160,8 @@ int grmhd_defaults(grmhd_grid* grid, grmhd_physics* phys, grmhd_opts* opts);
  * (GRMHD_EINVAL), builds the operator matrices on the host, allocates every device buffer
  * (GRMHD_ENOMEM), and binds the CUDA stream `cuda_stream` (a cudaStream_t, or NULL).
  * *out receives the handle, which the caller releases with grmhd_destroy (NULL is a
- * no-op there); on an error *out is left NULL and nothing stays allocated. */
+ * no-op there); on an error *out is left NULL and nothing stays allocated.  With
+ * opts.precision = 2 the context is created and the status is GRMHD_WPRECISION. */
 int grmhd_create(const grmhd_grid* grid, const grmhd_physics* phys, const grmhd_opts* opts,
                  void* cuda_stream, grmhd_ctx** out);
 int grmhd_destroy(grmhd_ctx* ctx);

@@ -178,6 +178,106 @@ def con2prim(D, S_d, tau, B_u, gam, gamma_eos, eps_min=0.0, n_scan=256, n_bisect
     return rho, v_u, eps, p, W, ok
 
 
+def con2prim_damped_guess(D, S_d, tau, gam, w_max=10.0, eps_min=0.0):
+    """Cold start of the damped iteration when no previous primitives exist: the dust
+    estimates v^i = gamma^ij S_j / (tau + D) (momentum over energy density, |v| capped at
+    the W <= w_max limit), W from v, eps = (tau + D)/(D W) - 1 (floored), rho = D / W.
+    (A reading: the paper starts the iteration from given primitives.)"""
+    ginv = inv3(gam)
+    v_u = np.einsum("...ij,...j->...i", ginv, S_d) / (tau + D)[..., None]
+    v2max = 1.0 - 1.0 / w_max ** 2
+    v2 = np.einsum("...i,...i->...", lower(gam, v_u), v_u)
+    v_u = v_u * np.sqrt(np.minimum(1.0, v2max / np.maximum(v2, 1e-300)))[..., None]
+    W = lorentz_factor(v_u, gam)
+    eps = np.maximum((tau + D) / (D * W) - 1.0, eps_min)
+    return D / W, v_u, eps
+
+
+def con2prim_damped(D, S_d, tau, B_u, gam, gamma_eos, rho, v_u, eps, lam0=0.5, maxit=40,
+                    tol=1e-13, eps_min=0.0, w_max=10.0, max_halvings=30):
+    """The paper's primitive recovery ("The Primitive Variable Recovery"), step by step,
+    from the primitives (rho, v^i, eps) given as the starting point:
+
+      1. W = (1 - v^2)^(-1/2), p = (Gamma - 1) rho eps, h = 1 + eps + p / rho, and the
+         conserved variables these primitives predict (S_i, tau; the map of
+         prim_to_cons_eulerian, which carries the metric and the field);
+      2. residuals dS_i = S_i - S_i^pred, dtau = tau - tau^pred;
+      3. damped update v^i += lam gamma^ij dS_j / (rho h W^2), eps += lam dtau / (rho W^2),
+         with lam = 0.5 at first; when the residual of the updated primitives exceeds
+         the current one, lam is halved and the update retried (lam stays halved);
+      4. rho = D / W of the updated velocity;
+      5. stop when ||dS|| + |dtau| < tol D (||dS||^2 = gamma^ij dS_i dS_j);
+    at most maxit iterations; a point still above tol then takes one Newton-Raphson update
+    of eps on the tau residual at fixed v and rho (d tau^pred / d eps = rho (Gamma W^2 -
+    Gamma + 1)).  Readings: the residual is measured relative to D (the paper's tol is
+    absolute, for states of density ~1); the indices are raised with the spatial metric
+    (the printed update is flat-space); v^2 is capped at W <= w_max and eps floored at
+    eps_min after every update.  Inputs undensitized; returns rho, v^i, eps, p, W, ok
+    (converged without the final Newton update and without a floor) and the iterations
+    taken."""
+    ginv = inv3(gam)
+    v2max = 1.0 - 1.0 / w_max ** 2
+
+    def clamp(v_u, eps):
+        v2 = np.einsum("...i,...i->...", lower(gam, v_u), v_u)
+        v_u = v_u * np.sqrt(np.minimum(1.0, v2max / np.maximum(v2, 1e-300)))[..., None]
+        return v_u, np.maximum(eps, eps_min)
+
+    def residual(rho, v_u, eps):
+        _, Sp, tp = prim_to_cons_eulerian(rho, v_u, eps, B_u, gam, gamma_eos)
+        dS = S_d - Sp
+        dt = tau - tp
+        nrm = np.sqrt(np.maximum(np.einsum("...i,...ij,...j->...", dS, ginv, dS), 0.0)) + np.abs(dt)
+        return dS, dt, nrm
+
+    rho = np.array(rho, dtype=np.float64)
+    v_u = np.array(v_u, dtype=np.float64)
+    eps = np.array(eps, dtype=np.float64)
+    v_u, eps = clamp(v_u, eps)
+    rho = D / lorentz_factor(v_u, gam)
+    lam = np.full(D.shape, float(lam0))
+    done = np.zeros(D.shape, dtype=bool)
+    iters = np.zeros(D.shape, dtype=np.int64)
+    for _ in range(maxit):
+        dS, dt, r0 = residual(rho, v_u, eps)
+        done |= r0 < tol * D
+        if done.all():
+            break
+        W = lorentz_factor(v_u, gam)
+        p = (gamma_eos - 1.0) * rho * eps
+        h = 1.0 + eps + p / rho
+        dv = np.einsum("...ij,...j->...i", ginv, dS) / (rho * h * W * W)[..., None]
+        de = dt / (rho * W * W)
+        trial_lam = lam.copy()
+        new_v, new_e, new_r = v_u.copy(), eps.copy(), rho.copy()
+        pending = ~done
+        for _h in range(max_halvings + 1):
+            tv, te = clamp(v_u + trial_lam[..., None] * dv, eps + trial_lam * de)
+            tr = D / lorentz_factor(tv, gam)
+            _, _, r1 = residual(tr, tv, te)
+            accept = pending & ((r1 <= r0) | (_h == max_halvings))
+            new_v = np.where(accept[..., None], tv, new_v)
+            new_e = np.where(accept, te, new_e)
+            new_r = np.where(accept, tr, new_r)
+            lam = np.where(accept, trial_lam, lam)
+            pending &= ~accept
+            if not pending.any():
+                break
+            trial_lam = np.where(pending, 0.5 * trial_lam, trial_lam)
+        v_u, eps, rho = new_v, new_e, new_r
+        iters += ~done
+    dS, dt, r0 = residual(rho, v_u, eps)
+    done |= r0 < tol * D
+    # the final Newton-Raphson update of eps for the points still above tol
+    W = lorentz_factor(v_u, gam)
+    dtde = rho * (gamma_eos * W * W - gamma_eos + 1.0)
+    eps = np.where(done, eps, eps + dt / dtde)
+    ok = done & (eps >= eps_min)
+    eps = np.maximum(eps, eps_min)
+    p = (gamma_eos - 1.0) * rho * eps
+    return rho, v_u, eps, p, W, ok, iters
+
+
 # ------------------------------------------------------------------ fluxes and T^{mu nu}
 def fluxes(rho, v_u, eps, B_u, alpha, beta_u, gam, gamma_eos):
     """script-F^i for the 8 undensitized conserved variables, shape [..., 3(i), 8].

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libgrmhd.so")
 
 GRMHD_OK, GRMHD_EINVAL, GRMHD_ENOMEM, GRMHD_ECUDA = 0, -1, -2, -3
 GRMHD_ENAN, GRMHD_ETIMEOUT, GRMHD_EUNSUPPORTED = -4, -5, -6
+GRMHD_WPRECISION = 1          # warning: created, but the TF32 mode misses the mixed bar
 NV, NPRIM, NDIAG = 32, 7, 8
 
 
@@ -36,7 +37,8 @@ class Opts(C.Structure):
                 ("filter", C.c_int), ("filt_alpha", C.c_double), ("filt_p", C.c_double),
                 ("dealias23_phi", C.c_int), ("c2p_maxit", C.c_int), ("c2p_tol", C.c_double),
                 ("contraction", C.c_int), ("coupling", C.c_int), ("glm", C.c_int),
-                ("glm_ch", C.c_double), ("glm_tau", C.c_double), ("dealias23_theta", C.c_int)]
+                ("glm_ch", C.c_double), ("glm_tau", C.c_double), ("dealias23_theta", C.c_int),
+                ("c2p_lambda", C.c_double)]
 
 
 _P = C.c_void_p
@@ -108,6 +110,10 @@ class GrmhdError(RuntimeError):
 
 
 def check(status, ctx=None):
+    if status > 0:            # a warning: the call did its work
+        import warnings
+        warnings.warn(load().grmhd_strerror(status).decode(), RuntimeWarning, stacklevel=3)
+        return
     if status != GRMHD_OK:
         lib = load()
         msg = lib.grmhd_strerror(status).decode()

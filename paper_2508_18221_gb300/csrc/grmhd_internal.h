@@ -50,6 +50,7 @@ struct PhysParams {
     double glm_ch2, glm_itau;
     int c2p_maxit;
     double c2p_tol;
+    double c2p_lambda;    // > 0: the paper's damped iteration with this initial damping
     double w_end;         // Clenshaw-Curtis end weight on [-1, 1] for n_r CGL nodes
 };
 

@@ -186,6 +186,109 @@ __device__ int con2prim_point(double D, const double S_d[3], double tau, const d
     return ok;
 }
 
+// The paper's primitive recovery (Methods, "The Primitive Variable Recovery") as an option
+// (opts.c2p_lambda > 0): predicted conserved variables from the current primitives,
+// residuals dS_i, dtau, the damped update v^i += lam gamma^ij dS_j / (rho h W^2),
+// eps += lam dtau / (rho W^2), rho = D / W, lam halved (and the update retried) while the
+// residual grows, stop at ||dS|| + |dtau| < tol D; after maxit updates one Newton-Raphson
+// update of eps on the tau residual.  The same sequence of steps and tests as the oracle's
+// con2prim_damped (W <= 10, eps >= eps_min after every update), in FP64.
+struct DampedResid {
+    double dS[3], dtau, nrm;
+};
+
+__device__ __forceinline__ double lorentz_w(const double v[3], const double g[3][3]) {
+    double v2 = 0.0;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) v2 += g[i][j] * v[i] * v[j];
+    return 1.0 / sqrt(1.0 - v2);
+}
+
+__device__ void damped_resid(double rho, const double v[3], double eps, const double B[3], const double g[3][3],
+                             const double gi[3][3], double gam, const double S_d[3], double tau, DampedResid* r) {
+    const double W = lorentz_w(v, g);
+    const double pr = (gam - 1.0) * rho * eps;
+    const double h = 1.0 + eps + pr / rho;
+    const double Z = rho * h * W * W;
+    double v_d[3], B_d[3];
+    for (int i = 0; i < 3; i++) {
+        v_d[i] = g[i][0] * v[0] + g[i][1] * v[1] + g[i][2] * v[2];
+        B_d[i] = g[i][0] * B[0] + g[i][1] * B[1] + g[i][2] * B[2];
+    }
+    const double B2 = B_d[0] * B[0] + B_d[1] * B[1] + B_d[2] * B[2];
+    const double vB = v_d[0] * B[0] + v_d[1] * B[1] + v_d[2] * B[2];
+    for (int i = 0; i < 3; i++) r->dS[i] = S_d[i] - ((Z + B2) * v_d[i] - vB * B_d[i]);
+    r->dtau = tau - (Z + B2 - pr - 0.5 * (B2 / (W * W) + vB * vB) - rho * W);
+    double q = 0.0;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) q += r->dS[i] * gi[i][j] * r->dS[j];
+    r->nrm = sqrt(fmax(q, 0.0)) + fabs(r->dtau);
+}
+
+__device__ __forceinline__ void damped_clamp(double v[3], double* eps, const double g[3][3], double v2max,
+                                             double eps_min) {
+    double v2 = 0.0;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) v2 += g[i][j] * v[i] * v[j];
+    const double f = sqrt(fmin(1.0, v2max / fmax(v2, 1e-300)));
+    for (int i = 0; i < 3; i++) v[i] *= f;
+    *eps = fmax(*eps, eps_min);
+}
+
+// Returns 1 if the residual fell below tol D without the final Newton update and without a
+// floor; rho, v, eps hold the starting point on entry.
+__device__ int con2prim_damped_point(double D, const double S_d[3], double tau, const double B_u[3],
+                                     const double g[3][3], const double gi[3][3], double gam, double eps_min,
+                                     int maxit, double tol, double lam0, double* rho, double v[3], double* eps,
+                                     double* pr, double* Wout) {
+    const double v2max = 1.0 - 1.0 / (10.0 * 10.0);
+    damped_clamp(v, eps, g, v2max, eps_min);
+    *rho = D / lorentz_w(v, g);
+    double lam = lam0;
+    bool done = false;
+    DampedResid r0;
+    for (int it = 0; it < maxit; it++) {
+        damped_resid(*rho, v, *eps, B_u, g, gi, gam, S_d, tau, &r0);
+        if (r0.nrm < tol * D) { done = true; break; }
+        const double W = lorentz_w(v, g);
+        const double pr0 = (gam - 1.0) * (*rho) * (*eps);
+        const double h = 1.0 + *eps + pr0 / (*rho);
+        const double iZ = 1.0 / (*rho * h * W * W);
+        double dv[3];
+        for (int i = 0; i < 3; i++)
+            dv[i] = (gi[i][0] * r0.dS[0] + gi[i][1] * r0.dS[1] + gi[i][2] * r0.dS[2]) * iZ;
+        const double de = r0.dtau / (*rho * W * W);
+        double tl = lam;
+        for (int hv = 0; hv <= 30; hv++) {
+            double tv[3] = {v[0] + tl * dv[0], v[1] + tl * dv[1], v[2] + tl * dv[2]};
+            double te = *eps + tl * de;
+            damped_clamp(tv, &te, g, v2max, eps_min);
+            const double tr = D / lorentz_w(tv, g);
+            DampedResid r1;
+            damped_resid(tr, tv, te, B_u, g, gi, gam, S_d, tau, &r1);
+            if (r1.nrm <= r0.nrm || hv == 30) {
+                for (int i = 0; i < 3; i++) v[i] = tv[i];
+                *eps = te;
+                *rho = tr;
+                lam = tl;
+                break;
+            }
+            tl *= 0.5;
+        }
+    }
+    if (!done) {
+        damped_resid(*rho, v, *eps, B_u, g, gi, gam, S_d, tau, &r0);
+        done = r0.nrm < tol * D;
+    }
+    const double W = lorentz_w(v, g);
+    if (!done) *eps += r0.dtau / (*rho * (gam * W * W - gam + 1.0));
+    const int ok = done && (*eps >= eps_min);
+    *eps = fmax(*eps, eps_min);
+    *pr = (gam - 1.0) * (*rho) * (*eps);
+    *Wout = W;
+    return ok;
+}
+
 // --------------------------------------------------------------------------- k_prep
 template <typename R>
 __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const double* __restrict__ U,
@@ -234,7 +337,26 @@ __global__ void __launch_bounds__(128) k_prep(Dims d, PhysParams pp, const doubl
         double mu0 = 1.0 / ((1.0 + pp.gam * eg) * Wg);
         double rho, v[3], eps, pr, W;
         int ok;
-        if (Dc > pp.rho_atm && isfinite(Dc) && isfinite(tau)) {
+        if (Dc > pp.rho_atm && isfinite(Dc) && isfinite(tau) && pp.c2p_lambda > 0.0) {
+            // the paper's damped iteration from the stored primitives, or (after a reset)
+            // from the dust estimates v^i = gamma^ij S_j / (tau + D), eps = (tau + D)/(D W) - 1
+            if (Wg >= 1.0 && prim[0 * P + p] > 0.0) {
+                rho = prim[0 * P + p];
+                for (int i = 0; i < 3; i++) v[i] = prim[(1 + i) * P + p];
+                eps = eg;
+            } else {
+                const double ie = 1.0 / (tau + Dc);
+                for (int i = 0; i < 3; i++)
+                    v[i] = (gi[i][0] * S_d[0] + gi[i][1] * S_d[1] + gi[i][2] * S_d[2]) * ie;
+                eps = 0.0;
+                damped_clamp(v, &eps, g, 1.0 - 1.0 / (10.0 * 10.0), 0.0);
+                const double W0 = lorentz_w(v, g);
+                eps = fmax((tau + Dc) / (Dc * W0) - 1.0, pp.eps_atm);
+                rho = Dc / W0;
+            }
+            ok = con2prim_damped_point(Dc, S_d, tau, B_u, g, gi, pp.gam, pp.eps_atm, pp.c2p_maxit, pp.c2p_tol,
+                                       pp.c2p_lambda, &rho, v, &eps, &pr, &W);
+        } else if (Dc > pp.rho_atm && isfinite(Dc) && isfinite(tau)) {
             ok = con2prim_point(Dc, S_d, tau, B_u, g, gi, pp.gam, pp.eps_atm, pp.c2p_maxit,
                                 pp.c2p_tol, mu0, &rho, v, &eps, &pr, &W);
         } else {

@@ -63,7 +63,8 @@ def test_host_only_calls(lib):
     ("p", "rho_atm", 0.0), ("p", "eps_atm", -1.0),
     ("o", "integrator", 2), ("o", "gauge", 2), ("o", "cfl", 0.0), ("o", "c2p_maxit", 0),
     ("o", "c2p_tol", 0.0), ("o", "filter", 64), ("o", "filter", -1), ("o", "contraction", 2),
-    ("o", "coupling", 2), ("o", "glm", 2), ("o", "dealias23_theta", 2),
+    ("o", "coupling", 2), ("o", "glm", 2), ("o", "dealias23_theta", 2), ("o", "c2p_lambda", -0.1),
+    ("o", "c2p_lambda", 1.5), ("o", "c2p_lambda", float("nan")),
 ])
 def test_invalid_parameters_rejected_before_device_work(lib, which, field, value):
     """Each parameter outside its documented range gives GRMHD_EINVAL from grmhd_create and
@@ -105,3 +106,19 @@ def test_empty_and_oversized_inputs_rejected(lib):
         assert lib.grmhd_cfl_dt_noalloc(buf, n, 0.1, 0.3, ctypes.byref(dt), None) == pkg.GRMHD_EINVAL
     assert lib.grmhd_cfl_dt_noalloc(buf, 10, 0.0, 0.3, ctypes.byref(dt), None) == pkg.GRMHD_EINVAL
     assert lib.grmhd_cfl_dt_noalloc(buf, 10, 0.1, -0.3, ctypes.byref(dt), None) == pkg.GRMHD_EINVAL
+
+
+def test_warning_status_of_the_tf32_mode(lib):
+    """Positive statuses are warnings (the call did its work); the TF32 mode's warning
+    names the mode and the recommended one, and the binding turns it into a Python
+    warning instead of an error."""
+    import warnings
+    import paper_2508_18221_gb300 as pkg
+    msg = lib.grmhd_strerror(pkg.GRMHD_WPRECISION).decode()
+    assert pkg.GRMHD_WPRECISION > 0 and "TF32" in msg and "precision 1" in msg
+    with warnings.catch_warnings(record=True) as w:
+        warnings.simplefilter("always")
+        pkg.check(pkg.GRMHD_WPRECISION)
+    assert len(w) == 1 and "TF32" in str(w[0].message)
+    with pytest.raises(pkg.GrmhdError):
+        pkg.check(pkg.GRMHD_EINVAL)

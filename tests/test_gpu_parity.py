@@ -47,7 +47,8 @@ def pkg():
 
 def _ctx(pkg, cfg, **kw):
     import torch
-    opt_keys = ("evolve_metric", "gauge", "integrator", "filter", "contraction", "coupling", "glm", "precision")
+    opt_keys = ("evolve_metric", "gauge", "integrator", "filter", "contraction", "coupling", "glm", "precision",
+                "c2p_lambda", "c2p_maxit", "c2p_tol")
     grid, phys, opts = pkg.make_structs(cfg, **{k: v for k, v in kw.items() if k in opt_keys})
     return pkg.Context(grid, phys, opts, torch.cuda.current_stream().cuda_stream)
 
@@ -209,6 +210,58 @@ def test_con2prim_parity(pkg):
     for i in range(7):
         sc = vmax if i in (1, 2, 3) else np.abs(ref[i]).max()
         assert np.abs(P[i] - ref[i]).max() <= 1e-12 * sc, i
+    ctx.close()
+
+
+def _damped_prims(U, g, p, maxit, tol):
+    """The oracle's damped recovery (the paper's iteration) from the dust estimates."""
+    from oracle import valencia as va
+    f = so.unpack_bssn(U)
+    gam, sqg = so.metric_from_bssn(f)
+    D = U[so.I_D] / sqg
+    S = so.vec_from(U, so.I_S) / sqg[..., None]
+    tau = U[so.I_TAU] / sqg
+    B = so.vec_from(U, so.I_B) / sqg[..., None]
+    r0, v0, e0 = va.con2prim_damped_guess(D, S, tau, gam, eps_min=p.eps_atm)
+    rho, v, eps, pr, W, ok, _ = va.con2prim_damped(D, S, tau, B, gam, p.gamma_eos, r0, v0, e0, lam0=0.5,
+                                                   maxit=maxit, tol=tol, eps_min=p.eps_atm)
+    return {"rho": rho, "v": v, "eps": eps, "p": pr, "W": W, "ok": ok, "B": B}
+
+
+@pytest.mark.parametrize("maxit", [40, 400])
+def test_con2prim_damped_parity(pkg, maxit):
+    """opts.c2p_lambda = 0.5: the paper's damped iteration on the GPU against the oracle's
+    con2prim_damped from the same start (the dust estimates: the state was just set), with
+    the same iteration limit and tolerance, and the right-hand side built on it; the
+    distance of both to the exact root is printed (the paper's 40 iterations: ~1e-9)."""
+    import torch
+    cfg = config("c1")
+    g, p, U = _oracle(cfg)
+    tol = 1e-13
+    ctx = _ctx(pkg, cfg, c2p_lambda=0.5, c2p_maxit=maxit, c2p_tol=tol)
+    ctx.set_state(torch.from_numpy(U.reshape(-1).copy()).cuda(), True)
+    out = torch.empty(7 * U[0].size, dtype=torch.float64, device="cuda")
+    nf = ctx.con2prim(out, True)
+    P = out.cpu().numpy().reshape((7,) + U.shape[1:])
+    ref = _damped_prims(U, g, p, maxit, tol)
+    exact = so.primitives(U, p)
+    assert nf == int(np.sum(~ref["ok"]))
+    names = ("rho", "v^r", "v^theta", "v^phi", "eps", "p", "W")
+    refs = [ref["rho"], ref["v"][..., 0], ref["v"][..., 1], ref["v"][..., 2], ref["eps"], ref["p"], ref["W"]]
+    exs = [exact["rho"], exact["v"][..., 0], exact["v"][..., 1], exact["v"][..., 2], exact["eps"],
+           exact["p"], exact["W"]]
+    vmax = max(np.abs(refs[i]).max() for i in (1, 2, 3))
+    for i in range(7):
+        sc = vmax if i in (1, 2, 3) else np.abs(refs[i]).max()
+        err = np.abs(P[i] - refs[i]).max() / sc
+        dist = np.abs(P[i] - exs[i]).max() / sc
+        print(f"[c2p damped {maxit}] {names[i]}: GPU vs oracle iteration {err:.2e}, "
+              f"GPU vs exact root {dist:.2e}")
+        assert err <= 1e-10, (names[i], err)
+    # the right-hand side on the damped primitives
+    R = _gpu_rhs(pkg, ctx, U)
+    fn = lambda X: so.rhs_from_prims(X, _damped_prims(X, g, p, maxit, tol), g, p)  # noqa: E731
+    assert_parity(R, fn(U), f"rhs on the damped recovery ({maxit} iterations)", fn, U, trials=2)
     ctx.close()
 
 
