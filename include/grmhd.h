@@ -306,11 +306,15 @@ const char* grmhd_batch_last_error(const grmhd_batch* b);
  * the canonical node order; rho is the primitive rest-mass density.  At most `iters`
  * iterations, fewer when max |psi_{k+1} - psi_k| < tol (tol = 0: all).  psi_out (may be NULL)
  * receives psi; changes (iters entries, may be NULL) the change of every iteration; stats
- * (3 entries, may be NULL) the set-up time in ms (operator assembly and LU factorisation),
- * the mean time per iteration and the iterations done.  Needs theta_basis = 1 and a
- * single-instance context (GRMHD_EUNSUPPORTED otherwise, or when cuSOLVER cannot be
- * opened: the dense per-phi-mode LU is its dgetrf / dgetrs); GRMHD_ENAN when the fixed
- * point diverges (too dense a source).  Allocates (N_phi/2 + 1) (E n_r n_theta)^2 doubles
+ * (3 entries, may be NULL) the set-up time in ms (the angular operators' real Schur forms
+ * on the host and the inversion of the radial systems), the mean time per iteration
+ * and the iterations done.  Each phi mode's operator is solved through the real Schur form
+ * Q T Q^T of its angular part: in the orthogonal basis Q it is block upper triangular, a back
+ * substitution over n_theta radial systems of E n_r unknowns, which the library inverts
+ * and solves in its own kernels.  Needs theta_basis = 1 and a single-instance context
+ * (GRMHD_EUNSUPPORTED otherwise, or when an angular operator has no real Schur form, or
+ * above 12,800 radial nodes); GRMHD_ENAN when the fixed
+ * point diverges (too dense a source).  Allocates 2 (N_phi/2 + 1) n_theta (E n_r)^2 doubles
  * of device memory for the call. */
 int grmhd_xcts_init(grmhd_ctx* ctx, const double* rho, const double* p, const double* vr,
                     const double* vth, const double* vph, const double* A_phi, int iters, double tol,

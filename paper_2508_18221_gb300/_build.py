@@ -13,7 +13,7 @@ LIB = os.path.join(HERE, "libgrmhd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["kernels_point.cu", "kernels_deriv.cu", "kernels_eo.cu", "kernels_tc.cu", "kernels_fx.cu", "api.cu",
       "noalloc.cu", "kernels_xcts.cu"]
-CPP = ["host_ops.cpp"]
+CPP = ["host_ops.cpp", "host_eig.cpp"]
 
 
 def _nvcc():

@@ -148,7 +148,7 @@ struct XctsOps {
     double M, r_min, r_max;
 };
 // psi_host: initial guess in, solution out (num_points values); changes (iters entries, may
-// be null): max |psi_{k+1} - psi_k|; stats (may be null): set-up ms (assembly + LU),
+// be null): max |psi_{k+1} - psi_k|; stats (may be null): set-up ms (Schur forms + inverses),
 // mean ms per iteration, iterations done; returns a GRMHD status, message in msg
 int xcts_solve(const XctsOps& o, const double* rho_host, double* psi_host, int iters, double tol,
                double* changes, double* stats, cudaStream_t s, char* msg, size_t msglen);

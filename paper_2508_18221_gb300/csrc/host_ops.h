@@ -36,4 +36,9 @@ void prim_to_cons_point(double rho, double p, const double v_u[3], const double 
                         const double g[3][3], double gam_eos, double* D, double S_d[3],
                         double* tau);
 void metric_from_bssn_point(const double* bssn, double g[3][3], double* sqg);
+// real Schur form of a real n x n row-major matrix with a real spectrum (host_eig.cpp):
+// A = Q T Q^T with Q orthogonal and T upper triangular (both row-major n x n); *resid (may
+// be null) max |Q T Q^T - A| / max |A|; false on a complex pair, no convergence or a
+// residual above 1e-11
+bool real_schur(int n, const double* A, double* Q, double* T, double* resid);
 }  // namespace gk

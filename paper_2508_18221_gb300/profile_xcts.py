@@ -1,5 +1,6 @@
 """Timing driver of the approximate XCTS initial-data solve (grmhd_xcts_init): set-up
-(operator assembly + per-phi-mode LU) and time per fixed-point iteration.
+(real Schur forms of the angular operators + inverses of the radial systems) and time per fixed-point
+iteration.
 
     python -m paper_2508_18221_gb300.profile_xcts --config x2 --iters 12
 """

@@ -2,10 +2,11 @@
 
 Both sides run the same number of fixed-point iterations from the puncture 1 + M/(2r); the
 oracle solves the whole 3-D boundary-value problem with one dense matrix built from its own
-derivative operators, the library per phi mode (dense LU of each mode's (r, theta)
-operator).  Bars: psi within 1e-11 of max psi (the solves' rounding: the spectral
-Laplacian's condition number times 2^-53, measured ~1e-13), the state at the FP64 parity
-bar 1e-11 of the per-tensor scale.
+derivative operators, the library per phi mode through the real Schur form of its angular
+operator (a back substitution over radial systems, factorised and solved in the library's
+own kernels).  Bars: psi within 1e-11 of max psi (the solves' rounding: the
+spectral Laplacian's condition number times 2^-53, measured ~1e-13), the state at the FP64
+parity bar.
 """
 import numpy as np
 import pytest
