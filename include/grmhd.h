@@ -320,6 +320,30 @@ int grmhd_xcts_init(grmhd_ctx* ctx, const double* rho, const double* p, const do
                     const double* vth, const double* vph, const double* A_phi, int iters, double tol,
                     double* psi_out, double* changes, double* stats);
 
+/* Autotuner of the FP64 digit-slice contractions (a service of the library, outside the
+ * paper).  The tensor-core contraction of a class (direction dir 0 r / 1 theta / 2 phi,
+ * nodes n along it, accumulators nacc: 6 for derivatives, 5 for the filter) runs either with
+ * one TMEM accumulator set (two CTAs per SM up to 6 x 32 columns) or with two (one CTA per
+ * SM; the MMAs of the next 128-line tile run while the previous tile's results are
+ * converted and stored).  A process-wide table keeps the choice per class: 0 = not tuned
+ * (one set), 1 or 2 sets.  At the first context or batch of a process the library reads
+ * the table a previous run stored, from the file the environment variable
+ * GRMHD_TUNING_FILE names or else fx_tuning.txt next to the library (lines
+ * "dir n nacc sets"; python -m paper_2508_18221_gb300.autotune writes it).
+ * grmhd_tune_contractions times both choices for every class the context uses (nfields
+ * fields of its own state per launch, reps launches each, CUDA events on its stream), keeps
+ * the faster in the table (two sets only when they are at least 2 % faster: the
+ * launch-to-launch spread is about 1 %) and returns the mean ms per launch in ms_out[(dir * 2 + kind) * 2 +
+ * sets - 1] (kind 0 derivative, 1 filter; -1 where the choice does not exist) and the choice
+ * in choice_out[dir * 2 + kind] (0 where the class runs on the FP64 units); either may be
+ * NULL.  It overwrites the context's scratch buffers only.  GRMHD_EINVAL for nfields
+ * outside [1, 32] or reps < 1; GRMHD_EUNSUPPORTED on a batch's group context.
+ * grmhd_tune_set sets one entry (GRMHD_EINVAL outside the ranges above); grmhd_tune_get
+ * returns it (or GRMHD_EINVAL). */
+int grmhd_tune_contractions(grmhd_ctx* ctx, int nfields, int reps, double* ms_out, int* choice_out);
+int grmhd_tune_set(int dir, int n, int nacc, int sets);
+int grmhd_tune_get(int dir, int n, int nacc);
+
 /* Test hook: apply the first derivative along direction dir (0 r, 1 theta, 2 phi) to
  * `nfields` canonical fields (nfields * num_points doubles) with the library's
  * operators (radial: per element, one-sided at element ends).  Device pointers. */

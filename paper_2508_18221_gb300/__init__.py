@@ -77,6 +77,9 @@ SIGNATURES = {
     "grmhd_batch_destroy": (C.c_int, [_P]),
     "grmhd_batch_last_error": (C.c_char_p, [_P]),
     "grmhd_xcts_init": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int, C.c_double, _P, _P, _P]),
+    "grmhd_tune_contractions": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
+    "grmhd_tune_set": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int]),
+    "grmhd_tune_get": (C.c_int, [C.c_int, C.c_int, C.c_int]),
     "grmhd_debug_deriv": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
     "grmhd_debug_theta": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "grmhd_debug_wait_timeout": (C.c_int, [_P]),
@@ -234,6 +237,20 @@ class Context:
         by = (C.c_double * n)()
         self._chk(self.lib.grmhd_kernel_times(self.h, int(reps), ms, fl, by, n))
         return {k: (ms[i], fl[i], by[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def tune_contractions(self, nfields: int = 21, reps: int = 10):
+        """Run the contraction autotuner on this context (grmhd_tune_contractions): returns
+        {(direction, kind): (ms with one accumulator set, ms with two, chosen sets)}, kind
+        "derivative" or "filter"; classes on the FP64 units are left out."""
+        ms = (C.c_double * 12)()
+        ch = (C.c_int * 6)()
+        self._chk(self.lib.grmhd_tune_contractions(self.h, nfields, reps, ms, ch))
+        out = {}
+        for d in range(3):
+            for k, kind in enumerate(("derivative", "filter")):
+                if ch[d * 2 + k]:
+                    out[(d, kind)] = (ms[(d * 2 + k) * 2], ms[(d * 2 + k) * 2 + 1], int(ch[d * 2 + k]))
+        return out
 
     def debug_deriv(self, src, dst, nfields: int, direction: int):
         self._chk(self.lib.grmhd_debug_deriv(self.h, _ptr(src), _ptr(dst), nfields, direction))

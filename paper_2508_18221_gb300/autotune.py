@@ -1,0 +1,76 @@
+"""Autotuner of the FP64 digit-slice contractions: for every (direction, nodes,
+accumulators) class of the given workloads it times the contraction with one and with two
+TMEM accumulator sets on a context of that shape (grmhd_tune_contractions) and writes the
+faster choice per class to fx_tuning.txt next to the library, which every later process
+reads at its first context.
+
+    python -m paper_2508_18221_gb300.autotune --workloads c2,c4,c5 [--out PATH]
+
+Shapes: each single-instance workload as it is; for the batched workload every group shape
+(N_r = N_theta in {8, 12, 16, 24, 32}, N_phi in {16, 32, 64}) as an 8-element instance.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workloads", default="c2,c4")
+    ap.add_argument("--out", default=None, help="tuning file (default: fx_tuning.txt next to the library)")
+    ap.add_argument("--nfields", type=int, default=21)
+    ap.add_argument("--reps", type=int, default=10)
+    a = ap.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import torch
+
+    import paper_2508_18221_gb300 as pkg
+    from workloads import config, batch_configs, primitive_profiles
+
+    shapes = []
+    for w in a.workloads.split(","):
+        if w == "c4":
+            seen = set()
+            for c in batch_configs(256):
+                key = (c.n_r, c.n_theta, c.n_phi)
+                if key not in seen:
+                    seen.add(key)
+                    shapes.append((f"c4 group {key}", config("c2", n_elem=8, n_r=c.n_r, n_theta=c.n_theta,
+                                                               n_phi=c.n_phi)))
+        else:
+            shapes.append((w, config(w)))
+    lib = pkg.load()
+    table = {}
+    stream = torch.cuda.Stream()
+    for name, cfg in shapes:
+        grid, phys, opts = pkg.make_structs(cfg)
+        ctx = pkg.Context(grid, phys, opts, stream.cuda_stream)
+        r, t, ph = ctx.coords()
+        pr = primitive_profiles(cfg, r.reshape(cfg.shape), t.reshape(cfg.shape), ph.reshape(cfg.shape))
+        ctx.init_prims(pr["rho"], pr["p"], pr["vr"], pr["vth"], pr["vph"], pr["A_phi"])
+        res = ctx.tune_contractions(nfields=a.nfields, reps=a.reps)
+        ns = (cfg.n_r, cfg.n_theta, cfg.n_phi)
+        for (d, kind), (m1, m2, ch) in sorted(res.items()):
+            nacc = 6 if kind == "derivative" else 5
+            key = (d, ns[d], nacc)
+            table[key] = ch
+            two = f"{m2:.4f} ms" if m2 >= 0 else "n/a"
+            print(f"{name:28s} dir {d} n {ns[d]:3d} {kind:10s} one set {m1:.4f} ms, two sets {two} -> {ch}",
+                  flush=True)
+        ctx.close()
+    out = a.out or os.path.join(os.path.dirname(pkg.LIB_PATH), "fx_tuning.txt")
+    with open(out, "w") as fh:
+        fh.write("# digit-slice contraction tuning: direction nodes accumulators sets "
+                 "(python -m paper_2508_18221_gb300.autotune)\n")
+        for (d, n, nacc), ch in sorted(table.items()):
+            fh.write(f"{d} {n} {nacc} {ch}\n")
+    print(f"wrote {out} ({len(table)} classes)")
+    assert lib is not None
+
+
+if __name__ == "__main__":
+    main()

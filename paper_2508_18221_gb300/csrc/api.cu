@@ -10,12 +10,15 @@
 // A time step adds the filter (3 directional contractions + interface mean of the BSSN
 // copies).  grmhd_step records nsteps steps into one CUDA graph.
 #include <cuda_runtime.h>
+#include <dlfcn.h>
 
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -301,8 +304,39 @@ static bool same_group(const grmhd_grid& g0, const grmhd_physics& p0, const grmh
            p.gamma_eos == p0.gamma_eos && p.rho_atm == p0.rho_atm && p.eps_atm == p0.eps_atm;
 }
 
+// The contraction tuning table a previous autotuner run stored: the file GRMHD_TUNING_FILE
+// names, else fx_tuning.txt next to this library; lines "direction nodes accumulators sets"
+// ('#' starts a comment).  Read once per process, at the first context or batch.
+static std::once_flag g_tuning_once;
+extern "C" int grmhd_create(const grmhd_grid*, const grmhd_physics*, const grmhd_opts*, void*, grmhd_ctx**);
+static void load_tuning_file() {
+    std::string path;
+    const char* env = getenv("GRMHD_TUNING_FILE");
+    if (env && *env) {
+        path = env;
+    } else {
+        Dl_info info;
+        if (!dladdr((void*)&grmhd_create, &info) || !info.dli_fname) return;
+        path = info.dli_fname;
+        const size_t pos = path.rfind('/');
+        path = (pos == std::string::npos ? std::string() : path.substr(0, pos + 1)) + "fx_tuning.txt";
+    }
+    FILE* f = fopen(path.c_str(), "r");
+    if (!f) return;
+    char line[256];
+    while (fgets(line, sizeof(line), f)) {
+        if (line[0] == '#') continue;
+        int dir, n, nacc, ts;
+        if (sscanf(line, "%d %d %d %d", &dir, &n, &nacc, &ts) == 4 && dir >= 0 && dir <= 2 && n >= 2 && n <= 128 &&
+            (nacc == 5 || nacc == 6) && ts >= 0 && ts <= 2)
+            fx_tune_set(dir, n, nacc, ts);
+    }
+    fclose(f);
+}
+
 static int ctx_create(int ninst, const grmhd_grid* grids, const grmhd_physics* physs,
                       const grmhd_opts* opts, void* cuda_stream, grmhd_ctx** out) {
+    std::call_once(g_tuning_once, load_tuning_file);
     if (!out || ninst < 1 || !grids || !physs || !opts) return GRMHD_EINVAL;
     *out = nullptr;
     char msg[256] = {0};
@@ -1523,6 +1557,90 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
         if (flops_out) flops_out[k] = fl[k];
         if (bytes_out) bytes_out[k] = by[k];
     }
+    return GRMHD_OK;
+}
+
+// ------------------------------------------------------------------ contraction autotuner
+// The digit-slice contraction can run with one TMEM accumulator set (two CTAs per SM for up
+// to 6 x 32 columns) or two (one CTA per SM; the MMAs of the next item overlap the epilogue
+// of the previous one).  Which is faster depends on the class (direction, nodes,
+// accumulators); the autotuner times both on the context's own buffers and records the
+// faster one in the process-wide table every later launch of that class reads.
+extern "C" int grmhd_tune_set(int dir, int n, int nacc, int tsets) {
+    if (dir < 0 || dir > 2 || n < 2 || n > 128 || (nacc != 5 && nacc != 6) || tsets < 0 || tsets > 2)
+        return GRMHD_EINVAL;
+    fx_tune_set(dir, n, nacc, tsets);
+    return GRMHD_OK;
+}
+
+extern "C" int grmhd_tune_get(int dir, int n, int nacc) {
+    if (dir < 0 || dir > 2 || n < 2 || n > 128 || (nacc != 5 && nacc != 6)) return GRMHD_EINVAL;
+    return fx_tune_get(dir, n, nacc);
+}
+
+extern "C" int grmhd_tune_contractions(grmhd_ctx* c, int nfields, int reps, double* ms_out, int* choice_out) {
+    NvtxRange nvtx_range("grmhd_tune_contractions");
+    if (!c || nfields < 1 || nfields > 32 || reps < 1) return GRMHD_EINVAL;
+    if (c->n_inst != 1) return set_err(c, GRMHD_EUNSUPPORTED, "tuning runs on a single-instance context");
+    const long long P = c->d.P;
+    std::vector<DerivJob> jb(nfields);
+    for (int f = 0; f < nfields; f++) {
+        jb[f].src = c->U[0] + (long long)f * P;
+        jb[f].dst = c->scratch + (long long)f * P;
+        jb[f].accumulate = 0;
+        jb[f].pad = 0;
+    }
+    CK(cudaMemcpyAsync(c->jobs + c->job_dbg, jb.data(), sizeof(DerivJob) * nfields, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return set_err(c, GRMHD_ECUDA, "events"); }
+    const int Ns[3] = {c->d.Nr, c->d.Nt, c->d.Np};
+    int st = GRMHD_OK;
+    for (int dir = 0; dir < 3 && st == GRMHD_OK; dir++)
+        for (int kind = 0; kind < 2 && st == GRMHD_OK; kind++) {      // 0 derivative, 1 filter
+            const int nacc = kind == 0 ? 6 : 5, N = Ns[dir];
+            const bool ftd = dir == 1 && c->ft;
+            const uint8_t* img = ftd ? (kind == 0 ? c->fx_dt[0] : c->fx_ft[0]) : (kind == 0 ? c->fx_d[dir] : c->fx_f[dir]);
+            // Chebyshev derivatives above 64 nodes run on the FP64 units
+            if (kind == 0 && dir < 2 && !c->ft && N > 64) img = nullptr;
+            const Dims& dd = ftd ? c->dh : c->d;
+            const long long estride = (dir == 0 && kind == 0) ? c->fx_estride : 0;
+            double best_ms = 1e30;
+            int best = 1;
+            for (int ts = 1; ts <= 2; ts++) {
+                double ms = -1.0;
+                if (img && fx_supported(dir, N) && (ts == 1 || fx_two_sets_possible(dir, N, nacc))) {
+                    cudaError_t e = launch_contract_fx(dir, dd, c->jobs + c->job_dbg, nfields, img, estride, c->tc_err,
+                                                       c->stream, 0, nacc, ts);
+                    cudaEventRecord(e0, c->stream);
+                    for (int r = 0; r < reps && e == cudaSuccess; r++)
+                        e = launch_contract_fx(dir, dd, c->jobs + c->job_dbg, nfields, img, estride, c->tc_err, c->stream,
+                                               0, nacc, ts);
+                    cudaEventRecord(e1, c->stream);
+                    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                        st = set_err(c, GRMHD_ECUDA, "tuning launch: %s", cudaGetErrorString(e));
+                        break;
+                    }
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    ms = t / reps;
+                    // a second set must win by 2 % (launch-to-launch noise is about 1 %)
+                    if (ts == 1 || ms < 0.98 * best_ms) { best_ms = ms; best = ts; }
+                }
+                if (ms_out) ms_out[(dir * 2 + kind) * 2 + (ts - 1)] = ms;
+            }
+            if (st) break;
+            if (img) fx_tune_set(dir, N, nacc, best);
+            if (choice_out) choice_out[dir * 2 + kind] = img ? best : 0;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    int te = 0;
+    CK(cudaMemcpyAsync(&te, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (te) return set_err(c, GRMHD_ETIMEOUT, "a tuning launch timed out");
     return GRMHD_OK;
 }
 

@@ -34,6 +34,10 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "grmhd_internal.h"
 
 namespace gk {
@@ -231,6 +235,8 @@ struct FxParams {
     uint32_t stg_bytes;
     int* err;
     int stall;               // test of the wait limits: the staging warp issues no copies
+    int tsets;               // TMEM accumulator sets: 1, or 2 (item k in set k % 2: the MMAs of
+                             // item k + 1 run while the epilogue drains item k; needs b_all)
 };
 
 template <int DIR>
@@ -304,7 +310,7 @@ constexpr int NA_RING = 2;
 // converters write item k's line exponents while the epilogue still reads item k - 1's
 struct FxBars {
     uint64_t stg_full[2], stg_empty[2], a_full[NA_RING], a_empty[NA_RING];
-    uint64_t acc_full, acc_empty[2], el_ready[2], b_full;
+    uint64_t acc_full[2], acc_empty[2], el_ready[2], b_full;
 };
 
 __device__ __forceinline__ uint64_t gtimer() {
@@ -329,6 +335,20 @@ __device__ __forceinline__ bool bwait(uint64_t* bar, uint32_t parity, volatile i
             *abort_flag = 1;
             return false;
         }
+    }
+}
+
+// wait for a phase regardless of the abort flag, at most `ns` nanoseconds (the wind-down
+// after an abort: work issued before it must finish before TMEM is freed)
+__device__ __forceinline__ bool bwait_for(uint64_t* bar, uint32_t parity, uint64_t ns) {
+    const uint64_t t0 = gtimer();
+    for (;;) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(smem_u32(bar)), "r"(parity), "r"(10000u) : "memory");
+        if (done) return true;
+        if (gtimer() - t0 > ns) return false;
     }
 }
 
@@ -377,8 +397,8 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars->a_full[a])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars->a_empty[a])));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars->acc_full)));
         for (int t = 0; t < 2; t++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars->acc_full[t])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars->acc_empty[t])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars->el_ready[t])));
         }
@@ -399,6 +419,7 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
     if (warp == 8) {
         // ---------------------------------------------------------------- staging
         int k = 0;
+        int last_k[2] = {-1, -1};          // last item staged into each buffer
         for (long long it = blockIdx.x; it < nitems; it += gridDim.x, k++) {
             const int b = k % fp.nstg;
             if (k >= fp.nstg) {
@@ -410,10 +431,16 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
             FxTile tl;
             int pass, job;
             fx_item<DIR>(fp, d, it, &tl, &pass, &job);
-            if (!fp.stall)
+            if (!fp.stall) {
                 fx_stage<DIR>(d, tl, N, fp.jobs[job].src, reinterpret_cast<double*>(sm + b * fp.stg_bytes),
                               &bars->stg_full[b], lane);
+                last_k[b] = k;
+            }
         }
+        // after an abort, the copies already issued land before the CTA frees its memory
+        if (*abort_flag && lane == 0)
+            for (int b = 0; b < fp.nstg; b++)
+                if (last_k[b] >= 0) bwait_for(&bars->stg_full[b], (uint32_t)((last_k[b] / fp.nstg) & 1), 1000000ull);
     } else if (warp == 9) {
         // ---------------------------------------------------------------- MMA issue
         if (lane == 0) {
@@ -421,13 +448,21 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
             const uint32_t lbo = 128u, sbo = (uint32_t)kcores * 128u;
             int k = 0, cur_e = -1;
             uint32_t n_b = 0;
+            int last_cg = -1, last_item = -1;   // last chunk / item whose MMAs were committed
             for (long long it = blockIdx.x; it < nitems; it += gridDim.x, k++) {
                 FxTile tl;
                 int pass, job;
                 fx_item<DIR>(fp, d, it, &tl, &pass, &job);
-                // the previous item's MMAs have finished with TMEM and the operator
-                if (k > 0 && !bwait(&bars->acc_empty[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), abort_flag)) break;
+                // the epilogue has drained the accumulator set this item writes (item k - tsets)
+                const int ts = fp.tsets;
+                if (k >= ts && !bwait(&bars->acc_empty[(k - ts) & 1], (uint32_t)(((k - ts) >> 1) & 1), abort_flag))
+                    break;
                 const uint8_t* op = fp.img + (DIR == 0 ? tl.e * fp.img_estride : 0);
+                // with two sets the previous item's MMAs may still read the operator: they
+                // finish (its commit) before a new element's operator overwrites it
+                if (ts > 1 && k > 0 && fp.b_all && cur_e != tl.e &&
+                    !bwait(&bars->acc_full[(k - 1) % ts], (uint32_t)(((k - 1) / ts) & 1), abort_flag))
+                    break;
                 if (fp.b_all && cur_e != tl.e) {  // radial: per-element operator; theta, phi: once
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
                                      smem_u32(&bars->b_full)),
@@ -475,16 +510,27 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
                         for (int q = 0; q <= sd; q++) {
                             const int l = sd - q;
                             const bool first = kc == 0 && q == 0 && (sd < NA - 1 || sd == NDIG - 1);
-                            mma_bf16(tmem + (uint32_t)(g * Npp), smem_desc(a0 + q * a_bytes, lbo, sbo),
+                            mma_bf16(tmem + (uint32_t)((k % ts) * NA * Npp + g * Npp), smem_desc(a0 + q * a_bytes, lbo, sbo),
                                      smem_desc(b0 + l * b_bytes, lbo, sbo), id, first ? 0u : 1u);
                         }
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         smem_u32(&bars->a_empty[a])));
+                    last_cg = cg;
                 }
                 if (stop) break;
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&bars->acc_full)));
+                    smem_u32(&bars->acc_full[k % ts])));
+                last_item = k;
+            }
+            // after an abort, the MMAs already committed finish writing TMEM, and an operator
+            // copy already issued lands, before TMEM and shared memory are given up
+            if (*abort_flag) {
+                if (last_cg >= 0)
+                    bwait_for(&bars->a_empty[last_cg % NA_RING], (uint32_t)((last_cg / NA_RING) & 1), 1000000ull);
+                if (last_item >= 0)
+                    bwait_for(&bars->acc_full[last_item % fp.tsets], (uint32_t)((last_item / fp.tsets) & 1), 1000000ull);
+                if (n_b > 0) bwait_for(&bars->b_full, (n_b - 1) & 1, 1000000ull);
             }
         }
         __syncwarp();
@@ -574,7 +620,7 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
             const DerivJob jb = fp.jobs[job];  // loaded before the waits
             const int t = k & 1;
             if (!bwait(&bars->el_ready[t], (uint32_t)((k >> 1) & 1), abort_flag)) break;
-            if (!bwait(&bars->acc_full, (uint32_t)(k & 1), abort_flag)) break;
+            if (!bwait(&bars->acc_full[k % fp.tsets], (uint32_t)((k / fp.tsets) & 1), abort_flag)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const bool valid = m < tl.nlines;
             long long base, stride;
@@ -594,11 +640,16 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
             }
             const int EL = sEL[t * 128 + m];
             const bool line_bad = EL == 0x7FF;
-            for (int cb = 0; cb < Npp; cb += 8) {
+            // column blocks holding output rows of this pass (the padding blocks beyond N are
+            // computed by the MMAs but not read)
+            const int ncol = min(Npp, N - pass * Npp);
+            const int cb_end = (ncol + 7) & ~7;
+            const uint32_t set_col = (uint32_t)((k % fp.tsets) * NA * Npp);
+            for (int cb = 0; cb < cb_end; cb += 8) {
                 uint32_t r[NA][8];
 #pragma unroll
                 for (int g = 0; g < NA; g++) {
-                    const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * Npp + cb);
+                    const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + set_col + (uint32_t)(g * Npp + cb);
                     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                                  : "=r"(r[g][0]), "=r"(r[g][1]), "=r"(r[g][2]), "=r"(r[g][3]), "=r"(r[g][4]),
                                    "=r"(r[g][5]), "=r"(r[g][6]), "=r"(r[g][7])
@@ -609,7 +660,7 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
                 int X[8];
 #pragma unroll
                 for (int j = 0; j < 8; j++) X[j] = EL + sF[t * 128 + c0 + j] - 2096;
-                if (cb + 8 >= Npp) {
+                if (cb + 8 >= cb_end) {
                     // every accumulator column has been read, and the row exponents too:
                     // hand TMEM (and this set of sEL, sF) back before the last block's
                     // arithmetic, so that the next item's MMAs start under it
@@ -652,9 +703,10 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
     __syncthreads();
     if (tid == 0 && *abort_flag) atomicExch(fp.err, 1);
     if (*abort_flag) {
-        // bulk copies issued before the abort land within microseconds: give them 2 ms
+        // the staging and MMA roles waited above for their own copies and MMAs; a further
+        // 0.2 ms covers any copy whose barrier phase was already past when they looked
         const uint64_t t0 = gtimer();
-        while (gtimer() - t0 < 2000000ull) {
+        while (gtimer() - t0 < 200000ull) {
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -690,15 +742,19 @@ static size_t fx_rest_bytes(int N, int b_all) {
 // dynamic shared memory, at least 1/(ctas + 1) of the SM so that no further CTA co-resides
 // (its TMEM allocation would wait for a CTA to finish all of its work)
 struct FxCfg {
-    int cols, ctas, nstg, b_all;
+    int cols, ctas, nstg, b_all, tsets;
     size_t smem;
 };
-static FxCfg fx_cfg(int dir, int N, int na) {
+// tsets = 2 asks for two accumulator sets (one CTA per SM for 6 x 32 columns); it falls back
+// to one set when they do not fit the 512 TMEM columns or the operator is not resident
+static FxCfg fx_cfg(int dir, int N, int na, int tsets = 1) {
     int Np, Kp, KC;
     fx_geometry(N, &Np, &Kp, &KC);
     FxCfg c;
     const int Npp = Np > 64 ? 64 : Np;
-    const int need = na * Npp;
+    if (tsets == 2 && 2 * na * Npp > 512) tsets = 1;
+    c.tsets = tsets;
+    const int need = tsets * na * Npp;
     c.cols = need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : (need <= 256 ? 256 : 512)));
     c.ctas = c.cols <= 256 ? 2 : 1;
     size_t share = 233472 / c.ctas - 1024;
@@ -709,6 +765,7 @@ static FxCfg fx_cfg(int dir, int N, int na) {
         share = 233472 - 1024;
         c.b_all = stg + fx_rest_bytes(N, 1) <= share;
     }
+    if (c.tsets == 2 && !c.b_all) return fx_cfg(dir, N, na, 1);
     const size_t rest = fx_rest_bytes(N, c.b_all);
     c.nstg = 2 * stg + rest <= share ? 2 : 1;
     const size_t b = c.nstg * stg + rest;
@@ -719,11 +776,35 @@ static FxCfg fx_cfg(int dir, int N, int na) {
 
 static size_t fx_smem_max(int dir, int na) {
     size_t mx = 0;
-    for (int n = 2; n <= 128; n++) {
-        const size_t b = fx_cfg(dir, n, na).smem;
-        mx = b > mx ? b : mx;
-    }
+    for (int n = 2; n <= 128; n++)
+        for (int ts = 1; ts <= 2; ts++) {
+            const size_t b = fx_cfg(dir, n, na, ts).smem;
+            mx = b > mx ? b : mx;
+        }
     return mx;
+}
+
+// ---- tuning table: accumulator sets per (direction, nodes, accumulators) class, chosen by
+// the autotuner (grmhd_tune_contractions) or read from a tuning file; 0 = not tuned (one set)
+namespace {
+std::mutex g_tune_lock;
+std::map<std::tuple<int, int, int>, int> g_tune;
+}  // namespace
+
+void fx_tune_set(int dir, int N, int nacc, int tsets) {
+    std::lock_guard<std::mutex> lk(g_tune_lock);
+    g_tune[std::make_tuple(dir, N, nacc)] = tsets;
+}
+
+int fx_tune_get(int dir, int N, int nacc) {
+    std::lock_guard<std::mutex> lk(g_tune_lock);
+    auto it = g_tune.find(std::make_tuple(dir, N, nacc));
+    return it == g_tune.end() ? 0 : it->second;
+}
+
+bool fx_two_sets_possible(int dir, int N, int nacc) {
+    if (!fx_supported(dir, N)) return false;
+    return fx_cfg(dir, N, nacc, 2).tsets == 2;
 }
 
 template <int DIR, int NA>
@@ -743,7 +824,7 @@ cudaError_t fx_init() {
 }
 
 cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int njobs, const uint8_t* img,
-                               long long img_estride, int* err, cudaStream_t s, int stall, int nacc) {
+                               long long img_estride, int* err, cudaStream_t s, int stall, int nacc, int tsets) {
     if (njobs <= 0) return cudaSuccess;
     if (nacc != NACC && nacc != 6) return cudaErrorNotSupported;
     const int N = dir == 0 ? d.Nr : (dir == 1 ? d.Nt : d.Np);
@@ -762,7 +843,8 @@ cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int
     fp.Kp = Kp;
     fp.Npp = Np > 64 ? 64 : Np;
     fp.npass = Np / fp.Npp;
-    const FxCfg cfg = fx_cfg(dir, N, nacc);
+    if (tsets <= 0) tsets = fx_tune_get(dir, N, nacc);
+    const FxCfg cfg = fx_cfg(dir, N, nacc, tsets == 2 ? 2 : 1);
     fp.tmem_cols = cfg.cols;
     fp.nstg = cfg.nstg;
     fp.b_all = cfg.b_all;
@@ -770,6 +852,7 @@ cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int
     fp.stg_bytes = fx_stg_bytes(dir, N);
     fp.err = err;
     fp.stall = stall;
+    fp.tsets = cfg.tsets;
     if (dir == 0) fp.ntiles = (long long)d.E * ((d.NtNp + 127) / 128);
     else if (dir == 1) fp.ntiles = ((long long)d.E * d.Nr * d.Np + 127) / 128;
     else fp.ntiles = (d.P / N + 127) / 128;

@@ -122,3 +122,16 @@ def test_warning_status_of_the_tf32_mode(lib):
     assert len(w) == 1 and "TF32" in str(w[0].message)
     with pytest.raises(pkg.GrmhdError):
         pkg.check(pkg.GRMHD_EINVAL)
+
+
+def test_tuning_table_entries(lib):
+    """The contraction tuning table (host side): entries in range are kept and read back,
+    entries outside the documented ranges are refused, 0 restores the untuned default."""
+    import paper_2508_18221_gb300 as pkg
+    assert lib.grmhd_tune_set(1, 33, 6, 2) == pkg.GRMHD_OK
+    assert lib.grmhd_tune_get(1, 33, 6) == 2
+    assert lib.grmhd_tune_set(1, 33, 6, 0) == pkg.GRMHD_OK
+    assert lib.grmhd_tune_get(1, 33, 6) == 0
+    for args in ((3, 24, 6, 1), (0, 1, 6, 1), (0, 129, 6, 1), (0, 24, 4, 1), (0, 24, 6, 3), (0, 24, 6, -1)):
+        assert lib.grmhd_tune_set(*args) == pkg.GRMHD_EINVAL, args
+    assert lib.grmhd_tune_get(0, 24, 7) == pkg.GRMHD_EINVAL

@@ -226,3 +226,32 @@ def test_six_accumulators_reach_fp64_accuracy(pkg):
         worst[f"{(nr, nt, nph)[d]} nodes dir {d}"] = float(err.max())
         assert err.max() <= 2e-15, ((nr, nt, nph), d, float(err.max()))
     _report("six_accumulators", worst)
+
+
+@pytest.mark.parametrize("nr,nt,nph", [(24, 32, 64), (8, 12, 16), (32, 32, 32)])
+def test_two_accumulator_sets_are_bitwise_equal(pkg, nr, nt, nph):
+    """One or two TMEM accumulator sets (the tuning choice) change the schedule, not the
+    arithmetic: derivative contractions in every direction give bitwise equal results,
+    and an element change of the radial operator under two sets (the operator reload waits
+    for the previous tile's MMAs) is covered by the multi-element grid."""
+    import torch
+    lib = pkg.load()
+    cfg = config("c1", n_elem=3, n_r=nr, n_theta=nt, n_phi=nph)
+    g, ctx = _setup(pkg, cfg, 0)
+    rng = np.random.default_rng(nr + nt + nph)
+    u = rng.normal(size=(4,) + g.shape) * 10.0 ** rng.uniform(-3, 3, size=(4, 1, 1, 1, 1))
+    src = torch.from_numpy(u.reshape(-1).copy()).cuda()
+    ns = (nr, nt, nph)
+    try:
+        for d in range(3):
+            outs = []
+            for ts in (1, 2):
+                assert lib.grmhd_tune_set(d, ns[d], 6, ts) == pkg.GRMHD_OK
+                dst = torch.zeros_like(src)
+                ctx.debug_deriv(src, dst, 4, d)
+                outs.append(dst.cpu().numpy())
+            np.testing.assert_array_equal(outs[0], outs[1])
+    finally:
+        for d in range(3):
+            lib.grmhd_tune_set(d, ns[d], 6, 0)
+        ctx.close()
