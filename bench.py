@@ -416,17 +416,17 @@ def _kernel_names(cfg, precision):
     for d, dn in enumerate(("r", "theta", "phi")):
         fx = 2 <= ns[d] <= 128 and (d != 2 or ns[d] % 2 == 0)
         fourier = d == 2 or (d == 1 and getattr(cfg, "theta_basis", 0) == 1)
-        # derivatives: six accumulators (Chebyshev above 64 nodes: the FP64 units); the
-        # filter: five
-        fp64_f = f"k_contract_fx<{d}, 5>" if fx else f"k_deriv_eo<{d}>"
-        fp64_d = f"k_contract_fx<{d}, 6>" if fx else f"k_deriv_eo<{d}>"
+        # derivatives and the filter: the digit-slice kernel (Chebyshev derivatives above 64
+        # nodes: the FP64 units)
+        fp64_f = f"k_contract_fx<{d}>" if fx else f"k_deriv_eo<{d}>"
+        fp64_d = f"k_contract_fx<{d}>" if fx else f"k_deriv_eo<{d}>"
         if fx and not fourier and ns[d] > 64:
             fp64_d = f"k_deriv<{d}>"
         if d == 1 and getattr(cfg, "theta_basis", 0) == 1:
             # Fourier theta: fold, two half-width contractions, unfold (timed together)
             fx_t = fx and cfg.n_phi % 4 == 0
-            fp64_f = "theta fold + k_contract_fx<1, 5> x2 + unfold" if fx_t else "theta fold + k_deriv_eo<1> x2 + unfold"
-            fp64_d = "theta fold + k_contract_fx<1, 6> x2 + unfold" if fx_t else fp64_f
+            fp64_f = "theta fold + k_contract_fx<1> x2 + unfold" if fx_t else "theta fold + k_deriv_eo<1> x2 + unfold"
+            fp64_d = fp64_f
             tc = "theta fold + k_contract_tc<1> x2 + unfold"
         else:
             tc = f"k_contract_tc<{d}>"

@@ -111,10 +111,8 @@ typedef struct {
  * the Newton solve.  contraction: how the FP64
  * spectral contractions (all derivatives at precision 0, the filter at every precision)
  * run: 0 (default) on the BF16 tensor cores with exact base-256 digit slices of the
- * FP64 values (Ozaki splitting; up to 128 nodes per direction; error about K 2^-53 of
- * sum_j |D_ij| max_j |u_j| for K nodes with five accumulators; derivatives along a
- * Chebyshev direction of 33-64 nodes take a sixth, exact one, since the composed second
- * derivatives would carry that error past 1e-11 of the right-hand side, and above 64
+ * FP64 values (Ozaki splitting; up to 128 nodes per direction; each digit-order sum in an
+ * exact accumulator of its own, error about 1e-15 of sum_j |D_ij| max_j |u_j|; above 64
  * Chebyshev nodes the FP64 units take the derivatives), 1 on the FP64 units.  coupling: 0 (default) one
  * unsplit right-hand side over all 32 variables per Runge-Kutta stage; 1 the paper's
  * coupled loop ("Coupled Main Loop"): per step the fluid is advanced by the selected
@@ -322,14 +320,14 @@ int grmhd_xcts_init(grmhd_ctx* ctx, const double* rho, const double* p, const do
 
 /* Autotuner of the FP64 digit-slice contractions (a service of the library, outside the
  * paper).  The tensor-core contraction of a class (direction dir 0 r / 1 theta / 2 phi,
- * nodes n along it, accumulators nacc: 6 for derivatives, 5 for the filter) runs either with
- * one TMEM accumulator set (two CTAs per SM up to 6 x 32 columns) or with two (one CTA per
- * SM; the MMAs of the next 128-line tile run while the previous tile's results are
- * converted and stored).  A process-wide table keeps the choice per class: 0 = not tuned
+ * nodes n along it, kind 0 derivative / 1 filter) runs either with one TMEM accumulator
+ * set (two CTAs per SM up to 32 nodes: 7 x 32 columns) or with two (one CTA per SM; the
+ * MMAs of the next 128-line tile run while the previous tile's results are converted and
+ * stored).  A process-wide table keeps the choice per class: 0 = not tuned
  * (one set), 1 or 2 sets.  At the first context or batch of a process the library reads
  * the table a previous run stored, from the file the environment variable
  * GRMHD_TUNING_FILE names or else fx_tuning.txt next to the library (lines
- * "dir n nacc sets"; python -m paper_2508_18221_gb300.autotune writes it).
+ * "dir n kind sets"; python -m paper_2508_18221_gb300.autotune writes it).
  * grmhd_tune_contractions times both choices for every class the context uses (nfields
  * fields of its own state per launch, reps launches each, CUDA events on its stream), keeps
  * the faster in the table (two sets only when they are at least 2 % faster: the
@@ -341,8 +339,8 @@ int grmhd_xcts_init(grmhd_ctx* ctx, const double* rho, const double* p, const do
  * grmhd_tune_set sets one entry (GRMHD_EINVAL outside the ranges above); grmhd_tune_get
  * returns it (or GRMHD_EINVAL). */
 int grmhd_tune_contractions(grmhd_ctx* ctx, int nfields, int reps, double* ms_out, int* choice_out);
-int grmhd_tune_set(int dir, int n, int nacc, int sets);
-int grmhd_tune_get(int dir, int n, int nacc);
+int grmhd_tune_set(int dir, int n, int kind, int sets);
+int grmhd_tune_get(int dir, int n, int kind);
 
 /* Test hook: apply the first derivative along direction dir (0 r, 1 theta, 2 phi) to
  * `nfields` canonical fields (nfields * num_points doubles) with the library's

@@ -1,5 +1,5 @@
 """Autotuner of the FP64 digit-slice contractions: for every (direction, nodes,
-accumulators) class of the given workloads it times the contraction with one and with two
+kind) class (kind: derivative or filter) of the given workloads it times the contraction with one and with two
 TMEM accumulator sets on a context of that shape (grmhd_tune_contractions) and writes the
 faster choice per class to fx_tuning.txt next to the library, which every later process
 reads at its first context.
@@ -55,8 +55,7 @@ def main(argv=None):
         res = ctx.tune_contractions(nfields=a.nfields, reps=a.reps)
         ns = (cfg.n_r, cfg.n_theta, cfg.n_phi)
         for (d, kind), (m1, m2, ch) in sorted(res.items()):
-            nacc = 6 if kind == "derivative" else 5
-            key = (d, ns[d], nacc)
+            key = (d, ns[d], 0 if kind == "derivative" else 1)
             table[key] = ch
             two = f"{m2:.4f} ms" if m2 >= 0 else "n/a"
             print(f"{name:28s} dir {d} n {ns[d]:3d} {kind:10s} one set {m1:.4f} ms, two sets {two} -> {ch}",
@@ -64,10 +63,10 @@ def main(argv=None):
         ctx.close()
     out = a.out or os.path.join(os.path.dirname(pkg.LIB_PATH), "fx_tuning.txt")
     with open(out, "w") as fh:
-        fh.write("# digit-slice contraction tuning: direction nodes accumulators sets "
+        fh.write("# digit-slice contraction tuning: direction nodes kind(0 derivative, 1 filter) sets "
                  "(python -m paper_2508_18221_gb300.autotune)\n")
-        for (d, n, nacc), ch in sorted(table.items()):
-            fh.write(f"{d} {n} {nacc} {ch}\n")
+        for (d, n, kind), ch in sorted(table.items()):
+            fh.write(f"{d} {n} {kind} {ch}\n")
     print(f"wrote {out} ({len(table)} classes)")
     assert lib is not None
 

@@ -326,10 +326,10 @@ static void load_tuning_file() {
     char line[256];
     while (fgets(line, sizeof(line), f)) {
         if (line[0] == '#') continue;
-        int dir, n, nacc, ts;
-        if (sscanf(line, "%d %d %d %d", &dir, &n, &nacc, &ts) == 4 && dir >= 0 && dir <= 2 && n >= 2 && n <= 128 &&
-            (nacc == 5 || nacc == 6) && ts >= 0 && ts <= 2)
-            fx_tune_set(dir, n, nacc, ts);
+        int dir, n, kind, ts;
+        if (sscanf(line, "%d %d %d %d", &dir, &n, &kind, &ts) == 4 && dir >= 0 && dir <= 2 && n >= 2 && n <= 128 &&
+            (kind == 0 || kind == 1) && ts >= 0 && ts <= 2)
+            fx_tune_set(dir, n, kind, ts);
     }
     fclose(f);
 }
@@ -869,9 +869,8 @@ static cudaError_t contract(grmhd_ctx* c, int dir, int filter, const DerivJob* j
     const int Ns[3] = {c->d.Nr, c->d.Nt, c->d.Np};
     const bool cheb_d = !filter && dir < 2;
     const uint8_t* fx = filter ? c->fx_f[dir] : ((cheb_d && Ns[dir] > 64 && !force_fx) ? nullptr : c->fx_d[dir]);
-    const int nacc = filter ? 5 : 6;
     if (fx) return launch_contract_fx(dir, c->d, jobs, njobs, fx, (dir == 0 && !filter) ? c->fx_estride : 0,
-                                      c->tc_err, c->stream, 0, nacc);
+                                      c->tc_err, c->stream, 0, filter ? 1 : 0);
     const double* split = filter ? c->Fs[dir] : c->Ds[dir];
     const double* rs = filter ? nullptr : c->r_scale;
     if (split) return launch_deriv_eo(dir, c->d, jobs, njobs, split, filter ? 1 : -1, rs, c->stream);
@@ -898,7 +897,7 @@ static cudaError_t theta_fourier(grmhd_ctx* c, int filter, int stage, int fold_o
             const uint8_t* fx = filter ? c->fx_ft[h] : c->fx_dt[h];
             const double* split = filter ? c->Fts[h] : c->Dts[h];
             const DerivJob* jb = c->jobs + c->job_fy[h] + i0;
-            if (fx) e = launch_contract_fx(1, c->dh, jb, n, fx, 0, c->tc_err, c->stream, 0, filter ? 5 : 6);
+            if (fx) e = launch_contract_fx(1, c->dh, jb, n, fx, 0, c->tc_err, c->stream, 0, filter ? 1 : 0);
             else if (split) e = launch_deriv_eo(1, c->dh, jb, n, split, filter ? 1 : -1, nullptr, c->stream);
             else e = launch_deriv(1, c->dh, jb, n, filter ? c->Ft2[h] : c->Dt2[h], nullptr, c->stream);
         }
@@ -1566,16 +1565,16 @@ extern "C" int grmhd_kernel_times(grmhd_ctx* c, int reps, double* ms_out, double
 // of the previous one).  Which is faster depends on the class (direction, nodes,
 // accumulators); the autotuner times both on the context's own buffers and records the
 // faster one in the process-wide table every later launch of that class reads.
-extern "C" int grmhd_tune_set(int dir, int n, int nacc, int tsets) {
-    if (dir < 0 || dir > 2 || n < 2 || n > 128 || (nacc != 5 && nacc != 6) || tsets < 0 || tsets > 2)
+extern "C" int grmhd_tune_set(int dir, int n, int kind, int tsets) {
+    if (dir < 0 || dir > 2 || n < 2 || n > 128 || (kind != 0 && kind != 1) || tsets < 0 || tsets > 2)
         return GRMHD_EINVAL;
-    fx_tune_set(dir, n, nacc, tsets);
+    fx_tune_set(dir, n, kind, tsets);
     return GRMHD_OK;
 }
 
-extern "C" int grmhd_tune_get(int dir, int n, int nacc) {
-    if (dir < 0 || dir > 2 || n < 2 || n > 128 || (nacc != 5 && nacc != 6)) return GRMHD_EINVAL;
-    return fx_tune_get(dir, n, nacc);
+extern "C" int grmhd_tune_get(int dir, int n, int kind) {
+    if (dir < 0 || dir > 2 || n < 2 || n > 128 || (kind != 0 && kind != 1)) return GRMHD_EINVAL;
+    return fx_tune_get(dir, n, kind);
 }
 
 extern "C" int grmhd_tune_contractions(grmhd_ctx* c, int nfields, int reps, double* ms_out, int* choice_out) {
@@ -1599,7 +1598,7 @@ extern "C" int grmhd_tune_contractions(grmhd_ctx* c, int nfields, int reps, doub
     int st = GRMHD_OK;
     for (int dir = 0; dir < 3 && st == GRMHD_OK; dir++)
         for (int kind = 0; kind < 2 && st == GRMHD_OK; kind++) {      // 0 derivative, 1 filter
-            const int nacc = kind == 0 ? 6 : 5, N = Ns[dir];
+            const int N = Ns[dir];
             const bool ftd = dir == 1 && c->ft;
             const uint8_t* img = ftd ? (kind == 0 ? c->fx_dt[0] : c->fx_ft[0]) : (kind == 0 ? c->fx_d[dir] : c->fx_f[dir]);
             // Chebyshev derivatives above 64 nodes run on the FP64 units
@@ -1610,13 +1609,13 @@ extern "C" int grmhd_tune_contractions(grmhd_ctx* c, int nfields, int reps, doub
             int best = 1;
             for (int ts = 1; ts <= 2; ts++) {
                 double ms = -1.0;
-                if (img && fx_supported(dir, N) && (ts == 1 || fx_two_sets_possible(dir, N, nacc))) {
+                if (img && fx_supported(dir, N) && (ts == 1 || fx_two_sets_possible(dir, N))) {
                     cudaError_t e = launch_contract_fx(dir, dd, c->jobs + c->job_dbg, nfields, img, estride, c->tc_err,
-                                                       c->stream, 0, nacc, ts);
+                                                       c->stream, 0, kind, ts);
                     cudaEventRecord(e0, c->stream);
                     for (int r = 0; r < reps && e == cudaSuccess; r++)
                         e = launch_contract_fx(dir, dd, c->jobs + c->job_dbg, nfields, img, estride, c->tc_err, c->stream,
-                                               0, nacc, ts);
+                                               0, kind, ts);
                     cudaEventRecord(e1, c->stream);
                     if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
                         st = set_err(c, GRMHD_ECUDA, "tuning launch: %s", cudaGetErrorString(e));
@@ -1631,7 +1630,7 @@ extern "C" int grmhd_tune_contractions(grmhd_ctx* c, int nfields, int reps, doub
                 if (ms_out) ms_out[(dir * 2 + kind) * 2 + (ts - 1)] = ms;
             }
             if (st) break;
-            if (img) fx_tune_set(dir, N, nacc, best);
+            if (img) fx_tune_set(dir, N, kind, best);
             if (choice_out) choice_out[dir * 2 + kind] = img ? best : 0;
         }
     cudaEventDestroy(e0);

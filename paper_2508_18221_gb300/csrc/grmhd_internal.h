@@ -109,18 +109,18 @@ void fx_geometry(int N, int* Np, int* Kp, int* KC);
 bool fx_supported(int dir, int N);   // 2..128 nodes (even in phi)
 cudaError_t fx_init();
 // stall = 1 (test of the wait limits only): the tiles are never staged, so every wait of the
-// kernel runs out (about 0.5 s), the CTAs leave and *err is set.  nacc: TMEM accumulators,
-// 5, or 6 for an exact accumulator of the digit-order sum 6 (every derivative; 5: filters)
-// tsets: TMEM accumulator sets (1, or 2: the next item's MMAs run while the epilogue drains
-// the previous one; one CTA per SM); 0 takes the tuning table's choice for the class
+// kernel runs out (about 0.5 s), the CTAs leave and *err is set.  kind: 0 derivative, 1
+// filter (the key of the tuning table; the arithmetic is the same).  tsets: TMEM accumulator
+// sets (1, or 2: the next item's MMAs run while the epilogue drains the previous one; one
+// CTA per SM); 0 takes the tuning table's choice for the class
 cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int njobs, const uint8_t* op_img,
-                               long long img_estride, int* err, cudaStream_t s, int stall = 0, int nacc = 5,
+                               long long img_estride, int* err, cudaStream_t s, int stall = 0, int kind = 0,
                                int tsets = 0);
 // tuning table of the digit-slice contraction (process-wide): accumulator sets per
-// (direction, nodes, accumulators); 0 when the class was not tuned
-void fx_tune_set(int dir, int N, int nacc, int tsets);
-int fx_tune_get(int dir, int N, int nacc);
-bool fx_two_sets_possible(int dir, int N, int nacc);
+// (direction, nodes, kind); 0 when the class was not tuned
+void fx_tune_set(int dir, int N, int kind, int tsets);
+int fx_tune_get(int dir, int N, int kind);
+bool fx_two_sets_possible(int dir, int N);
 cudaError_t launch_deriv(int dir, const Dims& d, const DerivJob* jobs_dev, int njobs,
                          const double* mat_dev, const double* r_scale_dev, cudaStream_t s);
 // reflection-split contraction (kernels_eo.cu): cudaErrorNotSupported when N has no

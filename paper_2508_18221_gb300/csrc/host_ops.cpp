@@ -243,7 +243,7 @@ std::vector<uint8_t> tc_operator_image(const std::vector<double>& D, int N, int 
 // significant first).  Slice l holds c_l 2^(-8 (l - 1)), exact in BF16.
 std::vector<uint8_t> fx_operator_image(const std::vector<double>& D, int N, double scale, int Np, int Kp,
                                        int KC) {
-    const int nch = Kp / KC, kcores = KC / 8;
+    const int nch = Kp / KC, kcores = KC / 8, Npp = Np > 64 ? 64 : Np;
     const size_t slice = (size_t)Np * KC * 2, chunk = 7 * slice;
     const size_t bytes = ((size_t)nch * chunk + (size_t)Np * 4 + 15) / 16 * 16;
     std::vector<uint8_t> img(bytes, 0);
@@ -265,15 +265,18 @@ std::vector<uint8_t> fx_operator_image(const std::vector<double>& D, int N, doub
             const long long Y = std::llround(std::ldexp(x, 1076 - F));
             const unsigned long long Z = (unsigned long long)(Y + 0x80808080808080LL);
             const int kc = k / KC, kk = k % KC;
-            const size_t off = (size_t)kc * chunk + ((size_t)((n >> 3) * kcores + (kk >> 3))) * 128 + (n & 7) * 16 +
-                               (kk & 7) * 2;
             for (int q = 1; q <= 7; q++) {
                 const int digit = (int)((Z >> (8 * (7 - q))) & 0xFF) - 128;
                 const float v = std::ldexp((float)digit, -8 * (q - 1));
                 uint32_t u;
                 std::memcpy(&u, &v, 4);
                 const uint16_t b = (uint16_t)(u >> 16);
-                std::memcpy(&img[off + (size_t)(q - 1) * slice], &b, 2);
+                // row of the chunk's tall B matrix: pass p (Npp = min(Np, 64) output rows),
+                // then slice, then the row within the pass
+                const int row = ((n / Npp) * 7 + (q - 1)) * Npp + n % Npp;
+                const size_t off = (size_t)kc * chunk + ((size_t)((row >> 3) * kcores + (kk >> 3))) * 128 +
+                                   (row & 7) * 16 + (kk & 7) * 2;
+                std::memcpy(&img[off], &b, 2);
             }
         }
     }

@@ -7,22 +7,21 @@
 //     balanced base-256 digits d_1..d_7 in [-128, 127] (most significant first);
 //   * a digit fits a BF16 exactly and a product of two digits (|.| <= 2^14) fits an FP32
 //     exactly, so the tensor core forms sum_j c_l(i,j) d_q(j) without rounding as long as
-//     the running sum stays below 2^24 (true for K <= 64 and the groups below);
-//   * the 28 digit pairs with q + l <= 8 are kept; those with q + l = 2, 3, 4, 5
-//     accumulate in four separate TMEM accumulators (exact), those with q + l = 6..8 in
-//     a fifth.  The tensor core adds terms of different magnitude with a truncating
-//     alignment, so only the fifth accumulator rounds, about 2^-23 of its own size (2^-40
-//     below the leading term) per addition (measured: folding from q + l = 5 on instead
-//     costs 1e-12 of the bound below).  Over the ~1.1 K additions of a K-long line that
-//     leaves about K 2^-53 of the bound; the NA = 6 instance gives q + l = 6 an exact
-//     accumulator too (7e-16 of the bound at K = 64 and 128), for derivatives that are
-//     composed into second derivatives on Chebyshev nodes;
-//   * the epilogue adds the five accumulators as a 64-bit integer and builds the IEEE
-//     double with integer instructions (no FP64 arithmetic: GB300 runs FP64 at ~2 fused
-//     operations per SM clock, integer and FP32 work at 64-128).
-// Error: below 2e-14 of sum_j |D_ij| max_j |u_j| with five accumulators (tested), about the
-// worst-case bound of an FP64 dot product of these lengths; about 1e-15 with six.  A line holding Inf or NaN yields NaN
-// outputs; values below 2^-1022 (subnormals) enter as zero.
+//     the running sum stays below 2^24 (true for K <= 128 and the sums below);
+//   * the 28 digit pairs with q + l <= 8 are kept, each digit-order sum s = q + l = 2..8 in
+//     a TMEM accumulator of its own, so every accumulator is exact (|sum| < 2^24 units of
+//     its order for K <= 128: at most 7 pairs of products below 2^14);
+//   * the operator's seven slices of one K chunk form one tall matrix (slice after slice),
+//     so the products of line slice q with operator slices 1 .. 8 - q are one MMA whose
+//     N = (8 - q) Npp output columns start at accumulator q + 1: seven MMAs per chunk (a
+//     few more where N would pass 256) instead of one per pair;
+//   * the epilogue adds the seven accumulators as a 64-bit integer (the s = 8 term rounded
+//     to the s = 7 unit) and builds the IEEE double with one integer-to-double conversion
+//     and an exponent add (GB300 runs FP64 at ~2 fused operations per SM clock, integer
+//     and FP32 work at 64-128).
+// Error: about 1e-15 of sum_j |D_ij| max_j |u_j| (the dropped pairs q + l > 8 and the final
+// roundings), below the worst-case bound of an FP64 dot product of these lengths.  A line
+// holding Inf or NaN yields NaN outputs; values below 2^-1022 (subnormals) enter as zero.
 //
 // Work item: 128 lines (tile) of one field (job) x K <= 128, one pass of at most 64 output
 // columns, processed in K chunks of 16.  The kernel is persistent and warp-specialised
@@ -45,7 +44,7 @@ namespace gk {
 namespace {
 
 constexpr int NDIG = 7;                                      // base-256 digits per operand
-constexpr int NACC = 5;                                      // TMEM accumulators (6: see combine6)
+constexpr int NACC = 7;                                      // TMEM accumulators: s = 2..8
 constexpr unsigned long long DIG_BIAS = 0x80808080808080ull;  // 128 in each digit
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -73,17 +72,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db
 
 // Digit word of one value: Z = X + bias with X = round(2 m 2^(e - EL)) the value as a
 // signed fixed-point integer relative to the line exponent EL (|X| <= 2^54; the value is
-// X 2^(EL - 1076)); byte b of Z minus 128 is the balanced digit of weight 256^b.
+// X 2^(EL - 1076)); byte b of Z minus 128 is the balanced digit of weight 256^b.  Branch-
+// free (the values of a thread overlap): round(2 m / 2^sh) = ((4 m >> sh) + 1) >> 1 for
+// sh = EL - e in 0 .. 63 (4 m < 2^56, so every sh >= 56 gives 0), zero for e = 0.
 __device__ __forceinline__ unsigned long long digit_word(double u, int EL) {
     const long long bits = __double_as_longlong(u);
     const int e = (int)((bits >> 52) & 0x7FF);
-    const unsigned long long m2 = (((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 1;
-    const int sh = EL - e;  // >= 0
-    unsigned long long mag = 0;
-    if (e != 0) {
-        if (sh == 0) mag = m2;
-        else if (sh < 60) mag = (m2 + (1ull << (sh - 1))) >> sh;
-    }
+    const unsigned long long m4 = (((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 2;
+    const int sh = min(EL - e, 63);
+    const unsigned long long mag = e != 0 ? ((m4 >> sh) + 1) >> 1 : 0ull;
     const long long x = bits < 0 ? -(long long)mag : (long long)mag;
     return (unsigned long long)(x + (long long)DIG_BIAS);
 }
@@ -103,14 +100,16 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 // R * 2^X: one correctly rounded integer-to-double conversion, then the power of two is
-// added to the exponent field (ldexp_int below when the result leaves the normal range)
+// added to the exponent field; *ok false when the result leaves the normal range or R = 0
+// (the caller then takes ldexp_int below).  Branch-free, so that the eight outputs of a
+// column block overlap their conversions.
 __device__ __forceinline__ double ldexp_int(long long R, int X);
-__device__ __forceinline__ double scale_int(long long R, int X) {
+__device__ __forceinline__ double scale_int_fast(long long R, int X, bool* ok) {
     const double v = __ll2double_rn(R);
-    const long long bits = __double_as_longlong(v);
-    const int be = (int)((bits >> 52) & 0x7FF) + X;
-    if (v != 0.0 && be >= 1 && be <= 2046) return __longlong_as_double(bits + ((long long)X << 52));
-    return v == 0.0 ? 0.0 : ldexp_int(R, X);
+    const int lo = __double2loint(v), hi = __double2hiint(v);
+    const int e = (hi >> 20) & 0x7FF;
+    *ok = e != 0 && (unsigned)(e + X - 1) < 2046u;
+    return __hiloint2double(hi + (X << 20), lo);
 }
 
 // R * 2^X as an IEEE double built with integer instructions (|R| < 2^62; ties away)
@@ -128,47 +127,44 @@ __device__ __forceinline__ double ldexp_int(long long R, int X) {
     return __longlong_as_double((long long)(sgn | ((((unsigned long long)(be - 1)) << 52) + mant)));
 }
 
-// T = g2 + g3 + g4 + g5 + gf as the integer R = round(T 2^40): g2 is an integer, g3 a
-// multiple of 2^-8, g4 of 2^-16, g5 of 2^-24 (all exact: |g_s 2^(8 (s-2))| <= 2^22 for
-// K <= 64, < 2^24 for K <= 128), gf carries the rounded low-order terms (|gf| < 2^-8).
-__device__ __forceinline__ long long combine(float g2, float g3, float g4, float g5, float gf, bool wide) {
-    const float MAG = 12582912.f;  // 1.5 * 2^23: float -> nearest integer for |x| <= 2^22
-    const int n2 = __float_as_int(g2 + MAG) - 0x4B400000;
-    const int n3 = __float_as_int(fmaf(g3, 256.f, MAG)) - 0x4B400000;
-    // K > 64: g4, g5 scaled reach 2^23 (exact integers below 2^24): plain conversions
-    const int n4 = wide ? __float2int_rn(g4 * 65536.f) : __float_as_int(fmaf(g4, 65536.f, MAG)) - 0x4B400000;
-    const int n5 = wide ? __float2int_rn(g5 * 16777216.f) : __float_as_int(fmaf(g5, 16777216.f, MAG)) - 0x4B400000;
-    const float fh = fmaf(gf, 16777216.f, MAG);
-    const int nfh = __float_as_int(fh) - 0x4B400000;
-    const float flo = fmaf(gf, 16777216.f, -(fh - MAG));  // exact remainder in [-1/2, 1/2]
-    const int nlo = __float_as_int(fmaf(flo, 65536.f, MAG)) - 0x4B400000;
-    const long long a = ((long long)n2 << 24) + ((long long)n3 << 16) + ((long long)n4 << 8) + (long long)(n5 + nfh);
-    return (a << 16) + (long long)nlo;
-}
-
-// Six accumulators (Chebyshev derivatives above 32 nodes): the digit-order sum q + l = 6
-// gets an exact accumulator of its own and only q + l = 7, 8 are folded.  With five, the
-// folded accumulator holds the q + l = 6 terms, about 2^-32 of the leading ones, and its
-// FP32 additions (truncating alignment, ~1.1 K of them) leave an error growing as K:
-// 3.5e-15 / 7.5e-15 / 1.4e-14 of the bound at 24 / 64 / 128 nodes, which the composed
-// second derivatives amplify past 1e-11 of the right-hand side above 32 Chebyshev nodes.
-// T = g2 + .. + g6 + gf as R = round(T 2^40): g_s an exact multiple of 2^(-8 (s-2)) with
-// |g_s 2^(8 (s-2))| < 2^24 (K <= 128), |gf| < 2^-15 (its scaled head < 2^18 rounds by
-// the magic-number add, the exact remainder gives the last 8 bits).
-__device__ __forceinline__ long long combine6(float g2, float g3, float g4, float g5, float g6, float gf) {
-    const int n2 = __float2int_rn(g2);
-    const int n3 = __float2int_rn(g3 * 256.f);
-    const int n4 = __float2int_rn(g4 * 65536.f);
-    const int n5 = __float2int_rn(g5 * 16777216.f);
-    const int n6 = __float2int_rn(g6 * 4294967296.f);
-    const float MAG = 12582912.f;
-    const float fh = fmaf(gf, 4294967296.f, MAG);
-    const int nfh = __float_as_int(fh) - 0x4B400000;
-    const float flo = fmaf(gf, 4294967296.f, -(fh - MAG));  // exact remainder in [-1/2, 1/2]
-    const int nlo = __float2int_rn(flo * 256.f);
-    const long long a = ((long long)n2 << 32) + ((long long)n3 << 24) + ((long long)n4 << 16) +
-                        ((long long)n5 << 8) + (long long)(n6 + nfh);
-    return (a << 8) + (long long)nlo;
+// T = g_2 + ... + g_8 as the integer R = round(T 2^40), g_s = acc[s - 2] an exact multiple
+// of 2^(-8 (s - 2)): n_s = g_s 2^(8 (s - 2)) is an integer with |n_s| <= (s - 1) K 2^14, below
+// 2^24 for K <= 128 and below 2^22 for K <= 32.
+// Each n_s is made non-negative by an offset, t_s = n_s + o_s: below 2^22 t_s is read off
+// the bits of g_s 2^(8 (s - 2)) + 1.5 * 2^23 (the low 23 bits hold n_s + 2^22; exact, as
+// the value is an integer), above it comes from a float-to-integer conversion (exact too).
+// The t_s are summed at their byte offsets with 32 x 32 -> 64-bit multiply-adds (an
+// unsigned sum below 2^63), the s = 8 term rounded to the unit of s = 7 (half up), and the
+// offsets' total is subtracted once.
+template <bool WIDE>
+__device__ __forceinline__ long long combine7(const uint32_t* acc) {
+    const float MAG = 12582912.f;  // 1.5 * 2^23
+    uint32_t t[NACC];
+    unsigned long long off;
+    if (!WIDE) {
+#pragma unroll
+        for (int s = 0; s < NACC; s++) {
+            const float sc = __int_as_float((127 + 8 * s) << 23);  // 2^(8 s)
+            t[s] = (uint32_t)__float_as_int(fmaf(__uint_as_float(acc[s]), sc, MAG)) & 0x7FFFFFu;
+        }
+        // o_s = 2^22 for every s
+        off = (1ull << 62) + (1ull << 54) + (1ull << 46) + (1ull << 38) + (1ull << 30) + (1ull << 22) + (1ull << 14);
+    } else {
+        // |n_s| <= (s - 1) K 2^14 <= (s - 1) 2^21: o_2 = 2^21, the others o_s = 2^24
+#pragma unroll
+        for (int s = 0; s < NACC; s++) {
+            const float sc = __int_as_float((127 + 8 * s) << 23);
+            t[s] = (uint32_t)(__float2int_rn(__uint_as_float(acc[s]) * sc) + (s == 0 ? (1 << 21) : (1 << 24)));
+        }
+        off = (1ull << 61) + (1ull << 56) + (1ull << 48) + (1ull << 40) + (1ull << 32) + (1ull << 24) + (1ull << 16);
+    }
+    // t_2 2^40 + t_3 2^32 + t_4 2^24 + t_5 2^16 + t_6 2^8 + t_7 + round(t_8 / 256)
+    unsigned long long a = (unsigned long long)t[2] * (1ull << 24) + t[5];
+    a += (unsigned long long)t[3] * (1ull << 16);
+    a += (unsigned long long)t[4] * (1ull << 8);
+    a += (unsigned long long)((t[0] << 8) + t[1]) << 32;
+    a += (t[6] + 128u) >> 8;
+    return (long long)(a - off);
 }
 
 }  // namespace
@@ -207,7 +203,7 @@ __device__ __forceinline__ void stg_copy(const Dims& d, const FxTile& tl, int N,
         *bytes = tl.nlines * 8;
     } else if (DIR == 1) {
         const int seg = c / N, k = c - seg * N;
-        const long long eil = tl.t0 / d.Np + seg;
+        const long long eil = (long long)((uint32_t)tl.t0 / (uint32_t)d.Np) + seg;
         const long long lo = max(tl.t0, eil * d.Np), hi = min(tl.t0 + tl.nlines, (eil + 1) * d.Np);
         *src_off = eil * d.NtNp + (long long)k * d.Np + (lo - eil * d.Np);
         *dst_off = k * 128 + (int)(lo - tl.t0);
@@ -232,6 +228,9 @@ struct FxParams {
     int npass;               // Np / Npp
     int b_all;               // 1: the operator digits of all K chunks stay in shared memory
     long long ntiles;        // 128-line tiles of one field
+    uint32_t per_job;        // items of one field: ntiles x npass
+    uint32_t tpe;            // radial: 128-line tiles per element
+    uint32_t nlf;            // lines of one field (theta, phi)
     uint32_t stg_bytes;
     int* err;
     int stall;               // test of the wait limits: the staging warp issues no copies
@@ -239,18 +238,19 @@ struct FxParams {
                              // item k + 1 run while the epilogue drains item k; needs b_all)
 };
 
+// tile b of a field (32-bit arithmetic: a field holds fewer than 2^31 points, since its 32
+// or 33 fields fit the device memory)
 template <int DIR>
-__device__ __forceinline__ void fx_tile(const Dims& d, long long b, int N, FxTile* tl) {
+__device__ __forceinline__ void fx_tile(const FxParams& fp, const Dims& d, uint32_t b, FxTile* tl) {
     if (DIR == 0) {
-        const long long tpe = (d.NtNp + 127) / 128;
-        tl->e = (int)(b / tpe);
-        tl->t0 = (b - (long long)tl->e * tpe) * 128;
-        tl->nlines = (int)min(128LL, d.NtNp - tl->t0);
+        const uint32_t e = b / fp.tpe, t0 = (b - e * fp.tpe) * 128u;
+        tl->e = (int)e;
+        tl->t0 = t0;
+        tl->nlines = (int)min(128u, (uint32_t)d.NtNp - t0);
     } else {
-        const long long nl = DIR == 1 ? (long long)d.E * d.Nr * d.Np : d.P / N;
         tl->e = 0;
-        tl->t0 = b * 128;
-        tl->nlines = (int)min(128LL, nl - tl->t0);
+        tl->t0 = b * 128u;
+        tl->nlines = (int)min(128u, fp.nlf - b * 128u);
     }
 }
 
@@ -261,12 +261,8 @@ __device__ __forceinline__ void fx_stage(const Dims& d, const FxTile& tl, int N,
                                          uint64_t* bar, int lane) {
     const int nc = stg_ncopies<DIR>(d, tl, N);
     if (lane == 0) {
-        uint32_t total = 0;
-        for (int c = 0; c < nc; c++) {
-            long long so; int dof, by;
-            stg_copy<DIR>(d, tl, N, c, &so, &dof, &by);
-            total += (uint32_t)by;
-        }
+        // the copies cover the tile's lines x N values exactly once
+        const uint32_t total = (uint32_t)tl.nlines * (uint32_t)N * 8u;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(total)
                      : "memory");
     }
@@ -287,12 +283,13 @@ __device__ __forceinline__ void fx_stage(const Dims& d, const FxTile& tl, int N,
 //              exponents, then the seven digit slices of each 16-wide K chunk into a
 //              two-stage ring of A buffers;
 //   warps 4-7  epilogue: thread m reads TMEM lane m (warp w serves lane quadrant w & 3),
-//              combines the five accumulators and stores the FP64 results, 8 columns
+//              combines the seven accumulators and stores the FP64 results, 8 columns
 //              at a time; TMEM goes back to the MMA warp once the last block is in
 //              registers, before its arithmetic (the epilogue's latency, not its
 //              instruction count, sets the rate at which items pass through TMEM);
 //   warp 8     stages the FP64 tiles in shared memory (bulk copies);
-//   warp 9     one thread loads the operator digits and issues the MMAs.
+//   warp 9     one thread loads the operator digits and issues the MMAs (per K chunk one
+//              per line slice q, over the stacked operator slices 1 .. 8 - q).
 // A work item is (field, 128-line tile, column pass); the CTA walks items blockIdx.x,
 // blockIdx.x + gridDim.x, ...  Every role follows the same item sequence; they hand over
 // through mbarriers (full / empty pairs), so conversion of one item overlaps the MMAs
@@ -303,7 +300,8 @@ __device__ __forceinline__ void fx_stage(const Dims& d, const FxTile& tl, int N,
 // Shared memory (bytes): [staging x nstg | A ring 2 x (7 x 128 x 16 x 2) |
 //   B digits of all chunks (nchunks x 7 x Np x 16 x 2) | sEL 2 x 128 x 4 | sF 2 x 128 x 4 |
 //   barriers | tmem address | abort flag]
-constexpr int FXW_THREADS = 320;
+// W = converter warps = epilogue warps: 4 at two CTAs per SM, 8 at one
+__host__ __device__ constexpr int fx_threads(int W) { return (2 * W + 2) * 32; }
 constexpr int NA_RING = 2;
 
 // exponents and their barriers alternate between two sets by item parity, so that the
@@ -356,25 +354,39 @@ __device__ __forceinline__ void barrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// warp-wide bounded wait: every lane polls; the warp goes on only if every lane saw the phase
+__device__ __forceinline__ bool wwait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    return __all_sync(0xffffffffu, bwait(bar, parity, abort_flag) ? 1 : 0) != 0;
+}
+
+// one lane of the (converged) warp
+__device__ __forceinline__ bool elect_one() {
+    uint32_t p;
+    asm volatile("{\n.reg .pred e;\nelect.sync _|e, 0xffffffff;\nselp.u32 %0, 1, 0, e;\n}\n" : "=r"(p));
+    return p != 0;
+}
+
+// work item it -> field (job), tile and column pass (npass is 1 or 2); items < 2^31
 template <int DIR>
 __device__ __forceinline__ void fx_item(const FxParams& fp, const Dims& d, long long it, FxTile* tl, int* pass,
                                         int* job) {
-    const long long per_job = fp.ntiles * fp.npass;
-    *job = (int)(it / per_job);
-    const long long r = it - (long long)(*job) * per_job;
-    *pass = (int)(r % fp.npass);
-    fx_tile<DIR>(d, r / fp.npass, fp.N, tl);
+    const uint32_t u = (uint32_t)it, j = u / fp.per_job, r = u - j * fp.per_job;
+    *job = (int)j;
+    *pass = fp.npass == 2 ? (int)(r & 1u) : 0;
+    fx_tile<DIR>(fp, d, fp.npass == 2 ? r >> 1 : r, tl);
 }
 
-template <int DIR, int NA>
-__global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams fp) {
+template <int DIR, int W>
+__global__ void __launch_bounds__(fx_threads(W), W == 4 ? 2 : 1) k_contract_fx(Dims d, FxParams fp) {
+    constexpr int NA = NACC;
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = fp.N, Np = fp.Np, Npp = fp.Npp;
     constexpr int KC = 16, kcores = 2;
     const uint32_t a_bytes = 128u * KC * 2;            // one digit slice of one chunk
     const uint32_t a_stage = NDIG * a_bytes;
-    const uint32_t b_bytes = (uint32_t)Np * KC * 2;
+    const uint32_t b_bytes = (uint32_t)Np * KC * 2;        // one slice of one chunk, all passes
+    const uint32_t bs_bytes = (uint32_t)Npp * KC * 2;      // one slice of one chunk and pass
     const uint32_t chunk_bytes = NDIG * b_bytes;
     const int nchunks = fp.Kp / KC;
     const uint32_t op_bytes = (uint32_t)nchunks * chunk_bytes;
@@ -391,7 +403,7 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
     if (tid == 0) {
         for (int b = 0; b < 2; b++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars->stg_full[b])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars->stg_empty[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars->stg_empty[b])), "r"(W));
         }
         for (int a = 0; a < NA_RING; a++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars->a_full[a])));
@@ -399,7 +411,7 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
         }
         for (int t = 0; t < 2; t++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars->acc_full[t])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars->acc_empty[t])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars->acc_empty[t])), "r"(W));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars->el_ready[t])));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars->b_full)));
@@ -416,7 +428,7 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 8) {
+    if (warp == 2 * W) {
         // ---------------------------------------------------------------- staging
         int k = 0;
         int last_k[2] = {-1, -1};          // last item staged into each buffer
@@ -441,29 +453,33 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
         if (*abort_flag && lane == 0)
             for (int b = 0; b < fp.nstg; b++)
                 if (last_k[b] >= 0) bwait_for(&bars->stg_full[b], (uint32_t)((last_k[b] / fp.nstg) & 1), 1000000ull);
-    } else if (warp == 9) {
+    } else if (warp == 2 * W + 1) {
         // ---------------------------------------------------------------- MMA issue
-        if (lane == 0) {
-            const uint32_t id = instr_desc_bf16(128, Npp);
-            const uint32_t lbo = 128u, sbo = (uint32_t)kcores * 128u;
-            int k = 0, cur_e = -1;
-            uint32_t n_b = 0;
-            int last_cg = -1, last_item = -1;   // last chunk / item whose MMAs were committed
-            for (long long it = blockIdx.x; it < nitems; it += gridDim.x, k++) {
-                FxTile tl;
-                int pass, job;
-                fx_item<DIR>(fp, d, it, &tl, &pass, &job);
-                // the epilogue has drained the accumulator set this item writes (item k - tsets)
-                const int ts = fp.tsets;
-                if (k >= ts && !bwait(&bars->acc_empty[(k - ts) & 1], (uint32_t)(((k - ts) >> 1) & 1), abort_flag))
-                    break;
-                const uint8_t* op = fp.img + (DIR == 0 ? tl.e * fp.img_estride : 0);
-                // with two sets the previous item's MMAs may still read the operator: they
-                // finish (its commit) before a new element's operator overwrites it
-                if (ts > 1 && k > 0 && fp.b_all && cur_e != tl.e &&
-                    !bwait(&bars->acc_full[(k - 1) % ts], (uint32_t)(((k - 1) / ts) & 1), abort_flag))
-                    break;
-                if (fp.b_all && cur_e != tl.e) {  // radial: per-element operator; theta, phi: once
+        // The whole warp walks the loop with warp-uniform values (descriptors, columns,
+        // counters); one elected lane issues the copies, MMAs and commits.  (Issued from
+        // a single-lane branch, each MMA cost ~150 cycles of issue.)
+        const bool leader = elect_one();
+        const int gmax = 256 / Npp;  // operator slices per MMA (N <= 256)
+        const uint32_t lbo = 128u, sbo = (uint32_t)kcores * 128u;
+        int k = 0, cur_e = -1;
+        uint32_t n_b = 0;
+        int last_cg = -1, last_item = -1;   // last chunk / item whose MMAs were committed
+        for (long long it = blockIdx.x; it < nitems; it += gridDim.x, k++) {
+            FxTile tl;
+            int pass, job;
+            fx_item<DIR>(fp, d, it, &tl, &pass, &job);
+            // the epilogue has drained the accumulator set this item writes (item k - tsets)
+            const int ts = fp.tsets;
+            if (k >= ts && !wwait(&bars->acc_empty[(k - ts) & 1], (uint32_t)(((k - ts) >> 1) & 1), abort_flag))
+                break;
+            const uint8_t* op = fp.img + (DIR == 0 ? tl.e * fp.img_estride : 0);
+            // with two sets the previous item's MMAs may still read the operator: they
+            // finish (its commit) before a new element's operator overwrites it
+            if (ts > 1 && k > 0 && fp.b_all && cur_e != tl.e &&
+                !wwait(&bars->acc_full[(k - 1) % ts], (uint32_t)(((k - 1) / ts) & 1), abort_flag))
+                break;
+            if (fp.b_all && cur_e != tl.e) {  // radial: per-element operator; theta, phi: once
+                if (leader) {
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
                                      smem_u32(&bars->b_full)),
                                  "r"(op_bytes) : "memory");
@@ -472,24 +488,28 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
                             smem_u32(sB)),
                         "l"(op), "r"(op_bytes), "r"(smem_u32(&bars->b_full))
                         : "memory");
-                    n_b++;
-                    cur_e = tl.e;
                 }
-                if (fp.b_all && !bwait(&bars->b_full, (n_b - 1) & 1, abort_flag)) break;
-                const uint32_t brow = (uint32_t)(pass * Npp / 8) * sbo;
-                bool stop = false;
-                for (int kc = 0; kc < nchunks; kc++) {
-                    const int cg = k * nchunks + kc, a = cg % NA_RING;
-                    if (!fp.b_all) {
-                        // one chunk of the operator at a time: the previous chunk's MMAs (the
-                        // previous item's are done: acc_empty) have finished reading it
-                        if (kc > 0) {
-                            const int cp = cg - 1;
-                            if (!bwait(&bars->a_empty[cp % NA_RING], (uint32_t)((cp / NA_RING) & 1), abort_flag)) {
-                                stop = true;
-                                break;
-                            }
+                __syncwarp();
+                n_b++;
+                cur_e = tl.e;
+            }
+            if (fp.b_all && !wwait(&bars->b_full, (n_b - 1) & 1, abort_flag)) break;
+            const uint32_t bpass = (uint32_t)pass * NDIG * bs_bytes;  // this pass's slices
+            const uint32_t set_col = (uint32_t)((k % ts) * NA * Npp);
+            bool stop = false;
+            for (int kc = 0; kc < nchunks; kc++) {
+                const int cg = k * nchunks + kc, a = cg % NA_RING;
+                if (!fp.b_all) {
+                    // one chunk of the operator at a time: the previous chunk's MMAs (the
+                    // previous item's are done: acc_empty) have finished reading it
+                    if (kc > 0) {
+                        const int cp = cg - 1;
+                        if (!wwait(&bars->a_empty[cp % NA_RING], (uint32_t)((cp / NA_RING) & 1), abort_flag)) {
+                            stop = true;
+                            break;
                         }
+                    }
+                    if (leader) {
                         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
                                          smem_u32(&bars->b_full)),
                                      "r"(chunk_bytes) : "memory");
@@ -498,45 +518,54 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
                                 smem_u32(sB)),
                             "l"(op + (size_t)kc * chunk_bytes), "r"(chunk_bytes), "r"(smem_u32(&bars->b_full))
                             : "memory");
-                        n_b++;
-                        if (!bwait(&bars->b_full, (n_b - 1) & 1, abort_flag)) { stop = true; break; }
                     }
-                    if (!bwait(&bars->a_full[a], (uint32_t)((cg / NA_RING) & 1), abort_flag)) { stop = true; break; }
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t a0 = smem_u32(sA + a * a_stage);
-                    const uint32_t b0 = smem_u32(sB + (fp.b_all ? kc * chunk_bytes : 0)) + brow;
-                    for (int sd = NDIG - 1; sd >= 0; sd--) {
-                        const int g = sd < NA - 1 ? sd : NA - 1;
-                        for (int q = 0; q <= sd; q++) {
-                            const int l = sd - q;
-                            const bool first = kc == 0 && q == 0 && (sd < NA - 1 || sd == NDIG - 1);
-                            mma_bf16(tmem + (uint32_t)((k % ts) * NA * Npp + g * Npp), smem_desc(a0 + q * a_bytes, lbo, sbo),
-                                     smem_desc(b0 + l * b_bytes, lbo, sbo), id, first ? 0u : 1u);
+                    __syncwarp();
+                    n_b++;
+                    if (!wwait(&bars->b_full, (n_b - 1) & 1, abort_flag)) { stop = true; break; }
+                }
+                if (!wwait(&bars->a_full[a], (uint32_t)((cg / NA_RING) & 1), abort_flag)) { stop = true; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t a0 = smem_u32(sA + a * a_stage);
+                const uint32_t b0 = smem_u32(sB + (fp.b_all ? kc * chunk_bytes : 0)) + bpass;
+                // line slice q times operator slices l0 .. l0 + c - 1 (consecutive rows of the
+                // chunk's tall operator matrix) into accumulators q + l0 .. q + l0 + c - 1;
+                // q = 0 of the first chunk writes every accumulator first
+                if (leader) {
+                    for (int q = 0; q < NDIG; q++)
+                        for (int l0 = 0; l0 < NDIG - q; l0 += gmax) {
+                            const int c = min(gmax, NDIG - q - l0);
+                            mma_bf16(tmem + set_col + (uint32_t)((q + l0) * Npp), smem_desc(a0 + q * a_bytes, lbo, sbo),
+                                     smem_desc(b0 + l0 * bs_bytes, lbo, sbo), instr_desc_bf16(128, c * Npp),
+                                     (kc == 0 && q == 0) ? 0u : 1u);
                         }
-                    }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         smem_u32(&bars->a_empty[a])));
-                    last_cg = cg;
                 }
-                if (stop) break;
+                __syncwarp();
+                last_cg = cg;
+            }
+            if (stop) break;
+            if (leader)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_u32(&bars->acc_full[k % ts])));
-                last_item = k;
-            }
-            // after an abort, the MMAs already committed finish writing TMEM, and an operator
-            // copy already issued lands, before TMEM and shared memory are given up
-            if (*abort_flag) {
-                if (last_cg >= 0)
-                    bwait_for(&bars->a_empty[last_cg % NA_RING], (uint32_t)((last_cg / NA_RING) & 1), 1000000ull);
-                if (last_item >= 0)
-                    bwait_for(&bars->acc_full[last_item % fp.tsets], (uint32_t)((last_item / fp.tsets) & 1), 1000000ull);
-                if (n_b > 0) bwait_for(&bars->b_full, (n_b - 1) & 1, 1000000ull);
-            }
+            __syncwarp();
+            last_item = k;
+        }
+        // after an abort, the MMAs already committed finish writing TMEM, and an operator
+        // copy already issued lands, before TMEM and shared memory are given up
+        if (*abort_flag && leader) {
+            if (last_cg >= 0)
+                bwait_for(&bars->a_empty[last_cg % NA_RING], (uint32_t)((last_cg / NA_RING) & 1), 1000000ull);
+            if (last_item >= 0)
+                bwait_for(&bars->acc_full[last_item % fp.tsets], (uint32_t)((last_item / fp.tsets) & 1), 1000000ull);
+            if (n_b > 0) bwait_for(&bars->b_full, (n_b - 1) & 1, 1000000ull);
         }
         __syncwarp();
-    } else if (warp < 4) {
+    } else if (warp < W) {
         // ---------------------------------------------------------------- conversion
-        const int m = tid;
+        // thread m = line m; with W = 8 two groups of 4 warps share the K chunks by A ring
+        // slot (group g writes the chunks that land in slot g); group 0 publishes exponents
+        const int m = tid & 127, grp = tid >> 7;
         int k = 0;
         for (long long it = blockIdx.x; it < nitems; it += gridDim.x, k++) {
             FxTile tl;
@@ -550,19 +579,22 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
             if (valid)
                 for (int j = 0; j < N; j++)
                     EL = max(EL, (int)((__double_as_longlong(stg_at<DIR>(stg, m, j, N)) >> 52) & 0x7FF));
-            // the epilogue of item k - 2 has read this set of sEL and sF
-            const int t = k & 1;
-            if (k > 1 && !bwait(&bars->acc_empty[t], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
-            sEL[t * 128 + m] = EL;
-            if (m < Np) {
-                const uint8_t* op = fp.img + (DIR == 0 ? tl.e * fp.img_estride : 0);
-                sF[t * 128 + m] = reinterpret_cast<const int*>(op + (size_t)op_bytes)[m];
+            if (grp == 0) {
+                // the epilogue of item k - 2 has read this set of sEL and sF
+                const int t = k & 1;
+                if (k > 1 && !bwait(&bars->acc_empty[t], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
+                sEL[t * 128 + m] = EL;
+                if (m < Np) {
+                    const uint8_t* op = fp.img + (DIR == 0 ? tl.e * fp.img_estride : 0);
+                    sF[t * 128 + m] = reinterpret_cast<const int*>(op + (size_t)op_bytes)[m];
+                }
+                __syncwarp();
+                if (lane == 0) barrive(&bars->el_ready[t]);
             }
-            __syncwarp();
-            if (lane == 0) barrive(&bars->el_ready[t]);
             bool stop = false;
             for (int kc = 0; kc < nchunks; kc++) {
                 const int cg = k * nchunks + kc, a = cg % NA_RING;
+                if (W == 8 && a != grp) continue;
                 if (cg >= NA_RING && !bwait(&bars->a_empty[a], (uint32_t)((cg / NA_RING - 1) & 1), abort_flag)) {
                     stop = true;
                     break;
@@ -610,8 +642,10 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
         }
     } else {
         // ---------------------------------------------------------------- epilogue
-        const int quad = warp & 3, m = quad * 32 + lane;
-        const bool wide = fp.Kp > 64;
+        // warp w reads TMEM lanes 32 (w & 3) ..; with W = 8 the two warps of a lane quadrant
+        // take the first and the second half of the column blocks
+        const int quad = warp & 3, m = quad * 32 + lane, half = (warp - W) >> 2;
+        const bool wide = fp.Kp > 32;   // scaled accumulators reach 2^22
         int k = 0;
         for (long long it = blockIdx.x; it < nitems; it += gridDim.x, k++) {
             FxTile tl;
@@ -630,8 +664,8 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
             } else {
                 const long long t = tl.t0 + m;
                 if (DIR == 1) {
-                    const long long eil = t / d.Np;
-                    base = eil * d.NtNp + (t - eil * d.Np);
+                    const uint32_t eil = (uint32_t)t / (uint32_t)d.Np;
+                    base = (long long)eil * d.NtNp + (t - (long long)eil * d.Np);
                     stride = d.Np;
                 } else {
                     base = t * N;
@@ -643,9 +677,15 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
             // column blocks holding output rows of this pass (the padding blocks beyond N are
             // computed by the MMAs but not read)
             const int ncol = min(Npp, N - pass * Npp);
-            const int cb_end = (ncol + 7) & ~7;
+            const int nblk = (ncol + 7) >> 3, nh = W == 8 ? (nblk + 1) >> 1 : nblk;
+            const int cb_beg = half == 0 ? 0 : nh * 8, cb_end = half == 0 ? nh * 8 : nblk * 8;
             const uint32_t set_col = (uint32_t)((k % fp.tsets) * NA * Npp);
-            for (int cb = 0; cb < cb_end; cb += 8) {
+            if (cb_beg >= cb_end) {       // no block for this warp: release at once
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) barrive(&bars->acc_empty[t]);
+            }
+            for (int cb = cb_beg; cb < cb_end; cb += 8) {
                 uint32_t r[NA][8];
 #pragma unroll
                 for (int g = 0; g < NA; g++) {
@@ -669,18 +709,37 @@ __global__ void __launch_bounds__(FXW_THREADS, 2) k_contract_fx(Dims d, FxParams
                     if (lane == 0) barrive(&bars->acc_empty[t]);
                 }
                 if (valid) {
+                    // phases over the eight outputs (combine, convert, fix-ups), so that their
+                    // dependency chains overlap
+                    long long R[8];
+                    if (wide) {
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            uint32_t acc[NA];
+#pragma unroll
+                            for (int g = 0; g < NA; g++) acc[g] = r[g][j];
+                            R[j] = combine7<true>(acc);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            uint32_t acc[NA];
+#pragma unroll
+                            for (int g = 0; g < NA; g++) acc[g] = r[g][j];
+                            R[j] = combine7<false>(acc);
+                        }
+                    }
                     double v[8];
+                    bool ok[8], all_ok = true;
 #pragma unroll
                     for (int j = 0; j < 8; j++) {
-                        const long long R =
-                            NA == 6 ? combine6(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]),
-                                               __uint_as_float(r[2][j]), __uint_as_float(r[3][j]),
-                                               __uint_as_float(r[4][j]), __uint_as_float(r[NA - 1][j]))
-                                    : combine(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]),
-                                              __uint_as_float(r[2][j]), __uint_as_float(r[3][j]),
-                                              __uint_as_float(r[4][j]), wide);
-                        v[j] = scale_int(R, X[j]);
+                        v[j] = scale_int_fast(R[j], X[j], &ok[j]);
+                        all_ok = all_ok && ok[j];
                     }
+                    if (!all_ok)
+#pragma unroll
+                        for (int j = 0; j < 8; j++)
+                            if (!ok[j]) v[j] = R[j] == 0 ? 0.0 : ldexp_int(R[j], X[j]);
                     if (line_bad)
 #pragma unroll
                         for (int j = 0; j < 8; j++) v[j] = __longlong_as_double(0x7FF8000000000000ll);
@@ -747,7 +806,8 @@ struct FxCfg {
 };
 // tsets = 2 asks for two accumulator sets (one CTA per SM for 6 x 32 columns); it falls back
 // to one set when they do not fit the 512 TMEM columns or the operator is not resident
-static FxCfg fx_cfg(int dir, int N, int na, int tsets = 1) {
+static FxCfg fx_cfg(int dir, int N, int tsets = 1) {
+    const int na = NACC;
     int Np, Kp, KC;
     fx_geometry(N, &Np, &Kp, &KC);
     FxCfg c;
@@ -765,7 +825,7 @@ static FxCfg fx_cfg(int dir, int N, int na, int tsets = 1) {
         share = 233472 - 1024;
         c.b_all = stg + fx_rest_bytes(N, 1) <= share;
     }
-    if (c.tsets == 2 && !c.b_all) return fx_cfg(dir, N, na, 1);
+    if (c.tsets == 2 && !c.b_all) return fx_cfg(dir, N, 1);
     const size_t rest = fx_rest_bytes(N, c.b_all);
     c.nstg = 2 * stg + rest <= share ? 2 : 1;
     const size_t b = c.nstg * stg + rest;
@@ -774,59 +834,60 @@ static FxCfg fx_cfg(int dir, int N, int na, int tsets = 1) {
     return c;
 }
 
-static size_t fx_smem_max(int dir, int na) {
+static size_t fx_smem_max(int dir) {
     size_t mx = 0;
     for (int n = 2; n <= 128; n++)
         for (int ts = 1; ts <= 2; ts++) {
-            const size_t b = fx_cfg(dir, n, na, ts).smem;
+            const size_t b = fx_cfg(dir, n, ts).smem;
             mx = b > mx ? b : mx;
         }
     return mx;
 }
 
-// ---- tuning table: accumulator sets per (direction, nodes, accumulators) class, chosen by
-// the autotuner (grmhd_tune_contractions) or read from a tuning file; 0 = not tuned (one set)
+// ---- tuning table: accumulator sets per (direction, nodes, kind) class (kind 0 derivative,
+// 1 filter), chosen by the autotuner (grmhd_tune_contractions) or read from a tuning file;
+// 0 = not tuned (one set)
 namespace {
 std::mutex g_tune_lock;
 std::map<std::tuple<int, int, int>, int> g_tune;
 }  // namespace
 
-void fx_tune_set(int dir, int N, int nacc, int tsets) {
+void fx_tune_set(int dir, int N, int kind, int tsets) {
     std::lock_guard<std::mutex> lk(g_tune_lock);
-    g_tune[std::make_tuple(dir, N, nacc)] = tsets;
+    g_tune[std::make_tuple(dir, N, kind)] = tsets;
 }
 
-int fx_tune_get(int dir, int N, int nacc) {
+int fx_tune_get(int dir, int N, int kind) {
     std::lock_guard<std::mutex> lk(g_tune_lock);
-    auto it = g_tune.find(std::make_tuple(dir, N, nacc));
+    auto it = g_tune.find(std::make_tuple(dir, N, kind));
     return it == g_tune.end() ? 0 : it->second;
 }
 
-bool fx_two_sets_possible(int dir, int N, int nacc) {
+bool fx_two_sets_possible(int dir, int N) {
     if (!fx_supported(dir, N)) return false;
-    return fx_cfg(dir, N, nacc, 2).tsets == 2;
+    return fx_cfg(dir, N, 2).tsets == 2;
 }
 
-template <int DIR, int NA>
+template <int DIR, int W>
 static cudaError_t set_attr_fx() {
-    return cudaFuncSetAttribute(k_contract_fx<DIR, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fx_smem_max(DIR, NA));
+    return cudaFuncSetAttribute(k_contract_fx<DIR, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fx_smem_max(DIR));
 }
 
 cudaError_t fx_init() {
     cudaError_t e;
-    if ((e = set_attr_fx<0, NACC>()) != cudaSuccess) return e;
-    if ((e = set_attr_fx<0, 6>()) != cudaSuccess) return e;
-    if ((e = set_attr_fx<1, NACC>()) != cudaSuccess) return e;
-    if ((e = set_attr_fx<1, 6>()) != cudaSuccess) return e;
-    if ((e = set_attr_fx<2, 6>()) != cudaSuccess) return e;
-    return set_attr_fx<2, NACC>();
+    if ((e = set_attr_fx<0, 4>()) != cudaSuccess) return e;
+    if ((e = set_attr_fx<1, 4>()) != cudaSuccess) return e;
+    if ((e = set_attr_fx<2, 4>()) != cudaSuccess) return e;
+    if ((e = set_attr_fx<0, 8>()) != cudaSuccess) return e;
+    if ((e = set_attr_fx<1, 8>()) != cudaSuccess) return e;
+    return set_attr_fx<2, 8>();
 }
 
 cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int njobs, const uint8_t* img,
-                               long long img_estride, int* err, cudaStream_t s, int stall, int nacc, int tsets) {
+                               long long img_estride, int* err, cudaStream_t s, int stall, int kind, int tsets) {
     if (njobs <= 0) return cudaSuccess;
-    if (nacc != NACC && nacc != 6) return cudaErrorNotSupported;
+    if (kind != 0 && kind != 1) return cudaErrorNotSupported;
     const int N = dir == 0 ? d.Nr : (dir == 1 ? d.Nt : d.Np);
     if (!fx_supported(dir, N)) return cudaErrorNotSupported;
     // r and theta tiles are staged with bulk copies of row segments: 16-byte alignment
@@ -843,8 +904,8 @@ cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int
     fp.Kp = Kp;
     fp.Npp = Np > 64 ? 64 : Np;
     fp.npass = Np / fp.Npp;
-    if (tsets <= 0) tsets = fx_tune_get(dir, N, nacc);
-    const FxCfg cfg = fx_cfg(dir, N, nacc, tsets == 2 ? 2 : 1);
+    if (tsets <= 0) tsets = fx_tune_get(dir, N, kind);
+    const FxCfg cfg = fx_cfg(dir, N, tsets == 2 ? 2 : 1);
     fp.tmem_cols = cfg.cols;
     fp.nstg = cfg.nstg;
     fp.b_all = cfg.b_all;
@@ -853,22 +914,34 @@ cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int
     fp.err = err;
     fp.stall = stall;
     fp.tsets = cfg.tsets;
-    if (dir == 0) fp.ntiles = (long long)d.E * ((d.NtNp + 127) / 128);
-    else if (dir == 1) fp.ntiles = ((long long)d.E * d.Nr * d.Np + 127) / 128;
-    else fp.ntiles = (d.P / N + 127) / 128;
+    if (d.P >= (1LL << 31) || (d.P / 16 + d.E) * 2 * (long long)njobs >= (1LL << 31))
+        return cudaErrorNotSupported;   // 32-bit line and item arithmetic
+    fp.tpe = (uint32_t)((d.NtNp + 127) / 128);
+    fp.nlf = dir == 1 ? (uint32_t)((long long)d.E * d.Nr * d.Np) : (uint32_t)(d.P / N);
+    if (dir == 0) fp.ntiles = (long long)d.E * fp.tpe;
+    else fp.ntiles = ((long long)fp.nlf + 127) / 128;
     if (fp.ntiles <= 0) return cudaSuccess;
+    fp.per_job = (uint32_t)(fp.ntiles * fp.npass);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long nitems = fp.ntiles * fp.npass * njobs;
     const long long grid = nitems < (long long)cfg.ctas * nsm ? nitems : (long long)cfg.ctas * nsm;
     const size_t sm = cfg.smem;
-    if (dir == 0 && nacc == 6) k_contract_fx<0, 6><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
-    else if (dir == 0) k_contract_fx<0, NACC><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
-    else if (dir == 1 && nacc == 6) k_contract_fx<1, 6><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
-    else if (dir == 1) k_contract_fx<1, NACC><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
-    else if (nacc == 6) k_contract_fx<2, 6><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
-    else k_contract_fx<2, NACC><<<(unsigned)grid, FXW_THREADS, sm, s>>>(d, fp);
+    // one CTA per SM: eight converter and eight epilogue warps (the register file holds
+    // them at up to 112 registers a thread); two: four of each
+    const bool w8 = cfg.ctas == 1;
+    const unsigned nt = (unsigned)fx_threads(w8 ? 8 : 4);
+    if (dir == 0) {
+        if (w8) k_contract_fx<0, 8><<<(unsigned)grid, nt, sm, s>>>(d, fp);
+        else k_contract_fx<0, 4><<<(unsigned)grid, nt, sm, s>>>(d, fp);
+    } else if (dir == 1) {
+        if (w8) k_contract_fx<1, 8><<<(unsigned)grid, nt, sm, s>>>(d, fp);
+        else k_contract_fx<1, 4><<<(unsigned)grid, nt, sm, s>>>(d, fp);
+    } else {
+        if (w8) k_contract_fx<2, 8><<<(unsigned)grid, nt, sm, s>>>(d, fp);
+        else k_contract_fx<2, 4><<<(unsigned)grid, nt, sm, s>>>(d, fp);
+    }
     return cudaGetLastError();
 }
 

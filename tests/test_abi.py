@@ -128,10 +128,12 @@ def test_tuning_table_entries(lib):
     """The contraction tuning table (host side): entries in range are kept and read back,
     entries outside the documented ranges are refused, 0 restores the untuned default."""
     import paper_2508_18221_gb300 as pkg
-    assert lib.grmhd_tune_set(1, 33, 6, 2) == pkg.GRMHD_OK
-    assert lib.grmhd_tune_get(1, 33, 6) == 2
-    assert lib.grmhd_tune_set(1, 33, 6, 0) == pkg.GRMHD_OK
-    assert lib.grmhd_tune_get(1, 33, 6) == 0
-    for args in ((3, 24, 6, 1), (0, 1, 6, 1), (0, 129, 6, 1), (0, 24, 4, 1), (0, 24, 6, 3), (0, 24, 6, -1)):
+    assert lib.grmhd_tune_set(1, 33, 0, 2) == pkg.GRMHD_OK
+    assert lib.grmhd_tune_get(1, 33, 0) == 2
+    assert lib.grmhd_tune_get(1, 33, 1) == 0          # the filter class is separate
+    assert lib.grmhd_tune_set(1, 33, 0, 0) == pkg.GRMHD_OK
+    assert lib.grmhd_tune_get(1, 33, 0) == 0
+    for args in ((3, 24, 0, 1), (0, 1, 0, 1), (0, 129, 0, 1), (0, 24, 2, 1), (0, 24, -1, 1), (0, 24, 0, 3),
+                 (0, 24, 0, -1)):
         assert lib.grmhd_tune_set(*args) == pkg.GRMHD_EINVAL, args
-    assert lib.grmhd_tune_get(0, 24, 7) == pkg.GRMHD_EINVAL
+    assert lib.grmhd_tune_get(0, 24, 2) == pkg.GRMHD_EINVAL

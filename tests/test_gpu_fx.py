@@ -178,11 +178,11 @@ def test_contraction_maximum_sizes(pkg, contraction):
 def test_maximum_sizes_rhs_and_limits(pkg):
     """Right-hand sides at the largest node counts (thin grids the oracle evaluates in
     seconds) with the default contraction choice against the oracle at the FP64 bar: 64
-    radial and 64 Chebyshev theta nodes (digit slices with six accumulators), 128
+    radial and 64 Chebyshev theta nodes (digit slices, seven exact accumulators), 128
     Chebyshev theta nodes (FP64 units: measured 9.3e-12 of the bar's normalisation, which
     follows first-derivative rounding, max|U| / dx_min, while Chebyshev second derivatives
     round with the square of the operator norm), 128 Fourier theta and 128 phi nodes
-    (digit slices, six accumulators).  Limits: n_phi above 128 or odd, n_theta above 128,
+    (digit slices).  Limits: n_phi above 128 or odd, n_theta above 128,
     n_r above 64 are invalid."""
     import torch
 
@@ -204,12 +204,13 @@ def test_maximum_sizes_rhs_and_limits(pkg):
             pkg.Context(grid, phys, opts, stream)
 
 
-def test_six_accumulators_reach_fp64_accuracy(pkg):
-    """Every derivative takes the six-accumulator instance (the digit-order sum 6 exact):
-    its error stays within a few times the FP64 units' (measured 7e-16 of the bound at 64
-    and 128 nodes against 7.5e-15 and 1.4e-14 with five accumulators), bar 2e-15 of the
-    bound, in every direction; the phi lines carry a large constant plus small noise, the
-    case where the five-accumulator error showed in the right-hand side."""
+def test_exact_accumulators_reach_fp64_accuracy(pkg):
+    """Every digit-order sum has an exact accumulator of its own, so the error is that of
+    the dropped digit pairs and the final roundings and stays within a few times the FP64
+    units' (an earlier form that folded the sums 6..8 into one rounding accumulator measured
+    7.5e-15 and 1.4e-14 of the bound at 64 and 128 nodes), bar 2e-15 of the bound, in
+    every direction; the phi lines carry a large constant plus small noise, the case
+    where a rounding accumulator's error showed in the right-hand side."""
     worst = {}
     for nr, nt, nph, d in ((24, 4, 4, 0), (32, 4, 4, 0), (40, 4, 4, 0), (64, 4, 4, 0), (4, 32, 4, 1),
                            (4, 48, 4, 1), (4, 128, 4, 1), (4, 4, 64, 2), (4, 4, 128, 2)):
@@ -225,7 +226,7 @@ def test_six_accumulators_reach_fp64_accuracy(pkg):
         err = np.abs(got - (g.d_r, g.d_t, g.d_p)[d](u)) / _bound(g, absD, u, d)
         worst[f"{(nr, nt, nph)[d]} nodes dir {d}"] = float(err.max())
         assert err.max() <= 2e-15, ((nr, nt, nph), d, float(err.max()))
-    _report("six_accumulators", worst)
+    _report("exact_accumulators", worst)
 
 
 @pytest.mark.parametrize("nr,nt,nph", [(24, 32, 64), (8, 12, 16), (32, 32, 32)])
@@ -246,12 +247,12 @@ def test_two_accumulator_sets_are_bitwise_equal(pkg, nr, nt, nph):
         for d in range(3):
             outs = []
             for ts in (1, 2):
-                assert lib.grmhd_tune_set(d, ns[d], 6, ts) == pkg.GRMHD_OK
+                assert lib.grmhd_tune_set(d, ns[d], 0, ts) == pkg.GRMHD_OK
                 dst = torch.zeros_like(src)
                 ctx.debug_deriv(src, dst, 4, d)
                 outs.append(dst.cpu().numpy())
             np.testing.assert_array_equal(outs[0], outs[1])
     finally:
         for d in range(3):
-            lib.grmhd_tune_set(d, ns[d], 6, 0)
+            lib.grmhd_tune_set(d, ns[d], 0, 0)
         ctx.close()
