@@ -744,7 +744,22 @@ __global__ void __launch_bounds__(fx_threads(W), W == 4 ? 2 : 1) k_contract_fx(D
 #pragma unroll
                         for (int j = 0; j < 8; j++) v[j] = __longlong_as_double(0x7FF8000000000000ll);
                     double* pd = jb.dst + base + (long long)c0 * stride;
-                    if (jb.accumulate) {
+                    if (DIR == 2 && c0 + 8 <= N && (reinterpret_cast<uintptr_t>(pd) & 15) == 0) {
+                        // phi: the block's outputs are contiguous in the line: 16-byte stores
+                        double2* p2 = reinterpret_cast<double2*>(pd);
+                        if (jb.accumulate) {
+#pragma unroll
+                            for (int h = 0; h < 4; h++) {
+                                double2 o = p2[h];
+                                o.x += v[2 * h];
+                                o.y += v[2 * h + 1];
+                                p2[h] = o;
+                            }
+                        } else {
+#pragma unroll
+                            for (int h = 0; h < 4; h++) p2[h] = make_double2(v[2 * h], v[2 * h + 1]);
+                        }
+                    } else if (jb.accumulate) {
 #pragma unroll
                         for (int j = 0; j < 8; j++)
                             if (c0 + j < N) pd[(long long)j * stride] += v[j];
