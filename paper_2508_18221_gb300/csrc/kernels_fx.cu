@@ -300,8 +300,10 @@ __device__ __forceinline__ void fx_stage(const Dims& d, const FxTile& tl, int N,
 // Shared memory (bytes): [staging x nstg | A ring 2 x (7 x 128 x 16 x 2) |
 //   B digits of all chunks (nchunks x 7 x Np x 16 x 2) | sEL 2 x 128 x 4 | sF 2 x 128 x 4 |
 //   barriers | tmem address | abort flag]
-// W = converter warps = epilogue warps: 4 at two CTAs per SM, 8 at one
-__host__ __device__ constexpr int fx_threads(int W) { return (2 * W + 2) * 32; }
+// WC converter warps and WE epilogue warps (multiples of 4), a staging warp and an MMA warp:
+// (4, 4) at two CTAs per SM, (8, 8) at one.  (Eight epilogue warps beside four converters at
+// two CTAs per SM, 72 registers a thread, spill and were measured slower.)
+__host__ __device__ constexpr int fx_threads(int WC, int WE) { return (WC + WE + 2) * 32; }
 constexpr int NA_RING = 2;
 
 // exponents and their barriers alternate between two sets by item parity, so that the
@@ -376,8 +378,8 @@ __device__ __forceinline__ void fx_item(const FxParams& fp, const Dims& d, long 
     fx_tile<DIR>(fp, d, fp.npass == 2 ? r >> 1 : r, tl);
 }
 
-template <int DIR, int W>
-__global__ void __launch_bounds__(fx_threads(W), W == 4 ? 2 : 1) k_contract_fx(Dims d, FxParams fp) {
+template <int DIR, int WC, int WE>
+__global__ void __launch_bounds__(fx_threads(WC, WE), WC == 4 ? 2 : 1) k_contract_fx(Dims d, FxParams fp) {
     constexpr int NA = NACC;
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(fx_threads(W), W == 4 ? 2 : 1) k_contract_fx(D
     if (tid == 0) {
         for (int b = 0; b < 2; b++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars->stg_full[b])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars->stg_empty[b])), "r"(W));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars->stg_empty[b])), "r"(WC));
         }
         for (int a = 0; a < NA_RING; a++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars->a_full[a])));
@@ -411,7 +413,7 @@ __global__ void __launch_bounds__(fx_threads(W), W == 4 ? 2 : 1) k_contract_fx(D
         }
         for (int t = 0; t < 2; t++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars->acc_full[t])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars->acc_empty[t])), "r"(W));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars->acc_empty[t])), "r"(WE));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars->el_ready[t])));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars->b_full)));
@@ -428,7 +430,7 @@ __global__ void __launch_bounds__(fx_threads(W), W == 4 ? 2 : 1) k_contract_fx(D
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 2 * W) {
+    if (warp == WC + WE) {
         // ---------------------------------------------------------------- staging
         int k = 0;
         int last_k[2] = {-1, -1};          // last item staged into each buffer
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(fx_threads(W), W == 4 ? 2 : 1) k_contract_fx(D
         if (*abort_flag && lane == 0)
             for (int b = 0; b < fp.nstg; b++)
                 if (last_k[b] >= 0) bwait_for(&bars->stg_full[b], (uint32_t)((last_k[b] / fp.nstg) & 1), 1000000ull);
-    } else if (warp == 2 * W + 1) {
+    } else if (warp == WC + WE + 1) {
         // ---------------------------------------------------------------- MMA issue
         // The whole warp walks the loop with warp-uniform values (descriptors, columns,
         // counters); one elected lane issues the copies, MMAs and commits.  (Issued from
@@ -561,7 +563,7 @@ __global__ void __launch_bounds__(fx_threads(W), W == 4 ? 2 : 1) k_contract_fx(D
             if (n_b > 0) bwait_for(&bars->b_full, (n_b - 1) & 1, 1000000ull);
         }
         __syncwarp();
-    } else if (warp < W) {
+    } else if (warp < WC) {
         // ---------------------------------------------------------------- conversion
         // thread m = line m; with W = 8 two groups of 4 warps share the K chunks by A ring
         // slot (group g writes the chunks that land in slot g); group 0 publishes exponents
@@ -594,7 +596,7 @@ __global__ void __launch_bounds__(fx_threads(W), W == 4 ? 2 : 1) k_contract_fx(D
             bool stop = false;
             for (int kc = 0; kc < nchunks; kc++) {
                 const int cg = k * nchunks + kc, a = cg % NA_RING;
-                if (W == 8 && a != grp) continue;
+                if (WC == 8 && a != grp) continue;
                 if (cg >= NA_RING && !bwait(&bars->a_empty[a], (uint32_t)((cg / NA_RING - 1) & 1), abort_flag)) {
                     stop = true;
                     break;
@@ -644,7 +646,7 @@ __global__ void __launch_bounds__(fx_threads(W), W == 4 ? 2 : 1) k_contract_fx(D
         // ---------------------------------------------------------------- epilogue
         // warp w reads TMEM lanes 32 (w & 3) ..; with W = 8 the two warps of a lane quadrant
         // take the first and the second half of the column blocks
-        const int quad = warp & 3, m = quad * 32 + lane, half = (warp - W) >> 2;
+        const int quad = warp & 3, m = quad * 32 + lane, half = (warp - WC) >> 2;
         const bool wide = fp.Kp > 32;   // scaled accumulators reach 2^22
         int k = 0;
         for (long long it = blockIdx.x; it < nitems; it += gridDim.x, k++) {
@@ -677,7 +679,7 @@ __global__ void __launch_bounds__(fx_threads(W), W == 4 ? 2 : 1) k_contract_fx(D
             // column blocks holding output rows of this pass (the padding blocks beyond N are
             // computed by the MMAs but not read)
             const int ncol = min(Npp, N - pass * Npp);
-            const int nblk = (ncol + 7) >> 3, nh = W == 8 ? (nblk + 1) >> 1 : nblk;
+            const int nblk = (ncol + 7) >> 3, nh = WE == 8 ? (nblk + 1) >> 1 : nblk;
             const int cb_beg = half == 0 ? 0 : nh * 8, cb_end = half == 0 ? nh * 8 : nblk * 8;
             const uint32_t set_col = (uint32_t)((k % fp.tsets) * NA * Npp);
             if (cb_beg >= cb_end) {       // no block for this warp: release at once
@@ -883,20 +885,24 @@ bool fx_two_sets_possible(int dir, int N) {
     return fx_cfg(dir, N, 2).tsets == 2;
 }
 
-template <int DIR, int W>
+template <int DIR, int WC, int WE>
 static cudaError_t set_attr_fx() {
-    return cudaFuncSetAttribute(k_contract_fx<DIR, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_contract_fx<DIR, WC, WE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)fx_smem_max(DIR));
+}
+
+template <int DIR>
+static cudaError_t set_attr_fx_dir() {
+    cudaError_t e;
+    if ((e = set_attr_fx<DIR, 4, 4>()) != cudaSuccess) return e;
+    return set_attr_fx<DIR, 8, 8>();
 }
 
 cudaError_t fx_init() {
     cudaError_t e;
-    if ((e = set_attr_fx<0, 4>()) != cudaSuccess) return e;
-    if ((e = set_attr_fx<1, 4>()) != cudaSuccess) return e;
-    if ((e = set_attr_fx<2, 4>()) != cudaSuccess) return e;
-    if ((e = set_attr_fx<0, 8>()) != cudaSuccess) return e;
-    if ((e = set_attr_fx<1, 8>()) != cudaSuccess) return e;
-    return set_attr_fx<2, 8>();
+    if ((e = set_attr_fx_dir<0>()) != cudaSuccess) return e;
+    if ((e = set_attr_fx_dir<1>()) != cudaSuccess) return e;
+    return set_attr_fx_dir<2>();
 }
 
 cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int njobs, const uint8_t* img,
@@ -944,18 +950,18 @@ cudaError_t launch_contract_fx(int dir, const Dims& d, const DerivJob* jobs, int
     const long long grid = nitems < (long long)cfg.ctas * nsm ? nitems : (long long)cfg.ctas * nsm;
     const size_t sm = cfg.smem;
     // one CTA per SM: eight converter and eight epilogue warps (the register file holds
-    // them at up to 112 registers a thread); two: four of each
+    // them at up to 112 registers a thread); two: four of each (96 registers)
     const bool w8 = cfg.ctas == 1;
-    const unsigned nt = (unsigned)fx_threads(w8 ? 8 : 4);
+    const unsigned nt = (unsigned)(w8 ? fx_threads(8, 8) : fx_threads(4, 4));
     if (dir == 0) {
-        if (w8) k_contract_fx<0, 8><<<(unsigned)grid, nt, sm, s>>>(d, fp);
-        else k_contract_fx<0, 4><<<(unsigned)grid, nt, sm, s>>>(d, fp);
+        if (w8) k_contract_fx<0, 8, 8><<<(unsigned)grid, nt, sm, s>>>(d, fp);
+        else k_contract_fx<0, 4, 4><<<(unsigned)grid, nt, sm, s>>>(d, fp);
     } else if (dir == 1) {
-        if (w8) k_contract_fx<1, 8><<<(unsigned)grid, nt, sm, s>>>(d, fp);
-        else k_contract_fx<1, 4><<<(unsigned)grid, nt, sm, s>>>(d, fp);
+        if (w8) k_contract_fx<1, 8, 8><<<(unsigned)grid, nt, sm, s>>>(d, fp);
+        else k_contract_fx<1, 4, 4><<<(unsigned)grid, nt, sm, s>>>(d, fp);
     } else {
-        if (w8) k_contract_fx<2, 8><<<(unsigned)grid, nt, sm, s>>>(d, fp);
-        else k_contract_fx<2, 4><<<(unsigned)grid, nt, sm, s>>>(d, fp);
+        if (w8) k_contract_fx<2, 8, 8><<<(unsigned)grid, nt, sm, s>>>(d, fp);
+        else k_contract_fx<2, 4, 4><<<(unsigned)grid, nt, sm, s>>>(d, fp);
     }
     return cudaGetLastError();
 }
