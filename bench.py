@@ -635,8 +635,9 @@ def tensor_rel_l2(a, b, nv):
 # test_precision_variant_report (asserted there to stay below the spectral truncation
 # level of every tensor); the largest and the tightest tensor.
 MIXED_STATED_ERROR = {"instance": "2 elements 12 x 12 x 16 (4,608 nodes), 100 SSP-RK3 steps",
-                      "max_rel_l2_vs_fp64_oracle": 7.6e-05, "tensor": "B_driver (starts at zero)",
-                      "tightest": "K: 2.8e-05 against a truncation level of 2.9e-05",
+                      "max_rel_l2_vs_fp64_oracle": 7.5e-05, "tensor": "B_driver (starts at zero)",
+                      "tightest": "K: 2.8e-05 against a truncation level of 2.9e-05 "
+                                  "(0.95-1.00 of it over five noise seeds)",
                       "source": "tests/test_gpu_mixed.py::test_precision_variant_report"}
 
 
