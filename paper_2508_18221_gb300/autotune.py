@@ -1,7 +1,8 @@
 """Autotuner of the FP64 digit-slice contractions: for every (direction, nodes,
 kind) class (kind: derivative or filter) of the given workloads it times the contraction with one and with two
-TMEM accumulator sets on a context of that shape (grmhd_tune_contractions) and writes the
-faster choice per class to fx_tuning.txt next to the library, which every later process
+TMEM accumulator sets on a context of that shape (grmhd_tune_contractions) and writes, per
+class, the choice with the lower time summed over the shapes that use it (two sets only
+when they win by 2 %) to fx_tuning.txt next to the library, which every later process
 reads at its first context.
 
     python -m paper_2508_18221_gb300.autotune --workloads c2,c4,c5 [--out PATH]
@@ -44,7 +45,9 @@ def main(argv=None):
         else:
             shapes.append((w, config(w)))
     lib = pkg.load()
-    table = {}
+    # per class: summed ms with one and with two sets over the shapes that use it (shapes of
+    # different sizes can disagree; the class takes the choice with the lower total)
+    sums = {}
     stream = torch.cuda.Stream()
     for name, cfg in shapes:
         grid, phys, opts = pkg.make_structs(cfg)
@@ -56,11 +59,22 @@ def main(argv=None):
         ns = (cfg.n_r, cfg.n_theta, cfg.n_phi)
         for (d, kind), (m1, m2, ch) in sorted(res.items()):
             key = (d, ns[d], 0 if kind == "derivative" else 1)
-            table[key] = ch
+            t = sums.setdefault(key, [0.0, 0.0, ch != 0])
+            t[0] += m1
+            t[1] = t[1] + m2 if (m2 >= 0 and t[1] >= 0) else -1.0
             two = f"{m2:.4f} ms" if m2 >= 0 else "n/a"
             print(f"{name:28s} dir {d} n {ns[d]:3d} {kind:10s} one set {m1:.4f} ms, two sets {two} -> {ch}",
                   flush=True)
         ctx.close()
+    # two sets only where they win by 2 % in total (the launch-to-launch spread is about 1 %)
+    table = {}
+    for key, (s1, s2, tc) in sums.items():
+        table[key] = 0 if not tc else (2 if 0 <= s2 < 0.98 * s1 else 1)
+    for key in sorted(table):
+        s1, s2, _ = sums[key]
+        two = f"{s2:.4f} ms" if s2 >= 0 else "n/a"
+        print(f"class dir {key[0]} n {key[1]:3d} kind {key[2]}: one set {s1:.4f} ms, two sets {two} in total "
+              f"-> {table[key]}", flush=True)
     out = a.out or os.path.join(os.path.dirname(pkg.LIB_PATH), "fx_tuning.txt")
     with open(out, "w") as fh:
         fh.write("# digit-slice contraction tuning: direction nodes kind(0 derivative, 1 filter) sets "
