@@ -110,7 +110,7 @@ typedef struct {
  * the exact root on the 2-element workload (2e-11 in the torus), so the default stays
  * the Newton solve.  contraction: how the FP64
  * spectral contractions (all derivatives at precision 0, the filter at every precision)
- * run: 0 (default) on the BF16 tensor cores with exact base-256 digit slices of the
+ * run: 0 (default) on the FP16 tensor cores with exact base-256 digit slices of the
  * FP64 values (Ozaki splitting; up to 128 nodes per direction; each digit-order sum in an
  * exact accumulator of its own, error about 1e-15 of sum_j |D_ij| max_j |u_j|; above 64
  * Chebyshev nodes the FP64 units take the derivatives), 1 on the FP64 units.  coupling: 0 (default) one

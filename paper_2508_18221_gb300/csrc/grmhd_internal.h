@@ -102,7 +102,7 @@ cudaError_t launch_rhs(const Dims& d, const PhysParams& pp, const double* U0, co
 cudaError_t launch_contract_tc(int dir, int in_fp32, const Dims& d, const TcJob* jobs, int njobs,
                                const uint8_t* op_img, int tf32, const double* r_scale, int* err,
                                cudaStream_t s);
-// FP64-accurate contraction on the BF16 tensor cores (kernels_fx.cu): exact digit
+// FP64-accurate contraction on the FP16 tensor cores (kernels_fx.cu): exact digit
 // slices of the FP64 values; op_img from fx_operator_image, img_estride = bytes between
 // per-element images (radial direction) or 0; Np, Kp, KC from fx_geometry
 void fx_geometry(int N, int* Np, int* Kp, int* KC);

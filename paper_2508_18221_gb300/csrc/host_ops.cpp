@@ -241,6 +241,16 @@ std::vector<uint8_t> tc_operator_image(const std::vector<double>& D, int N, int 
 // row); Y = round(x 2^(1076 - F_n)) is a signed integer with |Y| <= 2^54, and the bytes of
 // Y + 0x80808080808080 minus 128 are its balanced base-256 digits c_1..c_7 (most
 // significant first).  Slice l holds c_l 2^(-8 (l - 1)), exact in BF16.
+// IEEE binary16 bits of an integer d in [-128, 127] (exact: at most 8 significant bits)
+static uint16_t half_of_digit(int d) {
+    if (d == 0) return 0;
+    const uint16_t sgn = d < 0 ? 0x8000 : 0;
+    const int a = d < 0 ? -d : d;
+    int e = 0;
+    while ((a >> (e + 1)) != 0) e++;                      // a in [2^e, 2^(e+1))
+    return (uint16_t)(sgn | ((e + 15) << 10) | ((a - (1 << e)) << (10 - e)));
+}
+
 std::vector<uint8_t> fx_operator_image(const std::vector<double>& D, int N, double scale, int Np, int Kp,
                                        int KC) {
     const int nch = Kp / KC, kcores = KC / 8, Npp = Np > 64 ? 64 : Np;
@@ -267,10 +277,7 @@ std::vector<uint8_t> fx_operator_image(const std::vector<double>& D, int N, doub
             const int kc = k / KC, kk = k % KC;
             for (int q = 1; q <= 7; q++) {
                 const int digit = (int)((Z >> (8 * (7 - q))) & 0xFF) - 128;
-                const float v = std::ldexp((float)digit, -8 * (q - 1));
-                uint32_t u;
-                std::memcpy(&u, &v, 4);
-                const uint16_t b = (uint16_t)(u >> 16);
+                const uint16_t b = half_of_digit(digit);
                 // row of the chunk's tall B matrix: pass p (Npp = min(Np, 64) output rows),
                 // then slice, then the row within the pass
                 const int row = ((n / Npp) * 7 + (q - 1)) * Npp + n % Npp;

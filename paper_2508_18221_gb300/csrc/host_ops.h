@@ -25,10 +25,10 @@ std::vector<double> circulant(const std::vector<double>& row);
 // K-major core-matrix layout padded to 16 in both dims; 3 BF16 slices or 1 TF32 copy
 std::vector<uint8_t> tc_operator_image(const std::vector<double>& D, int N, int tf32);
 // operator scale * D (N x N) for the FP64-accurate tensor-core contraction
-// (kernels_fx.cu): per K chunk of KC columns one tall BF16 matrix in the K-major
+// (kernels_fx.cu): per K chunk of KC columns one tall FP16 matrix in the K-major
 // core-matrix layout whose rows are, per pass of Npp = min(Np, 64) output rows, the seven
-// balanced base-256 digit slices of those rows one after the other; then the Np row
-// exponents (int32); size a multiple of 16 bytes
+// balanced base-256 digit slices of those rows one after the other (each digit an FP16
+// integer in [-128, 127]); then the Np row exponents (int32); size a multiple of 16 bytes
 std::vector<uint8_t> fx_operator_image(const std::vector<double>& D, int N, double scale, int Np, int Kp,
                                        int KC);
 // BSSN variables 0..23 of the Kerr-Schild slice at (r, theta)

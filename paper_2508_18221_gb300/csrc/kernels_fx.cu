@@ -1,11 +1,11 @@
-// FP64-accurate spectral contractions on the BF16 tensor cores (tcgen05, sm_103a).
+// FP64-accurate spectral contractions on the 16-bit tensor cores (tcgen05, sm_103a).
 //
 // out[line][i] = sum_j D[i][j] u[line][j] in double precision, computed with the
 // error-free splitting of Ozaki, Ogita, Oishi & Rump (Numer. Algorithms 59, 2012):
 //   * every line of u gets one common exponent (its largest), every row of D its own;
 //     relative to it each value is a signed 54-bit fixed-point integer, written as seven
 //     balanced base-256 digits d_1..d_7 in [-128, 127] (most significant first);
-//   * a digit fits a BF16 exactly and a product of two digits (|.| <= 2^14) fits an FP32
+//   * a digit fits an FP16 exactly and a product of two digits (|.| <= 2^14) fits an FP32
 //     exactly, so the tensor core forms sum_j c_l(i,j) d_q(j) without rounding as long as
 //     the running sum stays below 2^24 (true for K <= 128 and the sums below);
 //   * the 28 digit pairs with q + l <= 8 are kept, each digit-order sum s = q + l = 2..8 in
@@ -30,7 +30,6 @@
 // on the host in the K-major core-matrix layout (8 rows x 16 bytes per core matrix) and
 // fetched by cp.async.bulk; the line digits are formed by the converter warps from the
 // FP64 bits.  Waits are bounded in time and report through *err.
-#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include <map>
@@ -58,13 +57,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;                // base offset 0, relative LBO, no swizzle
 }
 
-// D = F32, A = B = BF16, both K-major; N >> 3 at bit 17, M >> 4 at bit 24
-__device__ __forceinline__ uint32_t instr_desc_bf16(int m, int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+// D = F32, A = B = F16, both K-major; N >> 3 at bit 17, M >> 4 at bit 24
+__device__ __forceinline__ uint32_t instr_desc_f16(int m, int n) {
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t id, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t id, uint32_t acc) {
     asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
                  "l"(da), "l"(db), "r"(id), "r"(acc));
@@ -85,18 +84,24 @@ __device__ __forceinline__ unsigned long long digit_word(double u, int EL) {
     return (unsigned long long)(x + (long long)DIG_BIAS);
 }
 
-// FP32 value (b - 128) * 2^(-8 (q-1)) of byte b of `w` (byte index sel 0..3): the byte is
-// placed in the mantissa of 1.5 * 2^23 and the offset removed by one exact FMA.
-template <int Q>
-__device__ __forceinline__ float digit_val(uint32_t w, int sel) {
-    constexpr float S = Q == 1 ? 1.f : (Q == 2 ? 0x1p-8f : (Q == 3 ? 0x1p-16f : (Q == 4 ? 0x1p-24f : (Q == 5 ? 0x1p-32f : (Q == 6 ? 0x1p-40f : 0x1p-48f)))));
-    const float f = __uint_as_float(__byte_perm(w, 0x4B400000u, 0x7640u | (uint32_t)sel));
-    return fmaf(f, S, -12583040.f * S);
+// Digit words of a value pair (u0, u1) for the A operand: FP16x2 words holding digit q of
+// u0 (low half) and of u1 (high half).  A biased digit byte b is placed under the byte
+// 0x64, giving the FP16 number 1024 + b, and one packed FP16 add of -1152 leaves b - 128
+// exactly.  Per value, four byte permutes spread its digit bytes over halves whose high
+// byte is 0x64 (e: bytes 0 and 2, o: bytes 1 and 3 of each 32-bit word of Z); per digit,
+// one permute pairs the two values and one packed add removes the bias.
+struct DigitHalves {
+    uint32_t el, ol, eh, oh;
+};
+__device__ __forceinline__ DigitHalves digit_halves(unsigned long long z) {
+    const uint32_t l = (uint32_t)z, h = (uint32_t)(z >> 32), C = 0x64646464u;
+    return {__byte_perm(l, C, 0x4240), __byte_perm(l, C, 0x4341), __byte_perm(h, C, 0x4240),
+            __byte_perm(h, C, 0x4441)};
 }
-
-// two BF16 (exact: at most 8 significant bits) packed low = a, high = b
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632u);
+__device__ __forceinline__ uint32_t unbias(uint32_t w) {
+    uint32_t r;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(w), "r"(0xE480E480u));  // -1152 in both halves
+    return r;
 }
 
 // R * 2^X: one correctly rounded integer-to-double conversion, then the power of two is
@@ -127,12 +132,12 @@ __device__ __forceinline__ double ldexp_int(long long R, int X) {
     return __longlong_as_double((long long)(sgn | ((((unsigned long long)(be - 1)) << 52) + mant)));
 }
 
-// T = g_2 + ... + g_8 as the integer R = round(T 2^40), g_s = acc[s - 2] an exact multiple
-// of 2^(-8 (s - 2)): n_s = g_s 2^(8 (s - 2)) is an integer with |n_s| <= (s - 1) K 2^14, below
-// 2^24 for K <= 128 and below 2^22 for K <= 32.
+// T = sum_s n_s 2^(-8 (s - 2)) as the integer R = round(T 2^40), n_s = acc[s - 2] the exact
+// integer sum of the digit products of order s (digits are plain integers in both
+// operands), |n_s| <= (s - 1) K 2^14: below 2^24 for K <= 128 and below 2^22 for K <= 32.
 // Each n_s is made non-negative by an offset, t_s = n_s + o_s: below 2^22 t_s is read off
-// the bits of g_s 2^(8 (s - 2)) + 1.5 * 2^23 (the low 23 bits hold n_s + 2^22; exact, as
-// the value is an integer), above it comes from a float-to-integer conversion (exact too).
+// the bits of n_s + 1.5 * 2^23 (the low 23 bits hold n_s + 2^22; exact, as n_s is an
+// integer), above it comes from a float-to-integer conversion (exact too).
 // The t_s are summed at their byte offsets with 32 x 32 -> 64-bit multiply-adds (an
 // unsigned sum below 2^63), the s = 8 term rounded to the unit of s = 7 (half up), and the
 // offsets' total is subtracted once.
@@ -143,19 +148,14 @@ __device__ __forceinline__ long long combine7(const uint32_t* acc) {
     unsigned long long off;
     if (!WIDE) {
 #pragma unroll
-        for (int s = 0; s < NACC; s++) {
-            const float sc = __int_as_float((127 + 8 * s) << 23);  // 2^(8 s)
-            t[s] = (uint32_t)__float_as_int(fmaf(__uint_as_float(acc[s]), sc, MAG)) & 0x7FFFFFu;
-        }
+        for (int s = 0; s < NACC; s++) t[s] = (uint32_t)__float_as_int(__uint_as_float(acc[s]) + MAG) & 0x7FFFFFu;
         // o_s = 2^22 for every s
         off = (1ull << 62) + (1ull << 54) + (1ull << 46) + (1ull << 38) + (1ull << 30) + (1ull << 22) + (1ull << 14);
     } else {
         // |n_s| <= (s - 1) K 2^14 <= (s - 1) 2^21: o_2 = 2^21, the others o_s = 2^24
 #pragma unroll
-        for (int s = 0; s < NACC; s++) {
-            const float sc = __int_as_float((127 + 8 * s) << 23);
-            t[s] = (uint32_t)(__float2int_rn(__uint_as_float(acc[s]) * sc) + (s == 0 ? (1 << 21) : (1 << 24)));
-        }
+        for (int s = 0; s < NACC; s++)
+            t[s] = (uint32_t)(__float2int_rn(__uint_as_float(acc[s])) + (s == 0 ? (1 << 21) : (1 << 24)));
         off = (1ull << 61) + (1ull << 56) + (1ull << 48) + (1ull << 40) + (1ull << 32) + (1ull << 24) + (1ull << 16);
     }
     // t_2 2^40 + t_3 2^32 + t_4 2^24 + t_5 2^16 + t_6 2^8 + t_7 + round(t_8 / 256)
@@ -536,8 +536,8 @@ __global__ void __launch_bounds__(fx_threads(WC, WE), WC == 4 ? 2 : 1) k_contrac
                     for (int q = 0; q < NDIG; q++)
                         for (int l0 = 0; l0 < NDIG - q; l0 += gmax) {
                             const int c = min(gmax, NDIG - q - l0);
-                            mma_bf16(tmem + set_col + (uint32_t)((q + l0) * Npp), smem_desc(a0 + q * a_bytes, lbo, sbo),
-                                     smem_desc(b0 + l0 * bs_bytes, lbo, sbo), instr_desc_bf16(128, c * Npp),
+                            mma_f16(tmem + set_col + (uint32_t)((q + l0) * Npp), smem_desc(a0 + q * a_bytes, lbo, sbo),
+                                     smem_desc(b0 + l0 * bs_bytes, lbo, sbo), instr_desc_f16(128, c * Npp),
                                      (kc == 0 && q == 0) ? 0u : 1u);
                         }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -615,16 +615,16 @@ __global__ void __launch_bounds__(fx_threads(WC, WE), WC == 4 ? 2 : 1) k_contrac
                             const int kk = k0 + 2 * h;
                             const double u0 = kk < N ? stg_at<DIR>(stg, m, kk, N) : 0.0;
                             const double u1 = kk + 1 < N ? stg_at<DIR>(stg, m, kk + 1, N) : 0.0;
-                            const unsigned long long z0 = digit_word(u0, EL), z1 = digit_word(u1, EL);
-                            const uint32_t l0 = (uint32_t)z0, h0 = (uint32_t)(z0 >> 32);
-                            const uint32_t l1 = (uint32_t)z1, h1 = (uint32_t)(z1 >> 32);
-                            w[0][h] = pack_bf16(digit_val<1>(h0, 2), digit_val<1>(h1, 2));
-                            w[1][h] = pack_bf16(digit_val<2>(h0, 1), digit_val<2>(h1, 1));
-                            w[2][h] = pack_bf16(digit_val<3>(h0, 0), digit_val<3>(h1, 0));
-                            w[3][h] = pack_bf16(digit_val<4>(l0, 3), digit_val<4>(l1, 3));
-                            w[4][h] = pack_bf16(digit_val<5>(l0, 2), digit_val<5>(l1, 2));
-                            w[5][h] = pack_bf16(digit_val<6>(l0, 1), digit_val<6>(l1, 1));
-                            w[6][h] = pack_bf16(digit_val<7>(l0, 0), digit_val<7>(l1, 0));
+                            const DigitHalves a0 = digit_halves(digit_word(u0, EL));
+                            const DigitHalves a1 = digit_halves(digit_word(u1, EL));
+                            // digit q = 1 .. 7 sits in byte 7 - q of Z
+                            w[0][h] = unbias(__byte_perm(a0.eh, a1.eh, 0x7632));   // byte 6
+                            w[1][h] = unbias(__byte_perm(a0.oh, a1.oh, 0x5410));   // byte 5
+                            w[2][h] = unbias(__byte_perm(a0.eh, a1.eh, 0x5410));   // byte 4
+                            w[3][h] = unbias(__byte_perm(a0.ol, a1.ol, 0x7632));   // byte 3
+                            w[4][h] = unbias(__byte_perm(a0.el, a1.el, 0x7632));   // byte 2
+                            w[5][h] = unbias(__byte_perm(a0.ol, a1.ol, 0x5410));   // byte 1
+                            w[6][h] = unbias(__byte_perm(a0.el, a1.el, 0x5410));   // byte 0
                         }
                     }
                     const uint32_t off = (uint32_t)(((m >> 3) * kcores + g8) * 128 + (m & 7) * 16);
